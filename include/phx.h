@@ -1,0 +1,182 @@
+/*
+ * phx -- GB300 (sm_103a) three-phonon scattering library: C ABI.
+ *
+ * The library computes, for a crystal described by its second- and third-order
+ * interatomic force constants (IFCs), the harmonic phonons on a q-mesh, the anharmonic
+ * linewidths gamma of the modes at irreducible q-points, and the RTA lattice thermal
+ * conductivity.  It follows the kALDo 2.0 paper (arXiv 2602.23728): Sec. "Interatomic
+ * Force Constants" (Eqs. dynmat, dynmat_reciprocal, eigenvalue_crystal), Sec. "Group
+ * Velocities" (Eq. groupvel), Sec. "Phonon Populations and Heat Capacity" (Eqs. bose,
+ * heatcap), Sec. "Three-Phonon Scattering" (Eqs. gamma, phi3_proj, broadening,
+ * lifetime), Sec. "Computational Implementation" (min_frequency selection) and Sec.
+ * "Boltzmann Transport Equation" (Eq. rta).
+ *
+ * Units: Angstrom, eV, amu, ps.  Frequencies f in THz (w = 2 pi f rad/ps); linewidths
+ * gamma = 1/tau in 1/ps; velocities in A/ps; conductivity in W/(m K).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a phx_status; PHX_OK is 0.  Nothing is thrown across the ABI.
+ *    After an error, phx_last_error(ctx) returns a message (owned by ctx, valid until the
+ *    next call on ctx).
+ *  - Array arguments marked [mem] live in host memory when mem == PHX_MEM_HOST and in
+ *    device memory of the context's device when mem == PHX_MEM_DEVICE.  The caller owns
+ *    all of them; the library never keeps a pointer past the call.  With host memory the
+ *    call copies in and out and returns after the results are in host memory; with
+ *    device memory it enqueues on `stream` (a cudaStream_t, NULL = legacy default) and
+ *    returns without synchronising.
+ *  - Descriptor structs (phx_cell, phx_ifc2, phx_ifc3) always point to host memory.
+ *  - Complex arrays are interleaved (re, im) doubles, i.e. the C99 double _Complex layout.
+ *  - Eigenvectors: evec[q][i][nu] is component i (= 3*atom + alpha) of mode nu, columns
+ *    orthonormal, modes sorted by ascending frequency, gauge: the largest-modulus
+ *    component of each column is real and positive (first index on ties).
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef PHX_H
+#define PHX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PHX_OK = 0,
+    PHX_ERR_INVALID = 1,      /* bad argument (null pointer, size, index out of range, NaN) */
+    PHX_ERR_CUDA = 2,         /* CUDA runtime error (message says which)                    */
+    PHX_ERR_NOMEM = 3,        /* device allocation failed                                   */
+    PHX_ERR_TIMEOUT = 4,      /* a bounded device wait gave up (status word set by a kernel) */
+    PHX_ERR_UNSUPPORTED = 5,  /* size or option this build does not handle                  */
+    PHX_ERR_NUMERIC = 6       /* eigensolver did not converge, or non-finite results         */
+} phx_status;
+
+typedef enum { PHX_MEM_HOST = 0, PHX_MEM_DEVICE = 1 } phx_mem;
+typedef enum { PHX_GAUSS = 0, PHX_LORENTZ = 1 } phx_shape;
+typedef enum { PHX_FP64 = 0, PHX_TF32 = 1, PHX_BF16X3 = 2 } phx_precision;
+
+typedef struct phx_ctx phx_ctx;
+typedef struct phx_fc3 phx_fc3;
+
+/* Unit cell: lattice rows a1, a2, a3 (A), n_atoms masses (amu).  Positions are not needed
+ * by any computation (IFCs carry the geometry) and may be NULL. */
+typedef struct {
+    double lattice[9];
+    int32_t n_atoms;
+    const double* masses;
+    const double* positions;
+} phx_cell;
+
+/* Second-order IFCs: n_blocks 3x3 blocks Phi2(0 i alpha, R j beta) (eV/A^2).
+ * idx[5*b .. 5*b+4] = (i, j, R1, R2, R3) with R in lattice-vector units; val[9*b + 3*alpha + beta]. */
+typedef struct {
+    int32_t n_blocks;
+    const int32_t* idx;
+    const double* val;
+} phx_ifc2;
+
+/* Third-order IFCs, COO, home atom in cell 0 (eV/A^3):
+ * idx[9*k .. 9*k+8] = (3a+alpha, 3b+beta, 3c+gamma, R'1, R'2, R'3, R''1, R''2, R''3),
+ * val[k] = Phi3(0 a alpha, R' b beta, R'' c gamma). */
+typedef struct {
+    int64_t nnz;
+    const int32_t* idx;
+    const double* val;
+} phx_ifc3;
+
+/* Energy-conservation smearing, Eq. (broadening): Gaussian exp(-x^2/s^2)/(sqrt(pi) s) or
+ * Lorentzian (s/2)/(pi (x^2 + s^2/4)) in THz; terms with |x| >= window*s are dropped
+ * (window 2 in the paper; any value > 0 accepted). */
+typedef struct {
+    int32_t shape;        /* phx_shape */
+    double sigma_thz;
+    double window;
+} phx_broadening;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` (also made current on the calling thread). */
+phx_status phx_create(phx_ctx** out, int device);
+void phx_destroy(phx_ctx* ctx);
+const char* phx_last_error(const phx_ctx* ctx);
+/* Library version string, e.g. "phx 1.0 sm_103a". */
+const char* phx_version(void);
+
+/* ---------------------------------------------------------------- grid (host only)
+ * Irreducible set of a Gamma-centred mesh n1 x n2 x n3 (flat index (k1*n2+k2)*n3+k3)
+ * under n_rot integer rotations (rot[9*r + 3*row + col], acting on reduced q) plus time
+ * reversal q -> -q (always applied): Sec. "Overview of New Capabilities" (scattering on
+ * the irreducible wedge, results mapped back to the full grid).  Representatives are the
+ * smallest index of each orbit, listed in ascending order.
+ * Outputs (host, caller-allocated, nq = n1 n2 n3 entries each): irr[0..*n_irr), full_to_irr[nq]
+ * (position in irr of each point's orbit), weight[0..*n_irr) (orbit sizes).
+ * Errors: PHX_ERR_INVALID if a rotation does not map the mesh onto itself. */
+phx_status phx_irreducible(const int32_t mesh[3], int32_t n_rot, const int32_t* rot,
+                           int32_t* irr, int32_t* n_irr, int32_t* full_to_irr, int32_t* weight);
+
+/* ---------------------------------------------------------------- harmonic
+ * Eqs. (dynmat_reciprocal), (eigenvalue_crystal), (groupvel): for nq reduced q-points
+ * q_frac[3*k..3*k+2] build D(q) = sum_R Phi2 exp(-2 pi i q.R)/sqrt(m m), diagonalise it in
+ * FP64 (batched Jacobi on the GPU) and return
+ *   freq_thz[nq][n]     signed frequency sign(lambda) sqrt(|lambda|)/(2 pi)          [mem]
+ *   evec[nq][n][n]      complex eigenvectors (layout and gauge above)                [mem]
+ *   vel[nq][n][3]       Re<e|dD/dq|e>/(2w) with the analytic derivative (0 if f<=0)   [mem, may be NULL]
+ *   vv[nq][n][9]        basis-invariant v(x)v: within each degenerate set S
+ *                       (|df| < 1e-5 max|f|) every mode gets
+ *                       (1/|S|) sum_{m,m' in S} Re(V^a_{mm'} V^b_{m'm})/(4 w^2)         [mem, may be NULL]
+ * n = 3 * cell->n_atoms, 3 <= n <= 192.
+ * Errors: PHX_ERR_INVALID (block index out of range), PHX_ERR_NUMERIC (no convergence). */
+phx_status phx_harmonic(phx_ctx* ctx, const phx_cell* cell, const phx_ifc2* fc2,
+                        const double* q_frac, int32_t nq,
+                        double* freq_thz, double* evec, double* vel, double* vv,
+                        int32_t mem, void* stream);
+
+/* ---------------------------------------------------------------- scattering
+ * Prepare the third-order IFCs for a mesh (host-side sort of the COO by lattice difference
+ * d = R' - R'' folded into the mesh, upload).  The handle is immutable and may be used by
+ * any number of phx_gamma calls on the same context.  Errors: PHX_ERR_INVALID for an
+ * out-of-range component index. */
+phx_status phx_fc3_create(phx_ctx* ctx, const phx_cell* cell, const phx_ifc3* fc3,
+                          const int32_t mesh[3], phx_fc3** out);
+void phx_fc3_destroy(phx_fc3* h);
+int32_t phx_fc3_num_d(const phx_fc3* h);  /* number of distinct folded lattice differences */
+
+/* Eqs. (gamma), (phi3_proj), (broadening), (lifetime) for every band of the n_irr mesh
+ * points irr_q (flat mesh indices):
+ *   gamma_lambda = pi hbar/(8 N_q) sum_{q' nu' nu''} |Phi(lambda, q'nu', q''nu'')|^2 / (w w' w'')
+ *                  * [(1+n'+n'') delta(w-w'-w'') + 2 (n'-n'') delta(w+w'-w'')],   q'' = -(q+q')
+ * with delta(w) = g(f)/(2 pi), modes with f < f_min_thz given gamma 0 and partners with
+ * f' or f'' < f_min_thz skipped (decay/absorption counting as read in the library notes).
+ * Inputs: freq_thz[N_q][n], evec[N_q][n][n] over the full mesh [mem]; irr_q[n_irr] [mem].
+ * Outputs: gamma[n_irr][n] (1/ps) [mem]; wp2[n_irr][n] (ps^4, may be NULL): the same sum
+ * with |Phi|^2 -> 1 and without pi hbar/8 (weighted two-phonon phase space).
+ * prec: PHX_FP64 (all FP64, CUDA cores), PHX_TF32 or PHX_BF16X3 (V3 contraction on the
+ * tcgen05 tensor cores with FP32 accumulation; weights and sums in FP32/FP64).
+ * Errors: PHX_ERR_INVALID (index out of range, T <= 0, sigma <= 0), PHX_ERR_UNSUPPORTED
+ * (n or mesh beyond the precision's limits). */
+phx_status phx_gamma(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz,
+                     const double* evec, const int32_t* irr_q, int32_t n_irr,
+                     double temperature, phx_broadening br, double f_min_thz,
+                     int32_t prec, double* gamma, double* wp2, int32_t mem, void* stream);
+
+/* ---------------------------------------------------------------- transport
+ * Map irreducible linewidths to the full mesh: gamma_full[k][nu] = gamma_irr[full_to_irr[k]][nu]
+ * after averaging gamma_irr over each degenerate set (|df| < 1e-5 max|f|) of its own q
+ * point (freq_irr[n_irr][n]).  [mem] for all arrays. */
+phx_status phx_unfold(phx_ctx* ctx, int32_t n_irr, int32_t nq, int32_t n,
+                      const double* freq_irr, const double* gamma_irr,
+                      const int32_t* full_to_irr, double* gamma_full, int32_t mem, void* stream);
+
+/* Eq. (rta): kappa_ab = 1/(N_q V) sum_{q nu: f >= f_min, gamma > 0} c v_a v_b / gamma, with
+ * c from Eq. (heatcap) (is_classic: k_B).  Velocity products from vv[nq][n][9] if vv is
+ * not NULL, else from vel[nq][n][3].  kappa_wmk[9] is always host memory; the call
+ * synchronises `stream`.  [mem] for freq, vel/vv, gamma_full. */
+phx_status phx_kappa_rta(phx_ctx* ctx, const phx_cell* cell, int32_t nq, int32_t n,
+                         const double* freq_thz, const double* vel, const double* vv,
+                         const double* gamma_full, double temperature, double f_min_thz,
+                         int32_t is_classic, double* kappa_wmk, int32_t mem, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHX_H */

@@ -1,0 +1,277 @@
+"""ctypes binding of libphx.so: argument marshalling only.
+
+Every computation happens inside the CUDA library.  Arrays may be NumPy arrays (host
+memory) or CUDA torch tensors (device memory, enqueued on the current torch stream); all
+array arguments of one call must live on the same side.  If the compiled library is
+missing this module raises at import time: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libphx.so")
+
+PHX_MEM_HOST, PHX_MEM_DEVICE = 0, 1
+PHX_GAUSS, PHX_LORENTZ = 0, 1
+PHX_FP64, PHX_TF32, PHX_BF16X3 = 0, 1, 2
+STATUS = {0: "PHX_OK", 1: "PHX_ERR_INVALID", 2: "PHX_ERR_CUDA", 3: "PHX_ERR_NOMEM", 4: "PHX_ERR_TIMEOUT",
+          5: "PHX_ERR_UNSUPPORTED", 6: "PHX_ERR_NUMERIC"}
+PRECISIONS = {"fp64": PHX_FP64, "tf32": PHX_TF32, "bf16x3": PHX_BF16X3}
+SHAPES = {"gauss": PHX_GAUSS, "lorentz": PHX_LORENTZ}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libphx.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+                      "or python -m paper_2602_23728_gb300.build")
+lib = C.CDLL(LIB_PATH)
+
+
+class Cell(C.Structure):
+    _fields_ = [("lattice", C.c_double * 9), ("n_atoms", C.c_int32), ("masses", C.c_void_p),
+                ("positions", C.c_void_p)]
+
+
+class Ifc2(C.Structure):
+    _fields_ = [("n_blocks", C.c_int32), ("idx", C.c_void_p), ("val", C.c_void_p)]
+
+
+class Ifc3(C.Structure):
+    _fields_ = [("nnz", C.c_int64), ("idx", C.c_void_p), ("val", C.c_void_p)]
+
+
+class Broadening(C.Structure):
+    _fields_ = [("shape", C.c_int32), ("sigma_thz", C.c_double), ("window", C.c_double)]
+
+
+_P = C.c_void_p
+_I = C.c_int32
+lib.phx_create.argtypes = [C.POINTER(_P), C.c_int]
+lib.phx_create.restype = C.c_int
+lib.phx_destroy.argtypes = [_P]
+lib.phx_destroy.restype = None
+lib.phx_last_error.argtypes = [_P]
+lib.phx_last_error.restype = C.c_char_p
+lib.phx_version.argtypes = []
+lib.phx_version.restype = C.c_char_p
+lib.phx_irreducible.argtypes = [_P, _I, _P, _P, _P, _P, _P]
+lib.phx_irreducible.restype = C.c_int
+lib.phx_harmonic.argtypes = [_P, C.POINTER(Cell), C.POINTER(Ifc2), _P, _I, _P, _P, _P, _P, _I, _P]
+lib.phx_harmonic.restype = C.c_int
+lib.phx_fc3_create.argtypes = [_P, C.POINTER(Cell), C.POINTER(Ifc3), _P, C.POINTER(_P)]
+lib.phx_fc3_create.restype = C.c_int
+lib.phx_fc3_destroy.argtypes = [_P]
+lib.phx_fc3_destroy.restype = None
+lib.phx_fc3_num_d.argtypes = [_P]
+lib.phx_fc3_num_d.restype = C.c_int32
+lib.phx_gamma.argtypes = [_P, _P, _P, _P, _P, _I, C.c_double, Broadening, C.c_double, _I, _P, _P, _I, _P]
+lib.phx_gamma.restype = C.c_int
+lib.phx_unfold.argtypes = [_P, _I, _I, _I, _P, _P, _P, _P, _I, _P]
+lib.phx_unfold.restype = C.c_int
+lib.phx_kappa_rta.argtypes = [_P, C.POINTER(Cell), _I, _I, _P, _P, _P, _P, C.c_double, C.c_double, _I, _P, _I, _P]
+lib.phx_kappa_rta.restype = C.c_int
+
+EXPORTED = ["phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
+            "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_unfold", "phx_kappa_rta"]
+
+
+class PhxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _host(x, dtype):
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a
+
+
+def _mem_and_stream(arrays):
+    dev = [a for a in arrays if a is not None and _is_torch(a)]
+    if not dev:
+        return PHX_MEM_HOST, None
+    if len(dev) != len([a for a in arrays if a is not None]):
+        raise ValueError("mix of host (numpy) and device (torch) arrays in one call")
+    import torch
+    for a in dev:
+        if not a.is_cuda or not a.is_contiguous():
+            raise ValueError("device arrays must be contiguous CUDA tensors")
+    return PHX_MEM_DEVICE, torch.cuda.current_stream(dev[0].device).cuda_stream
+
+
+def make_cell(lattice, masses):
+    m = _host(masses, np.float64)
+    c = Cell()
+    for k, v in enumerate(np.asarray(lattice, dtype=np.float64).ravel()):
+        c.lattice[k] = v
+    c.n_atoms = m.shape[0]
+    c.masses = m.ctypes.data
+    c.positions = None
+    return c, m
+
+
+def irreducible(mesh, rotations):
+    """Irreducible set (host): returns irr, full_to_irr, weights as int32 arrays."""
+    mesh_a = np.asarray(mesh, dtype=np.int32)
+    rot = np.ascontiguousarray(rotations, dtype=np.int32).reshape(-1, 9)
+    nq = int(np.prod(mesh_a))
+    irr = np.zeros(nq, np.int32)
+    f2i = np.zeros(nq, np.int32)
+    wt = np.zeros(nq, np.int32)
+    n_irr = C.c_int32(0)
+    st = lib.phx_irreducible(mesh_a.ctypes.data, rot.shape[0], rot.ctypes.data, irr.ctypes.data,
+                             C.addressof(n_irr), f2i.ctypes.data, wt.ctypes.data)
+    if st != 0:
+        raise PhxError(st, "phx_irreducible failed (rotation does not map the mesh onto itself?)")
+    k = n_irr.value
+    return irr[:k].copy(), f2i, wt[:k].copy()
+
+
+class FC3:
+    """Handle of prepared third-order IFCs (phx_fc3)."""
+
+    def __init__(self, ctx, lattice, masses, idx, val, mesh):
+        self.ctx = ctx
+        self._idx = _host(idx, np.int32)
+        self._val = _host(val, np.float64)
+        cell, self._m = make_cell(lattice, masses)
+        f = Ifc3(self._val.shape[0], self._idx.ctypes.data, self._val.ctypes.data)
+        self._mesh = np.asarray(mesh, dtype=np.int32)
+        h = _P()
+        ctx._check(lib.phx_fc3_create(ctx.h, C.byref(cell), C.byref(f), self._mesh.ctypes.data, C.byref(h)))
+        self.h = h
+        self.n = 3 * self._m.shape[0]
+        self.mesh = tuple(int(x) for x in mesh)
+        self.nq = int(np.prod(self._mesh))
+
+    @property
+    def num_d(self):
+        return lib.phx_fc3_num_d(self.h)
+
+    def close(self):
+        if self.h:
+            lib.phx_fc3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """One phx context on a CUDA device."""
+
+    def __init__(self, device=0):
+        h = _P()
+        st = lib.phx_create(C.byref(h), int(device))
+        if st != 0:
+            raise PhxError(st, "phx_create failed (no CUDA device?)")
+        self.h = h
+        self.device = device
+
+    def _check(self, st):
+        if st != 0:
+            raise PhxError(st, lib.phx_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            lib.phx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ harmonic
+    def harmonic(self, lattice, masses, ifc2_idx, ifc2_val, q_frac, freq=None, evec=None, vel=None, vv=None,
+                 want_vel=True, want_vv=True):
+        """phx_harmonic.  With numpy q_frac, outputs are allocated as numpy arrays; with a CUDA
+        tensor q_frac the caller passes CUDA tensors for the outputs."""
+        cell, m = make_cell(lattice, masses)
+        bi = _host(ifc2_idx, np.int32)
+        bv = _host(ifc2_val, np.float64)
+        f2 = Ifc2(bi.shape[0], bi.ctypes.data, bv.ctypes.data)
+        n = 3 * m.shape[0]
+        if not _is_torch(q_frac):
+            q_frac = _host(q_frac, np.float64).reshape(-1, 3)
+            nq = q_frac.shape[0]
+            freq = np.zeros((nq, n)) if freq is None else freq
+            evec = np.zeros((nq, n, n), np.complex128) if evec is None else evec
+            if want_vel and vel is None:
+                vel = np.zeros((nq, n, 3))
+            if want_vv and vv is None:
+                vv = np.zeros((nq, n, 3, 3))
+        nq = q_frac.shape[0]
+        mem, stream = _mem_and_stream([q_frac, freq, evec, vel, vv])
+        self._check(lib.phx_harmonic(self.h, C.byref(cell), C.byref(f2), _ptr(q_frac), nq, _ptr(freq), _ptr(evec),
+                                     _ptr(vel), _ptr(vv), mem, stream))
+        return freq, evec, vel, vv
+
+    # ------------------------------------------------------------------ scattering
+    def fc3(self, lattice, masses, idx, val, mesh):
+        return FC3(self, lattice, masses, idx, val, mesh)
+
+    def gamma(self, fc3, freq, evec, irr_q, temperature, shape="gauss", sigma=0.1, window=2.0, f_min=0.01,
+              precision="fp64", gamma=None, wp2=None, want_wp2=False):
+        br = Broadening(SHAPES[shape], float(sigma), float(window))
+        if not _is_torch(freq):
+            freq = _host(freq, np.float64)
+            evec = _host(evec, np.complex128)
+            irr_q = _host(irr_q, np.int32)
+            gamma = np.zeros((irr_q.shape[0], fc3.n)) if gamma is None else gamma
+            if want_wp2 and wp2 is None:
+                wp2 = np.zeros((irr_q.shape[0], fc3.n))
+        mem, stream = _mem_and_stream([freq, evec, irr_q, gamma, wp2])
+        self._check(lib.phx_gamma(self.h, fc3.h, _ptr(freq), _ptr(evec), _ptr(irr_q), int(irr_q.shape[0]),
+                                  float(temperature), br, float(f_min), PRECISIONS[precision], _ptr(gamma),
+                                  _ptr(wp2), mem, stream))
+        return (gamma, wp2) if want_wp2 or wp2 is not None else gamma
+
+    # ------------------------------------------------------------------ transport
+    def unfold(self, freq_irr, gamma_irr, full_to_irr, out=None):
+        if not _is_torch(freq_irr):
+            freq_irr = _host(freq_irr, np.float64)
+            gamma_irr = _host(gamma_irr, np.float64)
+            full_to_irr = _host(full_to_irr, np.int32)
+            out = np.zeros((full_to_irr.shape[0], freq_irr.shape[1])) if out is None else out
+        mem, stream = _mem_and_stream([freq_irr, gamma_irr, full_to_irr, out])
+        self._check(lib.phx_unfold(self.h, freq_irr.shape[0], full_to_irr.shape[0], freq_irr.shape[1],
+                                   _ptr(freq_irr), _ptr(gamma_irr), _ptr(full_to_irr), _ptr(out), mem, stream))
+        return out
+
+    def kappa_rta(self, lattice, masses, freq, gamma_full, temperature, vel=None, vv=None, f_min=0.01,
+                  is_classic=False):
+        cell, m = make_cell(lattice, masses)
+        if not _is_torch(freq):
+            freq = _host(freq, np.float64)
+            gamma_full = _host(gamma_full, np.float64)
+            vel = None if vel is None else _host(vel, np.float64)
+            vv = None if vv is None else _host(vv, np.float64)
+        mem, stream = _mem_and_stream([freq, gamma_full, vel, vv])
+        k = np.zeros(9)
+        self._check(lib.phx_kappa_rta(self.h, C.byref(cell), freq.shape[0], freq.shape[1], _ptr(freq), _ptr(vel),
+                                      _ptr(vv), _ptr(gamma_full), float(temperature), float(f_min), int(is_classic),
+                                      k.ctypes.data, mem, stream))
+        return k.reshape(3, 3)
+
+
+def version():
+    return lib.phx_version().decode()

@@ -1,0 +1,152 @@
+// Internal declarations shared by the translation units of libphx (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/phx.h"
+
+// Physical constants (CODATA 2018) and unit conversions used by the library.
+namespace phx {
+constexpr double kHbarEvPs = 6.582119569e-4;    // eV ps
+constexpr double kKbEvK = 8.617333262e-5;       // eV / K
+constexpr double kEvJ = 1.602176634e-19;        // J / eV
+constexpr double kAmuKg = 1.66053906660e-27;    // kg / amu
+// eV/(A^2 amu) -> ps^-2 and eV/(ps A K) -> W/(m K)
+constexpr double kEvA2AmuToPs2 = kEvJ / (1e-20 * kAmuKg) * 1e-24;
+constexpr double kEvPsAKToWmK = kEvJ / 1e-12 / 1e-10;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kPi = 3.1415926535897932384626433832795;
+constexpr double kDegenerateRelTol = 1e-5;
+}  // namespace phx
+
+// Device-memory workspace owned by a context: grow-only named buffers.
+struct phx_ctx {
+    int device = 0;
+    std::string err;
+    std::map<std::string, std::pair<void*, size_t>> ws;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    size_t smem_optin = 0;
+    void* status_word = nullptr;     // device int32 written by kernels with bounded waits
+};
+
+struct phx_fc3 {
+    phx_ctx* ctx = nullptr;
+    int n = 0;                  // modes per q (3 * n_atoms)
+    int mesh[3] = {1, 1, 1};
+    int nq = 1;
+    int n_d = 0;                // distinct folded lattice differences
+    int64_t nnz = 0;
+    int64_t n_seg = 0;          // distinct (d, b, c) keys
+    // device arrays
+    int32_t* d_int = nullptr;       // [n_d][3] folded d in mesh units (0..n_i-1)
+    int32_t* seg_key = nullptr;     // [n_seg][3] (d index, b, c)
+    int64_t* seg_start = nullptr;   // [n_seg + 1]
+    int32_t* ent_a = nullptr;       // [nnz] component index a of each entry (sorted)
+    int32_t* ent_r2 = nullptr;      // [nnz][3] R'' of each entry
+    double* ent_w = nullptr;        // [nnz] Phi3 / sqrt(m_a m_b m_c)
+};
+
+// ---------------------------------------------------------------- host helpers
+
+phx_status phx_set_error(phx_ctx* ctx, phx_status st, const char* fmt, ...);
+void* phx_ws(phx_ctx* ctx, const char* name, size_t bytes);   // nullptr on failure (error set)
+
+#define PHX_CUDA_CHECK(ctx, expr)                                                        \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return phx_set_error((ctx), PHX_ERR_CUDA, "%s failed: %s (%s:%d)", #expr,    \
+                                 cudaGetErrorString(e_), __FILE__, __LINE__);            \
+    } while (0)
+
+#define PHX_TRY(expr)                 \
+    do {                              \
+        phx_status s_ = (expr);       \
+        if (s_ != PHX_OK) return s_;  \
+    } while (0)
+
+// Input staging: returns a device pointer holding `count` elements of `host_or_dev`.
+// For PHX_MEM_HOST the data are copied into workspace buffer `name` on `stream`.
+template <typename T>
+static inline phx_status phx_stage_in(phx_ctx* ctx, const char* name, const T* p, size_t count,
+                                      int mem, cudaStream_t stream, const T** out) {
+    if (mem == PHX_MEM_DEVICE || count == 0) {
+        *out = p;
+        return PHX_OK;
+    }
+    T* d = (T*)phx_ws(ctx, name, count * sizeof(T));
+    if (!d) return PHX_ERR_NOMEM;
+    PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(d, p, count * sizeof(T), cudaMemcpyHostToDevice, stream));
+    *out = d;
+    return PHX_OK;
+}
+
+template <typename T>
+static inline phx_status phx_stage_out_buf(phx_ctx* ctx, const char* name, T* p, size_t count,
+                                           int mem, T** out) {
+    if (mem == PHX_MEM_DEVICE || count == 0) {
+        *out = p;
+        return PHX_OK;
+    }
+    T* d = (T*)phx_ws(ctx, name, count * sizeof(T));
+    if (!d) return PHX_ERR_NOMEM;
+    *out = d;
+    return PHX_OK;
+}
+
+// ---------------------------------------------------------------- kernels (launchers)
+// Each launcher enqueues on `stream` and returns the launch error.
+
+// harmonic.cu
+cudaError_t phx_launch_dynmat(const double* q_frac, int nq, int n_atoms, const int32_t* blk_idx,
+                              const double* blk_val, const int32_t* pair_start, const double* masses,
+                              const double* lattice, double* D, double* dD, cudaStream_t s);
+cudaError_t phx_launch_jacobi(double* A, double* V, int n, int nq, double* freq, double* evec,
+                              int32_t* status, cudaStream_t s);
+cudaError_t phx_launch_velocity(const double* evec, const double* Y, const double* freq, int n,
+                                int nq, double* vel, double* vv, cudaStream_t s);
+
+// zgemm.cu: batched complex FP64 GEMM, row-major; see the kernel for the batch addressing.
+struct ZgemmBatch {
+    // C_b[M x N] = opA(A_b)[M x K] * B_b[K x N]
+    const double* A;    // complex
+    const double* B;
+    double* C;
+    int64_t strideA, strideB, strideC;   // complex elements per batch step (when no index map)
+    const int32_t* idxA;                 // optional: A_b = A + idxA[b / divA] * strideA
+    const int32_t* idxB;                 // optional: B_b = B + idxB[b / divB] * strideB
+    int divA, divB;                      // batch divisors for the index maps (>= 1)
+    int64_t strideB_inner;               // added per (b % divB) when idxB given
+    int lda, ldb, ldc;
+    int transA;                          // 1: A stored [K][M] (plain transpose, no conjugate)
+};
+cudaError_t phx_launch_zgemm(int M, int N, int K, int batch, const ZgemmBatch& p, cudaStream_t s);
+
+// transport.cu
+cudaError_t phx_launch_occupations(const double* freq, int count, double T, int is_classic,
+                                   double* nB, double* cV, cudaStream_t s);
+cudaError_t phx_launch_unfold(int n_irr, int nq, int n, const double* freq_irr,
+                              const double* gamma_irr, const int32_t* full_to_irr,
+                              double* gamma_full, cudaStream_t s);
+cudaError_t phx_launch_kappa(int nq, int n, const double* freq, const double* vel,
+                             const double* vv, const double* gamma_full, double T, double f_min,
+                             int is_classic, double* acc9, cudaStream_t s);
+
+// gamma path shared parameters
+struct GammaParams {
+    int n;                 // modes
+    int mesh[3];
+    int nq;
+    double T;
+    int shape;
+    double sigma;
+    double window;
+    double f_min;
+};

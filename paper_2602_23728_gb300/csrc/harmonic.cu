@@ -1,0 +1,342 @@
+// Harmonic phonons on the GPU in FP64 (paper Sec. "Interatomic Force Constants", Eqs.
+// (dynmat), (dynmat_reciprocal), (eigenvalue_crystal); Sec. "Group Velocities", Eq. (groupvel)).
+//
+//  dynmat_kernel    D(q) = sum_R Phi2(0i, Rj) exp(-2 pi i q.R) / sqrt(m_i m_j) and the analytic
+//                   dD/dq_a = sum_R (-i R_a) (...) for a batch of q (one CTA per q)
+//  jacobi_kernel    batched complex-Hermitian cyclic Jacobi eigensolver, one CTA per matrix,
+//                   round-robin ordering (n/2 disjoint rotations per step applied as one
+//                   left and one right multiplication); matrix in shared memory when it fits
+//  velocity_kernel  v_a = Re<e|dD/dq_a|e>/(2w) and the basis-invariant v(x)v per degenerate set
+#include "common.h"
+
+namespace {
+
+constexpr int kJacobiThreads = 256;
+constexpr int kMaxModes = 192;
+constexpr int kMaxPairs = kMaxModes / 2;
+constexpr int kMaxSweeps = 40;
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// One CTA per q.  pair_start is a CSR over (i, j) atom pairs (n_atoms^2 + 1 entries) into
+// blocks sorted by (i, j).
+__global__ void dynmat_kernel(const double* __restrict__ q_frac, int n_atoms,
+                              const int32_t* __restrict__ blk_idx, const double* __restrict__ blk_val,
+                              const int32_t* __restrict__ pair_start, const double* __restrict__ masses,
+                              const double* __restrict__ lattice, double2* __restrict__ D,
+                              double2* __restrict__ dD) {
+    const int q = blockIdx.x;
+    const int n = 3 * n_atoms;
+    const int64_t nn = (int64_t)n * n;
+    const double q0 = q_frac[3 * q], q1 = q_frac[3 * q + 1], q2 = q_frac[3 * q + 2];
+    for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int row = (int)(e / n), col = (int)(e % n);
+        const int i = row / 3, al = row % 3, j = col / 3, be = col % 3;
+        const int p = i * n_atoms + j;
+        double2 acc = make_double2(0.0, 0.0);
+        double2 dacc[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+        for (int b = pair_start[p]; b < pair_start[p + 1]; ++b) {
+            const int r1 = blk_idx[5 * b + 2], r2 = blk_idx[5 * b + 3], r3 = blk_idx[5 * b + 4];
+            const double x = 2.0 * (q0 * r1 + q1 * r2 + q2 * r3);
+            double s, c;
+            sincospi(x, &s, &c);                 // exp(-i pi x) = c - i s
+            const double v = blk_val[9 * b + 3 * al + be];
+            acc.x += v * c;
+            acc.y -= v * s;
+            if (dD) {
+                for (int a = 0; a < 3; ++a) {
+                    const double Ra = r1 * lattice[a] + r2 * lattice[3 + a] + r3 * lattice[6 + a];
+                    // (-i Ra) (c - i s) v = v Ra (-s - i c)
+                    dacc[a].x += -v * Ra * s;
+                    dacc[a].y += -v * Ra * c;
+                }
+            }
+        }
+        const double sc = 1.0 / sqrt(masses[i] * masses[j]);
+        D[(int64_t)q * nn + e] = make_double2(acc.x * sc, acc.y * sc);
+        if (dD) {
+            for (int a = 0; a < 3; ++a)
+                dD[((int64_t)q * 3 + a) * nn + e] = make_double2(dacc[a].x * sc, dacc[a].y * sc);
+        }
+    }
+}
+
+__device__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) red[0] = t;
+    }
+    __syncthreads();
+    t = red[0];
+    __syncthreads();
+    return t;
+}
+
+// Position of player x in round r of a round-robin tournament over m (even) players:
+// player 0 stays, the others rotate.
+__device__ __forceinline__ int rr_player(int x, int r, int m) {
+    return x == 0 ? 0 : 1 + ((x - 1 + r) % (m - 1));
+}
+
+template <bool kSmem>
+__global__ void __launch_bounds__(kJacobiThreads)
+jacobi_kernel(double2* __restrict__ Ag, double2* __restrict__ Vg, int n, double* __restrict__ freq,
+              double2* __restrict__ evec, int32_t* __restrict__ status) {
+    extern __shared__ double2 shA[];
+    __shared__ double rc[kMaxPairs], rs[kMaxPairs], rpc[kMaxPairs], rps[kMaxPairs];
+    __shared__ int rp[kMaxPairs], rq[kMaxPairs], ract[kMaxPairs];
+    __shared__ double red[32];
+    __shared__ double lam[kMaxModes];
+    __shared__ int rank_of[kMaxModes];
+
+    const int qi = blockIdx.x;
+    const int64_t nn = (int64_t)n * n;
+    double2* A = kSmem ? shA : Ag + (int64_t)qi * nn;
+    double2* V = Vg + (int64_t)qi * nn;
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    // Hermitian part (D + D^H)/2: the two triangles of D(q) are summed from different blocks
+    // and differ at the rounding level, which would otherwise keep the off-norm from vanishing
+    // (at Gamma D is pure rounding noise).
+    {
+        const double2* Dq = Ag + (int64_t)qi * nn;
+        for (int64_t e = tid; e < nn; e += nt) {
+            const int i = (int)(e / n), j = (int)(e % n);
+            if (i > j) continue;
+            const double2 a = Dq[(int64_t)i * n + j], b = Dq[(int64_t)j * n + i];
+            const double2 h = make_double2(0.5 * (a.x + b.x), i == j ? 0.0 : 0.5 * (a.y - b.y));
+            A[(int64_t)i * n + j] = h;
+            A[(int64_t)j * n + i] = make_double2(h.x, -h.y);
+        }
+    }
+    for (int64_t e = tid; e < nn; e += nt) V[e] = make_double2((e / n == e % n) ? 1.0 : 0.0, 0.0);
+    __syncthreads();
+
+    const int m = n + (n & 1);
+    const int np = m / 2;
+    int converged = 0, extra = 0;
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int64_t e = tid; e < nn; e += nt) {
+            const double2 a = A[e];
+            const double v = a.x * a.x + a.y * a.y;
+            tot += v;
+            if (e / n != e % n) off += v;
+        }
+        off = block_sum(off, red);
+        tot = block_sum(tot, red);
+        if (off <= 1e-26 * tot || tot == 0.0) {
+            if (extra) { converged = 1; break; }
+            extra = 1;  // one more sweep past the threshold
+        }
+        for (int r = 0; r < m - 1; ++r) {
+            for (int k = tid; k < np; k += nt) {
+                int p = rr_player(k, r, m), q = rr_player(m - 1 - k, r, m);
+                if (p > q) { int t = p; p = q; q = t; }
+                int act = 0;
+                double c = 1.0, s = 0.0, pc = 1.0, ps = 0.0;
+                if (q < n) {
+                    const double2 apq = A[(int64_t)p * n + q];
+                    const double h = hypot(apq.x, apq.y);
+                    if (h > 1e-300) {
+                        const double app = A[(int64_t)p * n + p].x, aqq = A[(int64_t)q * n + q].x;
+                        const double th = (aqq - app) / (2.0 * h);
+                        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        s = t * c;
+                        pc = apq.x / h;   // exp(i phi)
+                        ps = apq.y / h;
+                        act = 1;
+                    }
+                }
+                rc[k] = c; rs[k] = s; rpc[k] = pc; rps[k] = ps; rp[k] = p; rq[k] = q; ract[k] = act;
+            }
+            __syncthreads();
+            // rows: A <- U^H A ; row p: c a_p - s e^{i phi} a_q ; row q: s a_p + c e^{i phi} a_q
+            for (int64_t t = tid; t < (int64_t)np * n; t += nt) {
+                const int k = (int)(t / n), j = (int)(t % n);
+                if (!ract[k]) continue;
+                const int p = rp[k], q = rq[k];
+                const double c = rc[k], s = rs[k];
+                const double2 ph = make_double2(rpc[k], rps[k]);
+                const double2 ap = A[(int64_t)p * n + j], aq = A[(int64_t)q * n + j];
+                const double2 eaq = cmul(ph, aq);
+                A[(int64_t)p * n + j] = make_double2(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
+                A[(int64_t)q * n + j] = make_double2(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
+            }
+            __syncthreads();
+            // columns: A <- A U, V <- V U ; col p: c a_p - s e^{-i phi} a_q ; col q: s a_p + c e^{-i phi} a_q
+            for (int64_t t = tid; t < (int64_t)np * n; t += nt) {
+                const int i = (int)(t / np), k = (int)(t % np);
+                if (!ract[k]) continue;
+                const int p = rp[k], q = rq[k];
+                const double c = rc[k], s = rs[k];
+                const double2 phc = make_double2(rpc[k], -rps[k]);
+                {
+                    const double2 ap = A[(int64_t)i * n + p], aq = A[(int64_t)i * n + q];
+                    const double2 eaq = cmul(phc, aq);
+                    A[(int64_t)i * n + p] = make_double2(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
+                    A[(int64_t)i * n + q] = make_double2(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
+                }
+                {
+                    const double2 vp = V[(int64_t)i * n + p], vq = V[(int64_t)i * n + q];
+                    const double2 evq = cmul(phc, vq);
+                    V[(int64_t)i * n + p] = make_double2(c * vp.x - s * evq.x, c * vp.y - s * evq.y);
+                    V[(int64_t)i * n + q] = make_double2(s * vp.x + c * evq.x, s * vp.y + c * evq.y);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (!converged && tid == 0) atomicExch(status, (int)PHX_ERR_NUMERIC);
+
+    for (int i = tid; i < n; i += nt) lam[i] = A[(int64_t)i * n + i].x;
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) {
+        int r = 0;
+        const double li = lam[i];
+        for (int j = 0; j < n; ++j) r += (lam[j] < li) || (lam[j] == li && j < i);
+        rank_of[i] = r;
+        const double w2 = li * phx::kEvA2AmuToPs2;
+        freq[(int64_t)qi * n + r] = (w2 >= 0.0 ? sqrt(w2) : -sqrt(-w2)) / phx::kTwoPi;
+    }
+    __syncthreads();
+    // gauge: largest-modulus component real positive (first index on ties); one warp per column
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    for (int col = warp; col < n; col += nw) {
+        double best = -1.0;
+        int bi = 0;
+        for (int i = lane; i < n; i += 32) {
+            const double2 v = V[(int64_t)i * n + col];
+            const double a = v.x * v.x + v.y * v.y;
+            if (a > best) { best = a; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        const double2 vm = V[(int64_t)bi * n + col];
+        const double h = hypot(vm.x, vm.y);
+        const double2 g = h > 0.0 ? make_double2(vm.x / h, -vm.y / h) : make_double2(1.0, 0.0);
+        const int dst = rank_of[col];
+        for (int i = lane; i < n; i += 32)
+            evec[(int64_t)qi * nn + (int64_t)i * n + dst] = cmul(V[(int64_t)i * n + col], g);
+    }
+}
+
+// One CTA per q.  Y[q][a] = dD_a(q) E(q) (complex), E sorted by frequency.
+__global__ void velocity_kernel(const double2* __restrict__ E, const double2* __restrict__ Y,
+                                const double* __restrict__ freq, int n, double* __restrict__ vel,
+                                double* __restrict__ vv) {
+    __shared__ int grp_lo[kMaxModes], grp_hi[kMaxModes];
+    const int q = blockIdx.x;
+    const int64_t nn = (int64_t)n * n;
+    const double* f = freq + (int64_t)q * n;
+    if (threadIdx.x == 0) {
+        double fm = 0.0;
+        for (int i = 0; i < n; ++i) fm = fmax(fm, fabs(f[i]));
+        const double tol = phx::kDegenerateRelTol * fmax(fm, 1e-30);
+        int i = 0;
+        while (i < n) {          // frequencies ascend: groups anchored at their first member
+            int j = i + 1;
+            while (j < n && f[j] - f[i] < tol) ++j;
+            for (int k = i; k < j; ++k) { grp_lo[k] = i; grp_hi[k] = j; }
+            i = j;
+        }
+    }
+    __syncthreads();
+    const double2* Eq = E + (int64_t)q * nn;
+    for (int mu = threadIdx.x; mu < n; mu += blockDim.x) {
+        const double w = f[mu] * phx::kTwoPi;
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < 3; ++a) {
+            const double2* Ya = Y + ((int64_t)q * 3 + a) * nn;
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double2 e = Eq[(int64_t)i * n + mu], y = Ya[(int64_t)i * n + mu];
+                acc += e.x * y.x + e.y * y.y;        // Re(conj(e) y)
+            }
+            v[a] = w > 0.0 ? acc * phx::kEvA2AmuToPs2 / (2.0 * w) : 0.0;
+        }
+        if (vel)
+            for (int a = 0; a < 3; ++a) vel[((int64_t)q * n + mu) * 3 + a] = v[a];
+        if (vv) {
+            double t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            const int lo = grp_lo[mu], hi = grp_hi[mu];
+            const double w0 = f[lo] * phx::kTwoPi;
+            if (w0 > 0.0) {
+                for (int m1 = lo; m1 < hi; ++m1)
+                    for (int m2 = lo; m2 < hi; ++m2) {
+                        double2 G12[3], G21[3];     // G^a_{m1 m2}, G^a_{m2 m1}
+                        for (int a = 0; a < 3; ++a) {
+                            const double2* Ya = Y + ((int64_t)q * 3 + a) * nn;
+                            double2 g12 = make_double2(0, 0), g21 = make_double2(0, 0);
+                            for (int i = 0; i < n; ++i) {
+                                const double2 e1 = Eq[(int64_t)i * n + m1], e2 = Eq[(int64_t)i * n + m2];
+                                const double2 y1 = Ya[(int64_t)i * n + m1], y2 = Ya[(int64_t)i * n + m2];
+                                g12.x += e1.x * y2.x + e1.y * y2.y; g12.y += e1.x * y2.y - e1.y * y2.x;
+                                g21.x += e2.x * y1.x + e2.y * y1.y; g21.y += e2.x * y1.y - e2.y * y1.x;
+                            }
+                            G12[a] = g12; G21[a] = g21;
+                        }
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = 0; b < 3; ++b)
+                                t[3 * a + b] += G12[a].x * G21[b].x - G12[a].y * G21[b].y;
+                    }
+                const double sc = phx::kEvA2AmuToPs2 * phx::kEvA2AmuToPs2 / (4.0 * w0 * w0 * (hi - lo));
+                for (int k = 0; k < 9; ++k) t[k] *= sc;
+            }
+            for (int k = 0; k < 9; ++k) vv[((int64_t)q * n + mu) * 9 + k] = t[k];
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t phx_launch_dynmat(const double* q_frac, int nq, int n_atoms, const int32_t* blk_idx,
+                              const double* blk_val, const int32_t* pair_start, const double* masses,
+                              const double* lattice, double* D, double* dD, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    dynmat_kernel<<<nq, 256, 0, s>>>(q_frac, n_atoms, blk_idx, blk_val, pair_start, masses, lattice,
+                                     (double2*)D, (double2*)dD);
+    return cudaGetLastError();
+}
+
+cudaError_t phx_launch_jacobi(double* A, double* V, int n, int nq, double* freq, double* evec,
+                              int32_t* status, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    if (n > kMaxModes) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)n * n * sizeof(double2);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t static_bytes = 8 * 1024;     // rotation tables etc. (upper bound)
+    if (smem + static_bytes <= (size_t)optin) {
+        cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        jacobi_kernel<true><<<nq, kJacobiThreads, smem, s>>>((double2*)A, (double2*)V, n, freq,
+                                                             (double2*)evec, status);
+    } else {
+        jacobi_kernel<false><<<nq, kJacobiThreads, 0, s>>>((double2*)A, (double2*)V, n, freq,
+                                                           (double2*)evec, status);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t phx_launch_velocity(const double* evec, const double* Y, const double* freq, int n,
+                                int nq, double* vel, double* vv, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    velocity_kernel<<<nq, 128, 0, s>>>((const double2*)evec, (const double2*)Y, freq, n, vel, vv);
+    return cudaGetLastError();
+}

@@ -1,0 +1,76 @@
+"""The C-ABI library: it builds, loads, exports every symbol the header declares, and its
+host-only logic (the irreducible q set) matches the oracle bit for bit.  No GPU needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import phx_inputs as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    syms = set()
+    for name in os.listdir(os.path.join(ROOT, "include")):
+        if name.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", name)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            syms |= set(re.findall(r"\b(phx_[a-z0-9_]+)\s*\(", text))
+    return syms
+
+
+@pytest.fixture(scope="module")
+def phx():
+    lib = os.path.join(ROOT, "paper_2602_23728_gb300", "libphx.so")
+    if not os.path.exists(lib):
+        import __graft_entry__
+        __graft_entry__.build()
+    import paper_2602_23728_gb300 as m
+    return m
+
+
+def test_library_exports_every_declared_symbol(phx):
+    lib = ctypes.CDLL(phx.LIB_PATH)
+    declared = _declared_symbols()
+    assert len(declared) >= 12
+    for s in sorted(declared):
+        assert hasattr(lib, s), f"{s} declared in include/ but not exported"
+    assert set(phx.EXPORTED) <= declared
+
+
+def test_version_string(phx):
+    assert "sm_103a" in phx.version()
+
+
+@pytest.mark.parametrize("mesh,which", [((5, 5, 5), "oh1"), ((8, 8, 8), "tr"), ((4, 6, 5), "tr"),
+                                        ((8, 8, 8), "oh4"), ((24, 24, 24), "oh4"), ((1, 1, 1), "tr")])
+def test_irreducible_matches_oracle(phx, mesh, which):
+    if which == "oh1":
+        rots = P.cubic_rotations_reduced(P.fcc_primitive().lattice)
+    elif which == "oh4":
+        rots = P.cubic_rotations_reduced(P.fcc_conventional().lattice)
+    else:
+        rots = P.identity_rotation()
+    irr, f2i, wt = phx.irreducible(mesh, rots)
+    oirr, of2i, owt = O.grid.irreducible(mesh, rots)
+    assert np.array_equal(irr, oirr)
+    assert np.array_equal(f2i, of2i)
+    assert np.array_equal(wt, owt)
+
+
+def test_irreducible_rejects_incompatible_rotation(phx):
+    rot = np.array([[[0, 1, 0], [1, 0, 0], [0, 0, 1]]], dtype=np.int32)   # swaps axes of a 4x6 mesh
+    with pytest.raises(phx.PhxError):
+        phx.irreducible((4, 6, 5), rot)
+
+
+def test_create_without_gpu_fails_loudly(phx):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(phx.PhxError):
+        phx.Context(0)

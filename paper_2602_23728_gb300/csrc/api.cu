@@ -403,8 +403,9 @@ phx_status phx_gamma(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz, c
     if (n_irr < 0) return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma: n_irr < 0");
     if (n_irr == 0) return PHX_OK;
     if (!freq_thz || !evec || !irr_q || !gamma) return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma: null argument");
-    if (!(temperature > 0.0) || !(br.sigma_thz > 0.0) || !(br.window > 0.0) || !std::isfinite(f_min_thz))
-        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma: T, sigma and window must be > 0");
+    if (!(temperature > 0.0) || !(br.sigma_thz > 0.0) || !(br.window > 0.0) || !(f_min_thz > 0.0) ||
+        !std::isfinite(f_min_thz) || !std::isfinite(temperature))
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma: T, sigma, window and f_min must be finite and > 0");
     if (br.shape != PHX_GAUSS && br.shape != PHX_LORENTZ)
         return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma: unknown broadening shape %d", br.shape);
     if (prec != PHX_FP64 && prec != PHX_TF32 && prec != PHX_BF16X3)

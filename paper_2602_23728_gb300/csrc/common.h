@@ -139,6 +139,8 @@ cudaError_t phx_launch_kappa(int nq, int n, const double* freq, const double* ve
                              const double* vv, const double* gamma_full, double T, double f_min,
                              int is_classic, double* acc9, cudaStream_t s);
 
+cudaError_t phx_launch_third_index(int iq, const int* mesh, int32_t* qpp, cudaStream_t s);
+
 // gamma path shared parameters
 struct GammaParams {
     int n;                 // modes

@@ -1,10 +1,708 @@
-// Tensor-core (tcgen05) linewidth path: placeholder until the kernels land.
-#include "common.h"
+// Three-phonon linewidths on the tcgen05 tensor cores (paper Sec. "Three-Phonon Scattering",
+// Eqs. (phi3_proj), (gamma), (broadening); Sec. "Computational Implementation": the
+// projection done as tensor products).  Same regrouping as the FP64 path:
+//
+//   S3  W_q[(nu,b,c)][d]        = sum phi/sqrt(mmm) exp(+i q.R'') e_q[a][nu]      (fold kernel)
+//   S4  M_q'[(nu,b)][c]         = sum_d W[(nu,b,c)][d] exp(-i q'.d)               (GEMM, K = d)
+//   S5  X_q'[(nu,nu'')][b]      = sum_c M[(nu,b)][c] e_q''[c][nu'']               (GEMM, K = c)
+//       V_q'[(nu,nu'')][nu']    = sum_b X[(nu,nu'')][b] e_q'[b][nu']              (GEMM, K = b)
+//   S6  gamma[nu] += sum |V|^2 w(f, f', f'')   fused into the epilogue of the last GEMM
+//
+// Every complex product is one real GEMM on the "real embedding": an operand row holds
+// [Re(0..Kc) | Im(0..Kc)] (each half zero-padded to Kcp = 32-multiple), and the B table of
+// a complex matrix E (K x modes) has rows [Re outputs (np rows) | Im outputs (np rows)]:
+//     B[j][k] = Re E(k,j), B[j][Kcp+k] = -Im E(k,j), B[np+j][k] = Im E(k,j), B[np+j][Kcp+k] = Re E(k,j)
+// so D = A B^T holds [Re | Im] of the complex product.  Precisions: BF16x3 (x = hi + lo in
+// bf16, product hi*hi + hi*lo + lo*hi, FP32 accumulate in tensor memory) or TF32 (one pass).
+//
+// GEMM kernel: one CTA = 6 warps.  Warp 0 issues TMA loads of 128-row x 128-byte A chunks
+// (128B swizzle) into a ring of stages; warp 1 owns tensor memory and issues tcgen05.mma
+// (M = 128, N = the whole padded output width) into one of two accumulators; warps 2-5 read
+// the accumulator back with tcgen05.ld and run the fused epilogue while the next tile
+// accumulates.  The B operand of a problem (<= 150 KB) stays resident in shared memory.
+#include <cudaTypedefs.h>
 
-phx_status phx_gamma_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec,
-                        const double* nB, const int32_t* irr_host, int n_irr, const GammaParams& gp,
-                        int prec, double* gacc, double* wacc, cudaStream_t s) {
-    (void)f; (void)freq; (void)evec; (void)nB; (void)irr_host; (void)n_irr; (void)gp; (void)prec;
-    (void)gacc; (void)wacc; (void)s;
-    return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core precision not built yet");
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "common.h"
+#include "gamma_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+constexpr int kThreads = 192;
+constexpr int kMaxStages = 8;
+constexpr int kBoxRows = 128;                  // rows of an A tile (= MMA M)
+constexpr int kChunkBytes = 128;               // bytes of K per chunk (one swizzle row)
+constexpr int kStageBytesPerPlane = kBoxRows * kChunkBytes;
+constexpr int kMaxNp = 192;                    // padded modes (or q' slots) per output half
+constexpr size_t kSmemLimit = 232448;          // 227 KB opt-in
+
+enum { EPI_M = 0, EPI_X = 1, EPI_G = 2 };
+enum { P_BF16X3 = 0, P_TF32 = 1 };
+
+struct TcArgs {
+    CUtensorMap a_map[2];       // A operand planes (hi, lo) or (fp32)
+    CUtensorMap b_map[2];       // B operand planes
+    int rows;                   // valid rows per problem
+    int tiles;                  // ceil(rows / 128)
+    int np;                     // output half width (multiple of 8); N = 2 np
+    int nk;                     // K chunks (128 bytes each)
+    int stages;
+    int n_acc;                  // 1 or 2 accumulators in tensor memory
+    int a_rows_per_problem;     // A row offset between problems
+    const int32_t* b_idx;       // per problem: B table index (row offset b_idx[p] * 2 np)
+    int b_base;                 // used when b_idx == nullptr
+    uint32_t tmem_cols;
+    int32_t* status;
+    // ---- epilogue parameters
+    void* out_hi;               // EPI_M / EPI_X: destination operand planes
+    void* out_lo;
+    int out_rows_per_slot;      // rows of the destination per problem / q' slot
+    int out_kr;                 // destination row length (elements)
+    int out_kcp;                // destination imaginary-half offset
+    int n;                      // modes
+    int nq_slots;               // EPI_M: valid q' slots in this tile
+    // EPI_G
+    const double* freq;
+    const double* nB;
+    int iq, t0, nu0, m1, m2, m3;
+    float sigma, window, f_min;
+    int shape;
+    double* gacc;               // [n] for this irreducible q (offset applied)
+    double* wacc;               // may be null
+};
+
+template <int PREC>
+__device__ __forceinline__ void store_operand(void* hi, void* lo, int64_t idx, float v) {
+    if (PREC == P_BF16X3) {
+        __nv_bfloat16 h, l;
+        tc::split_bf16(v, &h, &l);
+        ((__nv_bfloat16*)hi)[idx] = h;
+        ((__nv_bfloat16*)lo)[idx] = l;
+    } else {
+        ((float*)hi)[idx] = tc::round_tf32(v);
+    }
+}
+
+__device__ __forceinline__ float broad_f(float x, float sigma, float window, int shape) {
+    if (!(fabsf(x) < window * sigma)) return 0.0f;
+    if (shape == PHX_GAUSS) {
+        const float u = x / sigma;
+        return expf(-u * u) * (0.56418958354775628f / sigma);     // 1/(sqrt(pi) sigma)
+    }
+    const float h = 0.5f * sigma;
+    return h / (3.14159265358979f * (x * x + h * h));
+}
+
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+template <int PREC, int EPI>
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcArgs args) {
+    constexpr int kPlanes = (PREC == P_BF16X3) ? 2 : 1;
+    constexpr uint32_t kFmt = (PREC == P_BF16X3) ? 1u : 2u;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
+    __shared__ __align__(8) uint64_t bfull_bar, tfull_bar[2], tempty_bar[2], drain_bar;
+    __shared__ uint32_t tmem_base_slot;
+    __shared__ volatile int abort_flag;
+    __shared__ float s_f1[kMaxNp], s_n1[kMaxNp];
+    __shared__ double s_red_g[kBoxRows], s_red_w[kBoxRows];
+
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int np = args.np, N = 2 * np, nk = args.nk, stages = args.stages;
+    const uint32_t b_bytes_plane = (uint32_t)nk * N * kChunkBytes;
+    uint8_t* b_smem = smem;                                        // [plane][kc][N rows][128 B]
+    uint8_t* a_smem = smem + kPlanes * b_bytes_plane;              // [stage][plane][128 rows][128 B]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.y;                                      // problem
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) { tc::mbar_init(&full_bar[s], 1); tc::mbar_init(&empty_bar[s], 1); }
+        tc::mbar_init(&bfull_bar, 1);
+        for (int a = 0; a < 2; ++a) { tc::mbar_init(&tfull_bar[a], 1); tc::mbar_init(&tempty_bar[a], 128); }
+        tc::mbar_init(&drain_bar, 1);
+        abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0 && lane == 0) {
+        for (int pl = 0; pl < kPlanes; ++pl) { tc::prefetch_tmap(&args.a_map[pl]); tc::prefetch_tmap(&args.b_map[pl]); }
+    }
+    if (warp == 1) tc::tmem_alloc(&tmem_base_slot, args.tmem_cols);
+    if (threadIdx.x >= 64) {
+        const int t = threadIdx.x - 64;
+        s_red_g[t] = 0.0;
+        s_red_w[t] = 0.0;
+    }
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem_base = tmem_base_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            const int brow = (args.b_idx ? args.b_idx[p] : args.b_base) * N;
+            tc::mbar_expect_tx(&bfull_bar, kPlanes * b_bytes_plane);
+            for (int pl = 0; pl < kPlanes; ++pl)
+                for (int kc = 0; kc < nk; ++kc)
+                    for (int half = 0; half < 2; ++half)
+                        tc::tma_load_2d(b_smem + pl * b_bytes_plane + ((size_t)kc * N + half * np) * kChunkBytes,
+                                        &args.b_map[pl], &bfull_bar, kc * (kChunkBytes / (PREC == P_BF16X3 ? 2 : 4)),
+                                        brow + half * np);
+            int stage = 0;
+            uint32_t phase = 0;
+            bool pending[kMaxStages];
+            uint32_t pend_phase[kMaxStages];
+            for (int s = 0; s < kMaxStages; ++s) { pending[s] = false; pend_phase[s] = 0; }
+            const int kelems = kChunkBytes / (PREC == P_BF16X3 ? 2 : 4);
+            for (int tile = blockIdx.x; tile < args.tiles && !abort_flag; tile += gridDim.x) {
+                const int arow = p * args.a_rows_per_problem + tile * kBoxRows;
+                for (int kc = 0; kc < nk; ++kc) {
+                    if (!tc::mbar_wait(&empty_bar[stage], phase ^ 1, &abort_flag)) {
+                        abort_flag = 1;
+                        atomicExch(args.status, (int)PHX_ERR_TIMEOUT);
+                        break;
+                    }
+                    pending[stage] = false;
+                    tc::mbar_expect_tx(&full_bar[stage], kPlanes * kStageBytesPerPlane);
+                    for (int pl = 0; pl < kPlanes; ++pl)
+                        tc::tma_load_2d(a_smem + ((size_t)stage * kPlanes + pl) * kStageBytesPerPlane, &args.a_map[pl],
+                                        &full_bar[stage], kc * kelems, arow);
+                    pending[stage] = true;
+                    pend_phase[stage] = phase;
+                    if (++stage == stages) { stage = 0; phase ^= 1; }
+                }
+            }
+            if (abort_flag) {
+                // let loads already issued land before the CTA retires (bounded)
+                for (int s = 0; s < stages; ++s)
+                    if (pending[s]) {
+                        const uint64_t t0 = tc::global_ns();
+                        while (!tc::mbar_try_wait(&full_bar[s], pend_phase[s]) &&
+                               tc::global_ns() - t0 < tc::kWaitLimitNs) {
+                        }
+                    }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t id_full = tc::idesc(128, N <= 256 ? N : np, kFmt);
+            bool ok = tc::mbar_wait(&bfull_bar, 0, &abort_flag);
+            if (!ok) { abort_flag = 1; atomicExch(args.status, (int)PHX_ERR_TIMEOUT); }
+            tc::tc_fence_after();
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, acc_phase = 0;
+            const uint32_t b_base = tc::smem_u32(b_smem);
+            const uint32_t a_base = tc::smem_u32(a_smem);
+            for (int tile = blockIdx.x; ok && tile < args.tiles; tile += gridDim.x) {
+                if (!tc::mbar_wait(&tempty_bar[acc], acc_phase ^ 1, &abort_flag)) {
+                    abort_flag = 1; atomicExch(args.status, (int)PHX_ERR_TIMEOUT); break;
+                }
+                tc::tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * N);
+                for (int kc = 0; kc < nk; ++kc) {
+                    if (!tc::mbar_wait(&full_bar[stage], phase, &abort_flag)) {
+                        abort_flag = 1; atomicExch(args.status, (int)PHX_ERR_TIMEOUT); ok = false; break;
+                    }
+                    tc::tc_fence_after();
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {                      // 4 x 32 bytes per chunk
+                        const uint32_t koff = (uint32_t)k * 32;
+                        const uint32_t a0 = a_base + (uint32_t)(stage * kPlanes) * kStageBytesPerPlane + koff;
+                        const uint32_t acc_flag = (kc | k) ? 1u : 0u;
+                        for (int part = 0; part < (N <= 256 ? 1 : 2); ++part) {
+                            const uint32_t bo = (uint32_t)((size_t)kc * N + part * np) * kChunkBytes + koff;
+                            const uint32_t dcol = d_tmem + (uint32_t)(part * np);
+                            if (PREC == P_BF16X3) {
+                                const uint64_t ah = tc::sdesc_sw128(a0);
+                                const uint64_t al = tc::sdesc_sw128(a0 + kStageBytesPerPlane);
+                                const uint64_t bh = tc::sdesc_sw128(b_base + bo);
+                                const uint64_t bl = tc::sdesc_sw128(b_base + b_bytes_plane + bo);
+                                tc::mma_f16(dcol, ah, bh, id_full, acc_flag);
+                                tc::mma_f16(dcol, ah, bl, id_full, 1u);
+                                tc::mma_f16(dcol, al, bh, id_full, 1u);
+                            } else {
+                                tc::mma_tf32(dcol, tc::sdesc_sw128(a0), tc::sdesc_sw128(b_base + bo), id_full,
+                                             acc_flag);
+                            }
+                        }
+                    }
+                    tc::mma_commit(&empty_bar[stage]);
+                    if (++stage == stages) { stage = 0; phase ^= 1; }
+                }
+                if (!ok) break;
+                tc::mma_commit(&tfull_bar[acc]);
+                if (args.n_acc == 2) { acc ^= 1; if (acc == 0) acc_phase ^= 1; } else { acc_phase ^= 1; }
+            }
+            // every MMA of this thread has completed once drain_bar flips
+            tc::mma_commit(&drain_bar);
+            const uint64_t t0 = tc::global_ns();
+            while (!tc::mbar_try_wait(&drain_bar, 0) && tc::global_ns() - t0 < tc::kWaitLimitNs) {
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (warps 2..5)
+        const int et = threadIdx.x - 64;                  // 0..127
+        const int lgrp = warp & 3;                        // tensor-memory lane group of this warp
+        int q1 = 0, q2 = 0;
+        if (EPI == EPI_G) {
+            q1 = args.t0 + p;
+            q2 = phx_third_index(args.iq, q1, args.m1, args.m2, args.m3);
+            for (int j = et; j < np; j += 128) {
+                const bool v = j < args.n;
+                s_f1[j] = v ? (float)args.freq[(int64_t)q1 * args.n + j] : 0.0f;
+                s_n1[j] = v ? (float)args.nB[(int64_t)q1 * args.n + j] : 0.0f;
+            }
+            epi_barrier();
+        }
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int tile = blockIdx.x; tile < args.tiles; tile += gridDim.x) {
+            const bool ok = tc::mbar_wait(&tfull_bar[acc], acc_phase, &abort_flag);
+            if (!ok) {
+                abort_flag = 1;
+                atomicExch(args.status, (int)PHX_ERR_TIMEOUT);
+            }
+            epi_barrier();                 // every epilogue thread takes the same decision
+            if (abort_flag) break;
+            tc::tc_fence_after();
+            const int row = tile * kBoxRows + lgrp * 32 + lane;
+            const bool valid = row < args.rows;
+            const uint32_t taddr = tmem_base + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)(acc * N);
+            float v[16];
+            if (EPI == EPI_M) {
+                // row (nu, b, c) of W -> M_slot[(nu, b)][c] (re) and [(nu, b)][Kcp + c] (im)
+                const int nb = row / args.n, c = row % args.n;
+                for (int j0 = 0; j0 < N; j0 += 16) {
+                    tc::tmem_ld16(taddr + j0, v);
+                    if (valid) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int j = j0 + i;
+                            const int slot = j < np ? j : j - np;
+                            if (slot >= args.nq_slots) continue;
+                            const int64_t idx = ((int64_t)slot * args.out_rows_per_slot + nb) * args.out_kr +
+                                                (j < np ? 0 : args.out_kcp) + c;
+                            store_operand<PREC>(args.out_hi, args.out_lo, idx, v[i]);
+                        }
+                    }
+                }
+            } else if (EPI == EPI_X) {
+                // row (nu, b) -> X[(nu, nu'')][b] (re) and [(nu, nu'')][Kcp + b] (im)
+                const int nu = row / args.n, b = row % args.n;
+                const int64_t base = (int64_t)p * args.out_rows_per_slot + (int64_t)nu * args.n;
+                for (int j0 = 0; j0 < N; j0 += 16) {
+                    tc::tmem_ld16(taddr + j0, v);
+                    if (valid) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int j = j0 + i;
+                            const int mode = j < np ? j : j - np;
+                            if (mode >= args.n) continue;
+                            const int64_t idx = (base + mode) * args.out_kr + (j < np ? 0 : args.out_kcp) + b;
+                            store_operand<PREC>(args.out_hi, args.out_lo, idx, v[i]);
+                        }
+                    }
+                }
+            } else {
+                // row (nu, nu'') holds V[nu'] = [Re | Im]; weight and reduce over nu'
+                const int nu = row / args.n, n2i = row % args.n;
+                float f0 = 0.f, f2 = 0.f, nn2 = 0.f;
+                if (valid) {
+                    f0 = (float)args.freq[(int64_t)args.iq * args.n + args.nu0 + nu];
+                    f2 = (float)args.freq[(int64_t)q2 * args.n + n2i];
+                    nn2 = (float)args.nB[(int64_t)q2 * args.n + n2i];
+                }
+                const bool live = valid && f0 >= args.f_min && f2 >= args.f_min;
+                // w = [...] / (2 pi)^4 / (f0 f1 f2): delta(w) = g(f)/(2 pi) and 1/(w0 w1 w2)
+                const float inv_f02 = live ? 1.0f / (1558.5454565440389f * f0 * f2) : 0.0f;
+                float gs = 0.f, ws = 0.f;
+                float vi[16];
+                for (int j0 = 0; j0 < np; j0 += 16) {
+                    tc::tmem_ld16(taddr + j0, v);
+                    tc::tmem_ld16(taddr + np + j0, vi);
+                    if (live) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int j = j0 + i;
+                            const float f1 = s_f1[j];
+                            if (j >= args.n || !(f1 >= args.f_min)) continue;
+                            const float gd = broad_f(f0 - f1 - f2, args.sigma, args.window, args.shape);
+                            const float ga = broad_f(f0 + f1 - f2, args.sigma, args.window, args.shape);
+                            if (gd == 0.f && ga == 0.f) continue;
+                            const float n1 = s_n1[j];
+                            const float w = ((1.f + n1 + nn2) * gd + 2.f * (n1 - nn2) * ga) * inv_f02 / f1;
+                            gs += (v[i] * v[i] + vi[i] * vi[i]) * w;
+                            ws += w;
+                        }
+                    }
+                }
+                // reduce rows of equal nu: shared accumulators indexed from the tile's first nu
+                const int nu_first = (tile * kBoxRows) / args.n;
+                if (live) {
+                    atomicAdd(&s_red_g[nu - nu_first], (double)gs);
+                    atomicAdd(&s_red_w[nu - nu_first], (double)ws);
+                }
+                epi_barrier();
+                const int nu_last = min(tile * kBoxRows + kBoxRows, args.rows) - 1;
+                const int cnt = nu_last / args.n - nu_first + 1;
+                if (et < cnt) {
+                    const double g = s_red_g[et], w = s_red_w[et];
+                    if (g != 0.0) atomicAdd(&args.gacc[args.nu0 + nu_first + et], g);
+                    if (args.wacc && w != 0.0) atomicAdd(&args.wacc[args.nu0 + nu_first + et], w);
+                    s_red_g[et] = 0.0;
+                    s_red_w[et] = 0.0;
+                }
+                epi_barrier();
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&tempty_bar[acc]);
+            if (args.n_acc == 2) { acc ^= 1; if (acc == 0) acc_phase ^= 1; } else { acc_phase ^= 1; }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem_base, args.tmem_cols);
+    }
+}
+
+// ---------------------------------------------------------------- operand preparation kernels
+
+// B tables of the eigenvectors of every mesh point: rows [Re out (np) | Im out (np)], K =
+// [Re e(c) (Kcp) | Im e(c) (Kcp)] (see the header comment for the signs).
+template <int PREC>
+__global__ void prep_evec_tables(const double2* __restrict__ evec, int nq, int n, int np, int kcp, void* hi,
+                                 void* lo) {
+    const int N = 2 * np, kr = 2 * kcp;
+    const int64_t total = (int64_t)nq * N * kr;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int kk = (int)(t % kr);
+        const int j = (int)((t / kr) % N);
+        const int q = (int)(t / ((int64_t)kr * N));
+        const int mode = j < np ? j : j - np;
+        const int k = kk < kcp ? kk : kk - kcp;
+        float val = 0.f;
+        if (mode < n && k < n) {
+            const double2 e = evec[((int64_t)q * n + k) * n + mode];
+            const bool re_out = j < np, re_in = kk < kcp;
+            val = (float)(re_out ? (re_in ? e.x : -e.y) : (re_in ? e.y : e.x));
+        }
+        store_operand<PREC>(hi, lo, t, val);
+    }
+}
+
+// B tables of the Fourier phases exp(-i q'.d) for every tile of Q q' (slot = q' - tile*Q).
+template <int PREC>
+__global__ void prep_phase_tables(const int32_t* __restrict__ d_int, int n_d, int m1, int m2, int m3, int Q,
+                                  int n_tiles, int qp_np, int kcp, void* hi, void* lo) {
+    const int N = 2 * qp_np, kr = 2 * kcp;
+    const int nq = m1 * m2 * m3;
+    const int64_t total = (int64_t)n_tiles * N * kr;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int kk = (int)(t % kr);
+        const int j = (int)((t / kr) % N);
+        const int tile = (int)(t / ((int64_t)kr * N));
+        const int slot = j < qp_np ? j : j - qp_np;
+        const int d = kk < kcp ? kk : kk - kcp;
+        const int qp = tile * Q + slot;
+        float val = 0.f;
+        if (slot < Q && qp < nq && d < n_d) {
+            const int k1 = qp / (m2 * m3), k2 = (qp / m3) % m2, k3 = qp % m3;
+            const int a1 = (k1 * d_int[3 * d]) % m1, a2 = (k2 * d_int[3 * d + 1]) % m2, a3 = (k3 * d_int[3 * d + 2]) % m3;
+            double s, c;
+            sincospi(2.0 * ((double)a1 / m1 + (double)a2 / m2 + (double)a3 / m3), &s, &c);
+            // E(d, slot) = exp(-i theta) = c - i s
+            const double er = c, ei = -s;
+            const bool re_out = j < qp_np, re_in = kk < kcp;
+            val = (float)(re_out ? (re_in ? er : -ei) : (re_in ? ei : er));
+        }
+        store_operand<PREC>(hi, lo, t, val);
+    }
+}
+
+// S3 fold into the DFT's A operand: row (nu, b, c), K = [Re W(d) | Im W(d)].  One thread per
+// (row, d); seg_of maps (d, b, c) to its COO segment (or -1).
+template <int PREC>
+__global__ void fold_tc_kernel(const int32_t* __restrict__ seg_of, const int64_t* __restrict__ seg_start,
+                               const int32_t* __restrict__ ent_a, const int32_t* __restrict__ ent_r2,
+                               const double* __restrict__ ent_w, int n_d, double qa, double qb, double qc,
+                               const double2* __restrict__ eq, int n, int nu0, int n_nu, int kcp, void* hi, void* lo) {
+    const int64_t nn = (int64_t)n * n;
+    const int64_t total = (int64_t)n_nu * nn * n_d;
+    const int kr = 2 * kcp;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(t % n_d);
+        const int64_t row = t / n_d;                 // (nu_l, b, c)
+        const int nl = (int)(row / nn);
+        const int bc = (int)(row % nn);
+        const int s = seg_of[(int64_t)d * nn + bc];
+        double ar = 0.0, ai = 0.0;
+        if (s >= 0) {
+            const int nu = nu0 + nl;
+            for (int64_t k = seg_start[s]; k < seg_start[s + 1]; ++k) {
+                const double x = 2.0 * (qa * ent_r2[3 * k] + qb * ent_r2[3 * k + 1] + qc * ent_r2[3 * k + 2]);
+                double sn, cs;
+                sincospi(x, &sn, &cs);
+                const double2 e = eq[(int64_t)ent_a[k] * n + nu];
+                const double w = ent_w[k];
+                ar += w * (cs * e.x - sn * e.y);
+                ai += w * (cs * e.y + sn * e.x);
+            }
+        }
+        store_operand<PREC>(hi, lo, row * kr + d, (float)ar);
+        store_operand<PREC>(hi, lo, row * kr + kcp + d, (float)ai);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool get_encoder() {
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    return g_encode != nullptr;
+}
+
+// 2D map over a row-major [rows][kr] operand plane, box = 128-byte K chunk x box_rows.
+bool make_map(CUtensorMap* m, const void* base, int prec, int64_t rows, int kr, int box_rows) {
+    const int esz = prec == P_BF16X3 ? 2 : 4;
+    cuuint64_t dims[2] = {(cuuint64_t)kr, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kr * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(kChunkBytes / esz), (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = g_encode(m, prec == P_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                          const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct Operand {
+    void* hi = nullptr;
+    void* lo = nullptr;
+    int64_t rows = 0;
+    int kr = 0;
+};
+
+phx_status alloc_operand(phx_ctx* ctx, const char* name, int prec, int64_t rows, int kr, Operand* o) {
+    const int esz = prec == P_BF16X3 ? 2 : 4;
+    const size_t bytes = (size_t)rows * kr * esz;
+    std::string nh = std::string(name) + ".hi", nl = std::string(name) + ".lo";
+    o->hi = phx_ws(ctx, nh.c_str(), bytes);
+    if (!o->hi) return PHX_ERR_NOMEM;
+    if (prec == P_BF16X3) {
+        o->lo = phx_ws(ctx, nl.c_str(), bytes);
+        if (!o->lo) return PHX_ERR_NOMEM;
+    }
+    o->rows = rows;
+    o->kr = kr;
+    return PHX_OK;
+}
+
+template <int PREC, int EPI>
+cudaError_t launch_gemm(phx_ctx* ctx, TcArgs& a, int n_problems, int ctas_per_problem, cudaStream_t s) {
+    constexpr int planes = PREC == P_BF16X3 ? 2 : 1;
+    const size_t b_bytes = (size_t)planes * a.nk * 2 * a.np * kChunkBytes;
+    const size_t smem = 1024 + b_bytes + (size_t)a.stages * planes * kStageBytesPerPlane;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<PREC, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(kSmemLimit - 8192));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    (void)ctx;
+    dim3 grid(std::min(ctas_per_problem, a.tiles), n_problems);
+    tc_gemm_kernel<PREC, EPI><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Shared-memory plan: B resident + as many A stages as fit (at least 2).
+bool plan_stages(int prec, int nk, int np, int* stages) {
+    const int planes = prec == P_BF16X3 ? 2 : 1;
+    const size_t b_bytes = (size_t)planes * nk * 2 * np * kChunkBytes;
+    const size_t avail = kSmemLimit - 8192 - 1024;   // static shared + alignment slack
+    if (b_bytes + 2 * (size_t)planes * kStageBytesPerPlane > avail) return false;
+    int st = (int)((avail - b_bytes) / ((size_t)planes * kStageBytesPerPlane));
+    *stages = std::min(st, kMaxStages);
+    return true;
+}
+
+uint32_t tmem_cols_for(int N, int n_acc) {
+    uint32_t need = (uint32_t)(N * n_acc), c = 32;
+    while (c < need) c <<= 1;
+    return c;
+}
+
+template <int PREC>
+phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec, const double* nB,
+                  const int32_t* irr_host, int n_irr, const GammaParams& gp, double* gacc, double* wacc,
+                  cudaStream_t s) {
+    const int n = f->n, nq = f->nq;
+    const int np = round_up(n, 16);
+    if (np > kMaxNp) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: n = %d > %d", n, kMaxNp);
+    const int kcp = round_up(n, 32), kr = 2 * kcp;
+    const int kelems = kChunkBytes / (PREC == P_BF16X3 ? 2 : 4);
+    const int nk = kr / kelems;
+    const int N = 2 * np;
+    int st_e = 0;
+    if (!plan_stages(PREC, nk, np, &st_e))
+        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: eigenvector table of n = %d exceeds shared memory", n);
+    // DFT shape
+    const int kcp_d = round_up(f->n_d, 32), kr_d = 2 * kcp_d, nk_d = kr_d / kelems;
+    // q' tile: keep M and X (Q * n^2 rows each) near 64 MB per operand plane so they stay in L2
+    const int64_t n2 = (int64_t)n * n;
+    const int esz = PREC == P_BF16X3 ? 2 : 4;
+    int Q = (int)std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)48 << 20) / (n2 * kr * esz)));
+    Q = std::min(Q, 128);
+    int st_d = 0;
+    while (!plan_stages(PREC, nk_d, round_up(Q, 8), &st_d)) {      // phase table must fit too
+        if (Q <= 8)
+            return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: %d lattice differences exceed shared memory", f->n_d);
+        Q = std::max(8, Q / 2);
+    }
+    const int qp_np = round_up(Q, 8);
+    const int n_tiles_q = (nq + Q - 1) / Q;
+    if (!get_encoder()) return phx_set_error(ctx, PHX_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    const int n_nu = n;                       // all modes of q at once
+    const int64_t rows_w = (int64_t)n_nu * n2;
+    const int64_t rows_a = (int64_t)n_nu * n;     // rows of M and X per q' slot
+
+    Operand opW, opM, opX, opE, opP;
+    PHX_TRY(alloc_operand(ctx, "tc.W", PREC, rows_w, kr_d, &opW));
+    PHX_TRY(alloc_operand(ctx, "tc.M", PREC, (int64_t)Q * rows_a, kr, &opM));
+    PHX_TRY(alloc_operand(ctx, "tc.X", PREC, (int64_t)Q * rows_a, kr, &opX));
+    PHX_TRY(alloc_operand(ctx, "tc.E", PREC, (int64_t)nq * N, kr, &opE));
+    PHX_TRY(alloc_operand(ctx, "tc.P", PREC, (int64_t)n_tiles_q * 2 * qp_np, kr_d, &opP));
+    int32_t* qpp = (int32_t*)phx_ws(ctx, "tc.qpp", (size_t)nq * 4);
+    int32_t* ident = (int32_t*)phx_ws(ctx, "tc.ident", (size_t)nq * 4);
+    int32_t* seg_of = (int32_t*)phx_ws(ctx, "tc.segof", (size_t)f->n_d * n2 * 4);
+    if (!qpp || !ident || !seg_of) return PHX_ERR_NOMEM;
+    // padding columns of M, X and W must read as zero
+    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opM.hi, 0, (size_t)opM.rows * kr * esz, s));
+    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opX.hi, 0, (size_t)opX.rows * kr * esz, s));
+    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opW.hi, 0, (size_t)opW.rows * kr_d * esz, s));
+    if (PREC == P_BF16X3) {
+        PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opM.lo, 0, (size_t)opM.rows * kr * esz, s));
+        PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opX.lo, 0, (size_t)opX.rows * kr * esz, s));
+        PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opW.lo, 0, (size_t)opW.rows * kr_d * esz, s));
+    }
+    {
+        std::vector<int32_t> id(nq);
+        for (int i = 0; i < nq; ++i) id[i] = i;
+        std::vector<int32_t> so((size_t)f->n_d * n2, -1);
+        std::vector<int32_t> keys((size_t)f->n_seg * 3);
+        PHX_CUDA_CHECK(ctx, cudaMemcpy(keys.data(), f->seg_key, keys.size() * 4, cudaMemcpyDeviceToHost));
+        for (int64_t sgi = 0; sgi < f->n_seg; ++sgi)
+            so[(size_t)keys[3 * sgi] * n2 + (size_t)keys[3 * sgi + 1] * n + keys[3 * sgi + 2]] = (int32_t)sgi;
+        PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(ident, id.data(), nq * 4, cudaMemcpyHostToDevice, s));
+        PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(seg_of, so.data(), so.size() * 4, cudaMemcpyHostToDevice, s));
+        PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
+    }
+    prep_evec_tables<PREC><<<2048, 256, 0, s>>>((const double2*)evec, nq, n, np, kcp, opE.hi, opE.lo);
+    PHX_CUDA_CHECK(ctx, cudaGetLastError());
+    prep_phase_tables<PREC><<<256, 256, 0, s>>>(f->d_int, f->n_d, f->mesh[0], f->mesh[1], f->mesh[2], Q, n_tiles_q,
+                                                qp_np, kcp_d, opP.hi, opP.lo);
+    PHX_CUDA_CHECK(ctx, cudaGetLastError());
+
+    // tensor maps (operand buffers are fixed for the whole call)
+    TcArgs aD{}, aA{}, aB{};
+    const int planes = PREC == P_BF16X3 ? 2 : 1;
+    for (int pl = 0; pl < planes; ++pl) {
+        const void* w = pl ? opW.lo : opW.hi;
+        const void* m = pl ? opM.lo : opM.hi;
+        const void* x = pl ? opX.lo : opX.hi;
+        const void* e = pl ? opE.lo : opE.hi;
+        const void* ph = pl ? opP.lo : opP.hi;
+        bool ok = make_map(&aD.a_map[pl], w, PREC, opW.rows, kr_d, kBoxRows) &&
+                  make_map(&aD.b_map[pl], ph, PREC, opP.rows, kr_d, qp_np) &&
+                  make_map(&aA.a_map[pl], m, PREC, opM.rows, kr, kBoxRows) &&
+                  make_map(&aA.b_map[pl], e, PREC, opE.rows, kr, np) &&
+                  make_map(&aB.a_map[pl], x, PREC, opX.rows, kr, kBoxRows) &&
+                  make_map(&aB.b_map[pl], e, PREC, opE.rows, kr, np);
+        if (!ok) return phx_set_error(ctx, PHX_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    }
+    const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
+    // DFT: W rows x (2 qp_np) ; epilogue scatters into M
+    aD.rows = (int)rows_w; aD.tiles = (int)((rows_w + kBoxRows - 1) / kBoxRows);
+    aD.np = qp_np; aD.nk = nk_d; aD.stages = st_d; aD.n_acc = (4 * qp_np <= 512) ? 2 : 1;
+    aD.tmem_cols = tmem_cols_for(2 * qp_np, aD.n_acc);
+    aD.a_rows_per_problem = 0; aD.b_idx = nullptr;
+    aD.status = (int32_t*)ctx->status_word;
+    aD.out_hi = opM.hi; aD.out_lo = opM.lo; aD.out_rows_per_slot = (int)rows_a; aD.out_kr = kr; aD.out_kcp = kcp;
+    aD.n = n;
+    // GEMM with e_q'': rows (nu, b), K = c ; epilogue writes X
+    aA.rows = (int)rows_a; aA.tiles = (int)((rows_a + kBoxRows - 1) / kBoxRows);
+    aA.np = np; aA.nk = nk; aA.stages = st_e; aA.n_acc = (4 * np <= 512) ? 2 : 1;
+    aA.tmem_cols = tmem_cols_for(N, aA.n_acc);
+    aA.a_rows_per_problem = (int)rows_a;
+    aA.status = aD.status;
+    aA.out_hi = opX.hi; aA.out_lo = opX.lo; aA.out_rows_per_slot = (int)rows_a; aA.out_kr = kr; aA.out_kcp = kcp;
+    aA.n = n;
+    // GEMM with e_q': rows (nu, nu''), K = b ; fused linewidth epilogue
+    aB.rows = (int)rows_a; aB.tiles = aA.tiles;
+    aB.np = np; aB.nk = nk; aB.stages = st_e; aB.n_acc = aA.n_acc; aB.tmem_cols = aA.tmem_cols;
+    aB.a_rows_per_problem = (int)rows_a;
+    aB.status = aD.status;
+    aB.n = n; aB.freq = freq; aB.nB = nB; aB.nu0 = 0;
+    aB.m1 = f->mesh[0]; aB.m2 = f->mesh[1]; aB.m3 = f->mesh[2];
+    aB.sigma = (float)gp.sigma; aB.window = (float)gp.window; aB.f_min = (float)gp.f_min; aB.shape = gp.shape;
+
+    for (int si = 0; si < n_irr; ++si) {
+        const int iq = irr_host[si];
+        const int k1 = iq / (f->mesh[1] * f->mesh[2]), k2 = (iq / f->mesh[2]) % f->mesh[1], k3 = iq % f->mesh[2];
+        PHX_CUDA_CHECK(ctx, phx_launch_third_index(iq, f->mesh, qpp, s));
+        {
+            const int64_t total = rows_w * f->n_d;
+            const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 16);
+            fold_tc_kernel<PREC><<<blocks, 256, 0, s>>>(seg_of, f->seg_start, f->ent_a, f->ent_r2, f->ent_w, f->n_d,
+                                                        (double)k1 / f->mesh[0], (double)k2 / f->mesh[1],
+                                                        (double)k3 / f->mesh[2],
+                                                        (const double2*)evec + (int64_t)iq * n2, n, 0, n_nu, kcp_d,
+                                                        opW.hi, opW.lo);
+            PHX_CUDA_CHECK(ctx, cudaGetLastError());
+        }
+        aB.iq = iq;
+        aB.gacc = gacc + (int64_t)si * n;
+        aB.wacc = wacc ? wacc + (int64_t)si * n : nullptr;
+        for (int tq = 0; tq < n_tiles_q; ++tq) {
+            const int t0 = tq * Q, Qt = std::min(Q, nq - t0);
+            aD.b_base = tq;
+            aD.nq_slots = Qt;
+            PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_M>(ctx, aD, 1, sms, s)));
+            const int cpp = std::max(1, sms / Qt);
+            aA.b_idx = qpp + t0;
+            PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_X>(ctx, aA, Qt, cpp, s)));
+            aB.b_idx = ident + t0;
+            aB.t0 = t0;
+            PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_G>(ctx, aB, Qt, cpp, s)));
+        }
+    }
+    return PHX_OK;
+}
+
+}  // namespace
+
+phx_status phx_gamma_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec, const double* nB,
+                        const int32_t* irr_host, int n_irr, const GammaParams& gp, int prec, double* gacc,
+                        double* wacc, cudaStream_t s) {
+    if (ctx->cc_major != 10)
+        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path needs a Blackwell (sm_10x) device");
+    if (prec == PHX_BF16X3) return run_tc<P_BF16X3>(ctx, f, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s);
+    return run_tc<P_TF32>(ctx, f, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s);
 }

@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Throughput of the three-phonon scattering hot path on GB300, in phonon triplets/s.
+
+One step = the whole path on the 32-atom mass-disordered LJ fcc cell (96 modes), 8x8x8
+mesh, 50 K, Gaussian 0.1 THz: harmonic phonons on every mesh point (FP64 eigensolver),
+linewidths of every mode of the 260 irreducible q-points (tensor-core contraction),
+unfolding, RTA conductivity.  A triplet is one (lambda, q', nu', nu'') element with
+lambda an irreducible mode above f_min (both scattering processes come from it).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|tf32|fp64]
+    python bench.py --impl reference ...     # the FP64 CPU oracle on a bounded sample
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own replica of the
+workload on its own GPU (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "phonon triplets/s (V3+gamma) on 1 GB300, mixed/batched vs FP64 path, at stated kappa error"
+UNIT = "triplets/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return None
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------- workload
+
+class Workload:
+    """Inputs of the 32-atom / 8x8x8 workload, resident on the device."""
+
+    def __init__(self, phx, ctx, precision, device):
+        import torch
+        import phx_inputs as P
+        self.torch = torch
+        self.w = w = P.fcc_massdisorder_32()
+        self.f2, f3 = w.ifc2(), w.ifc3()
+        self.f2val = self.f2.val.reshape(-1, 9)
+        c = w.crystal
+        self.c = c
+        self.n = 3 * c.n_atoms
+        self.precision = precision
+        self.ctx = ctx
+        self.h = ctx.fc3(c.lattice, c.masses, f3.idx, f3.val, w.mesh)
+        self.irr, self.f2i, _ = phx.irreducible(w.mesh, w.rotations)
+        nq = int(np.prod(w.mesh))
+        self.nq = nq
+        self.q_host = np.array([(i // (w.mesh[1] * w.mesh[2]) / w.mesh[0], (i // w.mesh[2]) % w.mesh[1] / w.mesh[1],
+                                 i % w.mesh[2] / w.mesh[2]) for i in range(nq)])
+        dev = device
+        f64 = torch.float64
+        self.q = torch.from_numpy(self.q_host).to(dev)
+        self.freq = torch.zeros((nq, self.n), dtype=f64, device=dev)
+        self.evec = torch.zeros((nq, self.n, self.n), dtype=torch.complex128, device=dev)
+        self.vv = torch.zeros((nq, self.n, 3, 3), dtype=f64, device=dev)
+        self.irr_d = torch.from_numpy(self.irr.astype(np.int32)).to(dev)
+        self.f2i_d = torch.from_numpy(self.f2i.astype(np.int32)).to(dev)
+        self.g_irr = torch.zeros((len(self.irr), self.n), dtype=f64, device=dev)
+        self.g_full = torch.zeros((nq, self.n), dtype=f64, device=dev)
+        self.kappa = None
+
+    def step(self, precision=None):
+        prec = precision or self.precision
+        w, c, ctx = self.w, self.c, self.ctx
+        ctx.harmonic(c.lattice, c.masses, self.f2.idx, self.f2val, self.q, freq=self.freq, evec=self.evec,
+                     vel=None, vv=self.vv, want_vel=False)
+        ctx.gamma(self.h, self.freq, self.evec, self.irr_d, w.temperature, w.shape, w.sigma_thz, w.window,
+                  w.f_min_thz, precision=prec, gamma=self.g_irr)
+        ctx.unfold(self.freq, self.irr_d, self.g_irr, self.f2i_d, out=self.g_full)
+        self.kappa = ctx.kappa_rta(c.lattice, c.masses, self.freq, self.g_full, w.temperature, vv=self.vv,
+                                   f_min=w.f_min_thz)
+        return self.kappa
+
+    def triplets(self):
+        f = self.freq.cpu().numpy()
+        valid = (f[self.irr] >= self.w.f_min_thz).sum()
+        return int(valid) * self.nq * self.n * self.n
+
+    # ---- end to end through the public API with host (pinned) buffers
+    def step_host(self, bufs):
+        w, c, ctx = self.w, self.c, self.ctx
+        ctx.harmonic(c.lattice, c.masses, self.f2.idx, self.f2val, bufs["q"], freq=bufs["freq"], evec=bufs["evec"],
+                     vel=None, vv=bufs["vv"], want_vel=False)
+        ctx.gamma(self.h, bufs["freq"], bufs["evec"], bufs["irr"], w.temperature, w.shape, w.sigma_thz, w.window,
+                  w.f_min_thz, precision=self.precision, gamma=bufs["g_irr"])
+        ctx.unfold(bufs["freq"], bufs["irr"], bufs["g_irr"], bufs["f2i"], out=bufs["g_full"])
+        return ctx.kappa_rta(c.lattice, c.masses, bufs["freq"], bufs["g_full"], w.temperature, vv=bufs["vv"],
+                             f_min=w.f_min_thz)
+
+    def host_buffers(self):
+        torch = self.torch
+
+        keep = []
+
+        def pinned(shape, dtype):
+            t = torch.zeros(shape, dtype=dtype).pin_memory()
+            keep.append(t)               # the numpy view does not own the pinned memory
+            return t.numpy()
+        n, nq = self.n, self.nq
+        b = {"q": pinned((nq, 3), torch.float64), "freq": pinned((nq, n), torch.float64),
+             "evec": pinned((nq, n, n), torch.complex128), "vv": pinned((nq, n, 3, 3), torch.float64),
+             "irr": pinned((len(self.irr),), torch.int32), "f2i": pinned((nq,), torch.int32),
+             "g_irr": pinned((len(self.irr), n), torch.float64), "g_full": pinned((nq, n), torch.float64)}
+        b["_keep"] = keep
+        b["q"][:] = self.q_host
+        b["irr"][:] = self.irr
+        b["f2i"][:] = self.f2i
+        return b
+
+    def host_bytes(self, b):
+        """H2D and D2H bytes one host-buffer step moves (counted from the arrays copied)."""
+        ifc2 = self.f2.idx.nbytes + self.f2val.nbytes
+        h2d = (b["q"].nbytes + ifc2 + b["freq"].nbytes + b["evec"].nbytes + b["irr"].nbytes       # harmonic, gamma
+               + b["freq"].nbytes + b["irr"].nbytes + b["g_irr"].nbytes + b["f2i"].nbytes        # unfold
+               + b["freq"].nbytes + b["vv"].nbytes + b["g_full"].nbytes)                          # kappa
+        d2h = (b["freq"].nbytes + b["evec"].nbytes + b["vv"].nbytes + 4                           # harmonic (+status)
+               + b["g_irr"].nbytes + 4 + b["g_full"].nbytes + 72)
+        return int(h2d), int(d2h)
+
+
+# ----------------------------------------------------------------------------- oracle timing
+
+def oracle_sample(n_qp=None, seed_q=1):
+    """FP64 oracle linewidths of one irreducible q-point (all or n_qp of the q'); returns
+    (seconds, triplets, description).  The harmonic part is prepared outside the clock."""
+    import oracle as O
+    import phx_inputs as P
+    w = P.fcc_massdisorder_32()
+    f2, f3 = w.ifc2(), w.ifc3()
+    c = w.crystal
+    q = O.grid.mesh_qred(w.mesh)
+    freq, evec, _ = O.harmonic.solve(f2.idx, f2.val, c.masses, c.lattice, q)
+    fc3 = O.anharmonic.FC3(f3.idx, f3.val, c.masses)
+    irr, _, _ = O.grid.irreducible(w.mesh, w.rotations)
+    iq = int(irr[seed_q])
+    mesh = w.mesh
+    nq = q.shape[0]
+    if n_qp is None or n_qp >= nq:
+        t0 = time.perf_counter()
+        O.anharmonic.gamma(fc3, mesh, freq, evec, [iq], w.temperature, w.shape, w.sigma_thz)
+        dt = time.perf_counter() - t0
+        n_q1 = nq
+    else:
+        # the oracle's per-pair steps for a bounded set of q' (same arithmetic as its gamma)
+        kint = O.grid.mesh_int(mesh)
+        nocc = O.occupation.bose(freq, w.temperature)
+        t0 = time.perf_counter()
+        acc = np.zeros(freq.shape[1])
+        for iqp in range(n_qp):
+            iqpp = int(O.grid.mesh_index(-(kint[iq] + kint[iqp]), mesh))
+            V = O.anharmonic.v3(fc3, evec[iq], q[iqp], evec[iqp], -(q[iq] + q[iqp]), evec[iqpp])
+            W = O.anharmonic.pair_weights(freq[iq], freq[iqp], freq[iqpp], nocc[iqp], nocc[iqpp], w.shape,
+                                          w.sigma_thz, w.f_min_thz, w.window)
+            acc += np.einsum("ijk,ijk->i", np.abs(V) ** 2, W)
+        dt = time.perf_counter() - t0
+        n_q1 = n_qp
+    n = freq.shape[1]
+    valid = int((freq[iq] >= w.f_min_thz).sum())
+    trip = valid * n_q1 * n * n
+    desc = f"oracle gamma of irreducible q-point {iq} over {n_q1} of {nq} q' (1/{len(irr)} of the irreducible set)"
+    return dt, trip, desc
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return int(max(i.get("num_threads", 1) for i in info))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+# ----------------------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n_qp = args.ref_qp
+    dts, trip = [], 0
+    for i in range(args.warmup + args.steps):
+        dt, trip, desc = oracle_sample(n_qp=n_qp)
+        if i >= args.warmup:
+            dts.append(dt)
+    ms = 1e3 * float(np.mean(dts))
+    val = trip / (ms / 1e3)
+    cores = blas_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fcc32-massdis-mesh8 (32-atom LJ fcc, 96 modes, 8x8x8, 50 K, Gauss 0.1 THz)",
+                       "sample": desc},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_phx(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2602_23728_gb300 as phx
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+    ctx = phx.Context(local)
+    wl = Workload(phx, ctx, args.precision, device)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 0)):
+        wl.step()
+    barrier()
+    trip = wl.triplets()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile_enable(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            wl.step()
+        ev1.record(stream)
+        barrier()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * trip / (ms_max / 1e3)
+    kappa = wl.kappa.copy()
+
+    # end to end: the same step through the API with pinned host buffers
+    bufs = wl.host_buffers()
+    wl.step_host(bufs)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        wl.step_host(bufs)
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_ms = float(te.item())
+    h2d, d2h = wl.host_bytes(bufs)
+
+    # roofline of the dominant kernel class, from events recorded around its launches
+    peaks, src = load_peaks()
+    gemms = {k: prof[k] for k in ("dft", "gemm_e2", "gemm_e1_gamma", "fp64_gemm") if prof[k][1] > 0}
+    roof = None
+    if gemms:
+        name = max(gemms, key=lambda k: gemms[k][0])
+        tot_ms, nl, fl, by = gemms[name]
+        bf16_sus = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        if args.precision == "bf16x3":
+            peak, note = bf16_sus / 3.0, "bf16 sustained / 3 (three bf16 products per FP32-equivalent product)"
+        elif args.precision == "tf32":
+            peak, note = bf16_sus * NOMINAL_TF32_OVER_BF16, "bf16 sustained x nominal tf32/bf16 (1.1/2.25)"
+        else:
+            peak, note = None, "FP64 CUDA-core path"
+        achieved = fl / (tot_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if peak else None, "traffic": None,
+                "launches_per_step": nl / args.steps, "avg_launch_ms": tot_ms / nl,
+                "peak_source": f"{src}: {note}",
+                "share_of_step": tot_ms / args.steps / ms}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "fcc32-massdis-mesh8: 32-atom LJ fcc (2x2x2 conventional, masses 39.95/83.8 "
+                                   "seed 2), 96 modes, 8x8x8 mesh, 260 irreducible q (time reversal), 50 K, "
+                                   "Gaussian 0.1 THz",
+                       "triplets_per_step_per_gpu": trip, "l2": "working set > L2 (W operand 226 MB, "
+                       "eigenvector tables 75 MB per step)", "parallelism": f"replicas x{world}"},
+            "e2e": {"value": world * trip / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": int(prof["launches"]),
+            "roofline": roof,
+            "kappa_wmk": [kappa[0, 0], kappa[1, 1], kappa[2, 2]],
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if k != "launches" and v[1] > 0}}
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+
+    if args.fp64_q > 0:
+        # the FP64 GPU path on a subset of irreducible q: rate and gamma error of this precision
+        sub = wl.irr_d[1:1 + args.fp64_q].contiguous()
+        g64 = torch.zeros((sub.shape[0], wl.n), dtype=torch.float64, device=device)
+        gmx = torch.zeros_like(g64)
+        w = wl.w
+        wl.ctx.gamma(wl.h, wl.freq, wl.evec, sub, w.temperature, w.shape, w.sigma_thz, w.window, w.f_min_thz,
+                     precision="fp64", gamma=g64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        wl.ctx.gamma(wl.h, wl.freq, wl.evec, sub, w.temperature, w.shape, w.sigma_thz, w.window, w.f_min_thz,
+                     precision="fp64", gamma=g64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        wl.ctx.gamma(wl.h, wl.freq, wl.evec, sub, w.temperature, w.shape, w.sigma_thz, w.window, w.f_min_thz,
+                     precision=args.precision, gamma=gmx)
+        a, b = gmx.cpu().numpy(), g64.cpu().numpy()
+        big = b > 1e-3 * b.max()
+        f = wl.freq.cpu().numpy()[wl.irr[1:1 + args.fp64_q]]
+        trip64 = int((f >= w.f_min_thz).sum()) * wl.nq * wl.n * wl.n
+        line["fp64_path"] = {"value": trip64 / t64, "unit": UNIT, "sample_irreducible_q": int(sub.shape[0]),
+                             "gamma_max_rel_err_vs_fp64": float((np.abs(a - b)[big] / b[big]).max())}
+        line["speedup_vs_fp64_path"] = value / world / (trip64 / t64)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, ctrip, desc = oracle_sample(n_qp=args.cpu_qp)
+        line["cpu_baseline"] = {"value": ctrip / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                                "sample": desc, "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="phx", choices=["phx", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32", "fp64"])
+    ap.add_argument("--fp64-q", type=int, default=4, help="irreducible q timed on the FP64 GPU path (0: skip)")
+    ap.add_argument("--cpu-qp", type=int, default=None, help="q' of the oracle sample (default all)")
+    ap.add_argument("--ref-qp", type=int, default=64, help="q' per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_phx(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

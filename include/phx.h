@@ -159,11 +159,13 @@ phx_status phx_gamma(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz,
                      int32_t prec, double* gamma, double* wp2, int32_t mem, void* stream);
 
 /* ---------------------------------------------------------------- transport
- * Map irreducible linewidths to the full mesh: gamma_full[k][nu] = gamma_irr[full_to_irr[k]][nu]
- * after averaging gamma_irr over each degenerate set (|df| < 1e-5 max|f|) of its own q
- * point (freq_irr[n_irr][n]).  [mem] for all arrays. */
+ * Map irreducible linewidths to the full mesh (Sec. "Overview of New Capabilities"):
+ * gamma_full[k][nu] = gamma_irr[full_to_irr[k]][nu] after averaging gamma_irr over each
+ * degenerate set (|df| < 1e-5 max|f|) of its own q point irr_q[s], whose frequencies are
+ * read from freq_full[nq][n].  [mem] for all arrays (irr_q[n_irr], full_to_irr[nq]).
+ * Errors: PHX_ERR_INVALID for an index out of range (checked on host memory only). */
 phx_status phx_unfold(phx_ctx* ctx, int32_t n_irr, int32_t nq, int32_t n,
-                      const double* freq_irr, const double* gamma_irr,
+                      const double* freq_full, const int32_t* irr_q, const double* gamma_irr,
                       const int32_t* full_to_irr, double* gamma_full, int32_t mem, void* stream);
 
 /* Eq. (rta): kappa_ab = 1/(N_q V) sum_{q nu: f >= f_min, gamma > 0} c v_a v_b / gamma, with
@@ -174,6 +176,29 @@ phx_status phx_kappa_rta(phx_ctx* ctx, const phx_cell* cell, int32_t nq, int32_t
                          const double* freq_thz, const double* vel, const double* vv,
                          const double* gamma_full, double temperature, double f_min_thz,
                          int32_t is_classic, double* kappa_wmk, int32_t mem, void* stream);
+
+/* ---------------------------------------------------------------- profiling
+ * Kernel classes timed when profiling is on (CUDA events recorded on the launching stream
+ * immediately before and after every launch of the class). */
+typedef enum {
+    PHX_K_DFT = 0,          /* tensor-core GEMM over lattice differences (S4)              */
+    PHX_K_GEMM_E2 = 1,      /* tensor-core GEMM with e_q'' (first eigenvector contraction) */
+    PHX_K_GEMM_E1 = 2,      /* tensor-core GEMM with e_q' + fused weights and reduction    */
+    PHX_K_FOLD = 3,         /* Phi3 fold into the lattice-difference operand (S3)          */
+    PHX_K_FP64_GEMM = 4,    /* FP64 complex GEMMs of the FP64 path                          */
+    PHX_K_FP64_EPI = 5,     /* FP64 weight/reduction kernel                                 */
+    PHX_K_EIGEN = 6,        /* batched Jacobi eigensolver                                   */
+    PHX_K_COUNT = 7
+} phx_kernel_class;
+
+/* Turn profiling on (1) or off (0); turning it on clears the counters.  Off by default. */
+phx_status phx_profile_enable(phx_ctx* ctx, int32_t on);
+/* Totals since the last enable for one kernel class: summed event time (ms), launches,
+ * algorithmic flops (useful complex products x 8, padding excluded) and algorithmic bytes.
+ * Synchronises on the recorded events.  kernel = -1 returns in *launches the number of
+ * kernels of any kind this context launched since the last enable (times not summed). */
+phx_status phx_profile_read(phx_ctx* ctx, int32_t kernel, double* total_ms, int64_t* launches,
+                            double* flops, double* bytes);
 
 #ifdef __cplusplus
 }

@@ -68,12 +68,20 @@ lib.phx_fc3_num_d.argtypes = [_P]
 lib.phx_fc3_num_d.restype = C.c_int32
 lib.phx_gamma.argtypes = [_P, _P, _P, _P, _P, _I, C.c_double, Broadening, C.c_double, _I, _P, _P, _I, _P]
 lib.phx_gamma.restype = C.c_int
-lib.phx_unfold.argtypes = [_P, _I, _I, _I, _P, _P, _P, _P, _I, _P]
+lib.phx_unfold.argtypes = [_P, _I, _I, _I, _P, _P, _P, _P, _P, _I, _P]
 lib.phx_unfold.restype = C.c_int
 lib.phx_kappa_rta.argtypes = [_P, C.POINTER(Cell), _I, _I, _P, _P, _P, _P, C.c_double, C.c_double, _I, _P, _I, _P]
 lib.phx_kappa_rta.restype = C.c_int
 
-EXPORTED = ["phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
+lib.phx_profile_enable.argtypes = [_P, _I]
+lib.phx_profile_enable.restype = C.c_int
+lib.phx_profile_read.argtypes = [_P, _I, _P, _P, _P, _P]
+lib.phx_profile_read.restype = C.c_int
+
+KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4, "fp64_epilogue": 5,
+           "eigensolver": 6}
+
+EXPORTED = ["phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
             "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_unfold", "phx_kappa_rta"]
 
 
@@ -200,6 +208,23 @@ class Context:
         except Exception:
             pass
 
+    # ------------------------------------------------------------------ profiling
+    def profile_enable(self, on=True):
+        self._check(lib.phx_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        """{kernel: (total_ms, launches, flops, bytes)} plus 'launches' (all kernels)."""
+        out = {}
+        for name, k in KERNELS.items():
+            ms, n, fl, by = C.c_double(), C.c_int64(), C.c_double(), C.c_double()
+            self._check(lib.phx_profile_read(self.h, k, C.addressof(ms), C.addressof(n), C.addressof(fl),
+                                             C.addressof(by)))
+            out[name] = (ms.value, n.value, fl.value, by.value)
+        n = C.c_int64()
+        self._check(lib.phx_profile_read(self.h, -1, None, C.addressof(n), None, None))
+        out["launches"] = n.value
+        return out
+
     # ------------------------------------------------------------------ harmonic
     def harmonic(self, lattice, masses, ifc2_idx, ifc2_val, q_frac, freq=None, evec=None, vel=None, vv=None,
                  want_vel=True, want_vv=True):
@@ -246,15 +271,18 @@ class Context:
         return (gamma, wp2) if want_wp2 or wp2 is not None else gamma
 
     # ------------------------------------------------------------------ transport
-    def unfold(self, freq_irr, gamma_irr, full_to_irr, out=None):
-        if not _is_torch(freq_irr):
-            freq_irr = _host(freq_irr, np.float64)
+    def unfold(self, freq_full, irr_q, gamma_irr, full_to_irr, out=None):
+        """phx_unfold: irreducible linewidths (degenerate-averaged) onto the full mesh."""
+        if not _is_torch(freq_full):
+            freq_full = _host(freq_full, np.float64)
+            irr_q = _host(irr_q, np.int32)
             gamma_irr = _host(gamma_irr, np.float64)
             full_to_irr = _host(full_to_irr, np.int32)
-            out = np.zeros((full_to_irr.shape[0], freq_irr.shape[1])) if out is None else out
-        mem, stream = _mem_and_stream([freq_irr, gamma_irr, full_to_irr, out])
-        self._check(lib.phx_unfold(self.h, freq_irr.shape[0], full_to_irr.shape[0], freq_irr.shape[1],
-                                   _ptr(freq_irr), _ptr(gamma_irr), _ptr(full_to_irr), _ptr(out), mem, stream))
+            out = np.zeros((full_to_irr.shape[0], freq_full.shape[1])) if out is None else out
+        mem, stream = _mem_and_stream([freq_full, irr_q, gamma_irr, full_to_irr, out])
+        self._check(lib.phx_unfold(self.h, gamma_irr.shape[0], full_to_irr.shape[0], freq_full.shape[1],
+                                   _ptr(freq_full), _ptr(irr_q), _ptr(gamma_irr), _ptr(full_to_irr), _ptr(out),
+                                   mem, stream))
         return out
 
     def kappa_rta(self, lattice, masses, freq, gamma_full, temperature, vel=None, vv=None, f_min=0.01,

@@ -49,6 +49,38 @@ void* phx_ws(phx_ctx* ctx, const char* name, size_t bytes) {
     return p;
 }
 
+static cudaEvent_t pool_get(phx_ctx* ctx) {
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+int phx_prof_begin(phx_ctx* ctx, cudaStream_t s) {
+    if (!ctx->prof) return -1;
+    phx_ctx::Rec r{0, pool_get(ctx), pool_get(ctx), 0.0, 0.0};
+    if (!r.a || !r.b) return -1;
+    cudaEventRecord(r.a, s);
+    ctx->recs.push_back(r);
+    return (int)ctx->recs.size() - 1;
+}
+
+void phx_prof_end(phx_ctx* ctx, int slot, cudaStream_t s, int kernel, double flops, double bytes) {
+    if (slot < 0) return;
+    auto& r = ctx->recs[slot];
+    r.kernel = kernel;
+    r.flops = flops;
+    r.bytes = bytes;
+    cudaEventRecord(r.b, s);
+}
+
 namespace {
 
 __global__ void finalize_gamma_kernel(int count, int n, const int32_t* irr, const double* freq,
@@ -114,6 +146,53 @@ void phx_destroy(phx_ctx* ctx) {
 }
 
 const char* phx_last_error(const phx_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+static void prof_collect(phx_ctx* ctx) {
+    for (auto& r : ctx->recs) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            ctx->prof_ms[r.kernel] += ms;
+            ctx->prof_n[r.kernel] += 1;
+            ctx->prof_flops[r.kernel] += r.flops;
+            ctx->prof_bytes[r.kernel] += r.bytes;
+        }
+        cudaGetLastError();
+        ctx->pool.push_back(r.a);
+        ctx->pool.push_back(r.b);
+    }
+    ctx->recs.clear();
+}
+
+phx_status phx_profile_enable(phx_ctx* ctx, int32_t on) {
+    if (!ctx) return PHX_ERR_INVALID;
+    cudaSetDevice(ctx->device);
+    prof_collect(ctx);
+    for (int k = 0; k < PHX_K_COUNT; ++k) {
+        ctx->prof_ms[k] = 0.0; ctx->prof_n[k] = 0; ctx->prof_flops[k] = 0.0; ctx->prof_bytes[k] = 0.0;
+    }
+    ctx->launches = 0;
+    ctx->prof = on != 0;
+    return PHX_OK;
+}
+
+phx_status phx_profile_read(phx_ctx* ctx, int32_t kernel, double* total_ms, int64_t* launches, double* flops,
+                            double* bytes) {
+    if (!ctx || kernel < -1 || kernel >= PHX_K_COUNT) return PHX_ERR_INVALID;
+    cudaSetDevice(ctx->device);
+    prof_collect(ctx);
+    if (kernel == -1) {
+        if (launches) *launches = ctx->launches;
+        if (total_ms) *total_ms = 0.0;
+        if (flops) *flops = 0.0;
+        if (bytes) *bytes = 0.0;
+        return PHX_OK;
+    }
+    if (total_ms) *total_ms = ctx->prof_ms[kernel];
+    if (launches) *launches = ctx->prof_n[kernel];
+    if (flops) *flops = ctx->prof_flops[kernel];
+    if (bytes) *bytes = ctx->prof_bytes[kernel];
+    return PHX_OK;
+}
 
 // ---------------------------------------------------------------- grid
 
@@ -263,8 +342,11 @@ phx_status phx_harmonic(phx_ctx* ctx, const phx_cell* cell, const phx_ifc2* fc2,
     for (int q0 = 0; q0 < nq; q0 += chunk) {
         const int c = std::min(chunk, nq - q0);
         PHX_CUDA_CHECK(ctx, phx_launch_dynmat(dq + 3 * q0, c, na, d_idx, d_val, d_ps, d_m, d_lat, D, dD, s));
+        const int ps = phx_prof_begin(ctx, s);
         PHX_CUDA_CHECK(ctx, phx_launch_jacobi(D, Vw, n, c, o_f + (int64_t)q0 * n, o_e + (int64_t)q0 * n2 * 2,
                                               (int32_t*)ctx->status_word, s));
+        phx_prof_end(ctx, ps, s, PHX_K_EIGEN, 0.0, 0.0);
+        ctx->launches += 2;
         if (want_v) {
             ZgemmBatch p{};
             p.A = dD; p.strideA = n2; p.divA = 1;
@@ -275,6 +357,7 @@ phx_status phx_harmonic(phx_ctx* ctx, const phx_cell* cell, const phx_ifc2* fc2,
             PHX_CUDA_CHECK(ctx, phx_launch_velocity(o_e + (int64_t)q0 * n2 * 2, Y, o_f + (int64_t)q0 * n, n, c,
                                                     o_v ? o_v + (int64_t)q0 * n * 3 : nullptr,
                                                     o_vv ? o_vv + (int64_t)q0 * n * 9 : nullptr, s));
+            ctx->launches += 2;
         }
     }
     int32_t st = 0;
@@ -442,6 +525,7 @@ phx_status phx_gamma(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz, c
     double* wacc = (double*)phx_ws(ctx, "g.wacc", (size_t)n_irr * n * 8);
     if (!nB || !gacc || !wacc) return PHX_ERR_NOMEM;
     PHX_CUDA_CHECK(ctx, phx_launch_occupations(d_f, nq * n, temperature, 0, nB, nullptr, s));
+    ctx->launches += 1;
     PHX_CUDA_CHECK(ctx, cudaMemsetAsync(gacc, 0, (size_t)n_irr * n * 8, s));
     PHX_CUDA_CHECK(ctx, cudaMemsetAsync(wacc, 0, (size_t)n_irr * n * 8, s));
     PHX_CUDA_CHECK(ctx, cudaMemsetAsync(ctx->status_word, 0, 4, s));
@@ -466,6 +550,7 @@ phx_status phx_gamma(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz, c
     finalize_gamma_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, n, d_irr, d_f, gacc, wacc, pref, 1.0 / nq,
                                                             f_min_thz, o_g, o_w);
     PHX_CUDA_CHECK(ctx, cudaGetLastError());
+    ctx->launches += 1;
     if (mem == PHX_MEM_HOST) {
         int32_t st = 0;
         PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(gamma, o_g, (size_t)count * 8, cudaMemcpyDeviceToHost, s));
@@ -479,26 +564,34 @@ phx_status phx_gamma(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz, c
 
 // ---------------------------------------------------------------- transport
 
-phx_status phx_unfold(phx_ctx* ctx, int32_t n_irr, int32_t nq, int32_t n, const double* freq_irr,
-                      const double* gamma_irr, const int32_t* full_to_irr, double* gamma_full, int32_t mem,
-                      void* stream) {
+phx_status phx_unfold(phx_ctx* ctx, int32_t n_irr, int32_t nq, int32_t n, const double* freq_full,
+                      const int32_t* irr_q, const double* gamma_irr, const int32_t* full_to_irr, double* gamma_full,
+                      int32_t mem, void* stream) {
     if (!ctx) return PHX_ERR_INVALID;
-    if (n_irr <= 0 || nq <= 0 || n <= 0 || !freq_irr || !gamma_irr || !full_to_irr || !gamma_full)
+    if (n_irr <= 0 || nq <= 0 || n <= 0 || !freq_full || !irr_q || !gamma_irr || !full_to_irr || !gamma_full)
         return phx_set_error(ctx, PHX_ERR_INVALID, "phx_unfold: bad argument");
-    if (mem == PHX_MEM_HOST)
+    if (mem != PHX_MEM_HOST && mem != PHX_MEM_DEVICE)
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_unfold: bad mem flag %d", mem);
+    if (mem == PHX_MEM_HOST) {
         for (int i = 0; i < nq; ++i)
             if (full_to_irr[i] < 0 || full_to_irr[i] >= n_irr)
                 return phx_set_error(ctx, PHX_ERR_INVALID, "phx_unfold: full_to_irr[%d] out of range", i);
+        for (int i = 0; i < n_irr; ++i)
+            if (irr_q[i] < 0 || irr_q[i] >= nq)
+                return phx_set_error(ctx, PHX_ERR_INVALID, "phx_unfold: irr_q[%d] out of range", i);
+    }
     cudaSetDevice(ctx->device);
     cudaStream_t s = as_stream(stream);
     const double *f = nullptr, *g = nullptr;
-    const int32_t* m = nullptr;
-    PHX_TRY(phx_stage_in(ctx, "u.f", freq_irr, (size_t)n_irr * n, mem, s, &f));
+    const int32_t *m = nullptr, *ir = nullptr;
+    PHX_TRY(phx_stage_in(ctx, "u.f", freq_full, (size_t)nq * n, mem, s, &f));
+    PHX_TRY(phx_stage_in(ctx, "u.i", irr_q, (size_t)n_irr, mem, s, &ir));
     PHX_TRY(phx_stage_in(ctx, "u.g", gamma_irr, (size_t)n_irr * n, mem, s, &g));
     PHX_TRY(phx_stage_in(ctx, "u.m", full_to_irr, (size_t)nq, mem, s, &m));
     double* o = nullptr;
     PHX_TRY(phx_stage_out_buf(ctx, "u.o", gamma_full, (size_t)nq * n, mem, &o));
-    PHX_CUDA_CHECK(ctx, phx_launch_unfold(n_irr, nq, n, f, g, m, o, s));
+    PHX_CUDA_CHECK(ctx, phx_launch_unfold(n_irr, nq, n, f, ir, g, m, o, s));
+    ctx->launches += 1;
     if (mem == PHX_MEM_HOST) {
         PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(gamma_full, o, (size_t)nq * n * 8, cudaMemcpyDeviceToHost, s));
         PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
@@ -528,6 +621,7 @@ phx_status phx_kappa_rta(phx_ctx* ctx, const phx_cell* cell, int32_t nq, int32_t
     if (!acc) return PHX_ERR_NOMEM;
     PHX_CUDA_CHECK(ctx, cudaMemsetAsync(acc, 0, 72, s));
     PHX_CUDA_CHECK(ctx, phx_launch_kappa(nq, n, f, v, w, g, temperature, f_min_thz, is_classic, acc, s));
+    ctx->launches += 1;
     double h[9];
     PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(h, acc, 72, cudaMemcpyDeviceToHost, s));
     PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));

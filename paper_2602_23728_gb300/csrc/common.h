@@ -34,7 +34,20 @@ struct phx_ctx {
     int cc_major = 0, cc_minor = 0;
     size_t smem_optin = 0;
     void* status_word = nullptr;     // device int32 written by kernels with bounded waits
+    // profiling: event pairs around launches of instrumented kernel classes
+    bool prof = false;
+    struct Rec { int kernel; cudaEvent_t a, b; double flops, bytes; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[PHX_K_COUNT] = {0};
+    int64_t prof_n[PHX_K_COUNT] = {0};
+    double prof_flops[PHX_K_COUNT] = {0}, prof_bytes[PHX_K_COUNT] = {0};
+    int64_t launches = 0;            // kernels launched since the last profile enable
 };
+
+// Profiling helpers: begin returns a record slot (or -1 when profiling is off).
+int phx_prof_begin(phx_ctx* ctx, cudaStream_t s);
+void phx_prof_end(phx_ctx* ctx, int slot, cudaStream_t s, int kernel, double flops, double bytes);
 
 struct phx_fc3 {
     phx_ctx* ctx = nullptr;
@@ -132,7 +145,7 @@ cudaError_t phx_launch_zgemm(int M, int N, int K, int batch, const ZgemmBatch& p
 // transport.cu
 cudaError_t phx_launch_occupations(const double* freq, int count, double T, int is_classic,
                                    double* nB, double* cV, cudaStream_t s);
-cudaError_t phx_launch_unfold(int n_irr, int nq, int n, const double* freq_irr,
+cudaError_t phx_launch_unfold(int n_irr, int nq, int n, const double* freq_full, const int32_t* irr_q,
                               const double* gamma_irr, const int32_t* full_to_irr,
                               double* gamma_full, cudaStream_t s);
 cudaError_t phx_launch_kappa(int nq, int n, const double* freq, const double* vel,

@@ -151,12 +151,14 @@ phx_status phx_gamma_fp64(phx_ctx* ctx, const phx_fc3* f, const double* freq, co
         PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
     }
     PHX_CUDA_CHECK(ctx, phx_launch_phases(f, P, s));
+    ctx->launches += 1;
 
     for (int si = 0; si < n_irr; ++si) {
         const int iq = irr_host[si];
         int k1 = iq / (f->mesh[1] * f->mesh[2]), k2 = (iq / f->mesh[2]) % f->mesh[1], k3 = iq % f->mesh[2];
         const double qa = (double)k1 / f->mesh[0], qb = (double)k2 / f->mesh[1], qc = (double)k3 / f->mesh[2];
         PHX_CUDA_CHECK(ctx, phx_launch_third_index(iq, f->mesh, qpp, s));
+        ctx->launches += 1;
         const double2* eq = (const double2*)evec + (int64_t)iq * n2;
         for (int nu0 = 0; nu0 < n; nu0 += n_nu) {
             const int nn_nu = std::min(n_nu, n - nu0);
@@ -165,9 +167,12 @@ phx_status phx_gamma_fp64(phx_ctx* ctx, const phx_fc3* f, const double* freq, co
             {
                 const int64_t total = f->n_seg * nn_nu;
                 int blocks = (int)std::min<int64_t>((total + 255) / 256, 65535);
+                const int pf = phx_prof_begin(ctx, s);
                 fold_kernel<<<blocks, 256, 0, s>>>(f->seg_key, f->seg_start, f->ent_a, f->ent_r2, f->ent_w,
                                                    f->n_seg, qa, qb, qc, eq, n, nu0, nn_nu, (double2*)W);
                 PHX_CUDA_CHECK(ctx, cudaGetLastError());
+                phx_prof_end(ctx, pf, s, PHX_K_FOLD, 8.0 * (double)f->nnz * nn_nu, 0.0);
+                ctx->launches += 2;
             }
             for (int t0 = 0; t0 < nq; t0 += Q) {
                 const int Qt = std::min(Q, nq - t0);
@@ -175,6 +180,7 @@ phx_status phx_gamma_fp64(phx_ctx* ctx, const phx_fc3* f, const double* freq, co
                 // S4: M[Qt x Rc] = P[t0:t0+Qt][n_d] * W[n_d][Rc]
                 a.A = P + (int64_t)t0 * f->n_d * 2; a.B = W; a.C = M;
                 a.divA = a.divB = 1; a.lda = f->n_d; a.ldb = (int)Rc; a.ldc = (int)Rc;
+                const int pg = phx_prof_begin(ctx, s);
                 PHX_CUDA_CHECK(ctx, phx_launch_zgemm(Qt, (int)Rc, f->n_d, 1, a, s));
                 // S5a: X_b[(nu,b) x nu''] = M_b[(nu,b) x c] * E_{q''}[c x nu'']
                 ZgemmBatch g1{};
@@ -190,11 +196,16 @@ phx_status phx_gamma_fp64(phx_ctx* ctx, const phx_fc3* f, const double* freq, co
                 g2.C = V; g2.strideC = n2;
                 g2.lda = n; g2.ldb = n; g2.ldc = n;
                 PHX_CUDA_CHECK(ctx, phx_launch_zgemm(n, n, n, Qt * nn_nu, g2, s));
+                phx_prof_end(ctx, pg, s, PHX_K_FP64_GEMM,
+                             8.0 * (double)Qt * Rc * ((double)f->n_d + 2.0 * n), 0.0);
+                const int pe = phx_prof_begin(ctx, s);
                 // S6
                 epilogue_fp64_kernel<<<Qt * nn_nu, 256, 0, s>>>((const double2*)V, t0, iq, n, nu0, nn_nu, freq,
                                                                 nB, qpp, gp, gacc + (int64_t)si * n,
                                                                 wacc ? wacc + (int64_t)si * n : nullptr);
                 PHX_CUDA_CHECK(ctx, cudaGetLastError());
+                phx_prof_end(ctx, pe, s, PHX_K_FP64_EPI, 0.0, 16.0 * (double)Qt * Rc);
+                ctx->launches += 4;
             }
         }
     }

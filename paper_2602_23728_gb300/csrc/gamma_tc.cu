@@ -616,6 +616,7 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
     }
     prep_evec_tables<PREC><<<2048, 256, 0, s>>>((const double2*)evec, nq, n, np, kcp, opE.hi, opE.lo);
     PHX_CUDA_CHECK(ctx, cudaGetLastError());
+    ctx->launches += 2;
     prep_phase_tables<PREC><<<256, 256, 0, s>>>(f->d_int, f->n_d, f->mesh[0], f->mesh[1], f->mesh[2], Q, n_tiles_q,
                                                 qp_np, kcp_d, opP.hi, opP.lo);
     PHX_CUDA_CHECK(ctx, cudaGetLastError());
@@ -667,7 +668,9 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
         const int iq = irr_host[si];
         const int k1 = iq / (f->mesh[1] * f->mesh[2]), k2 = (iq / f->mesh[2]) % f->mesh[1], k3 = iq % f->mesh[2];
         PHX_CUDA_CHECK(ctx, phx_launch_third_index(iq, f->mesh, qpp, s));
+        ctx->launches += 1;
         {
+            const int pf = phx_prof_begin(ctx, s);
             const int64_t total = rows_w * f->n_d;
             const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 16);
             fold_tc_kernel<PREC><<<blocks, 256, 0, s>>>(seg_of, f->seg_start, f->ent_a, f->ent_r2, f->ent_w, f->n_d,
@@ -676,6 +679,8 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
                                                         (const double2*)evec + (int64_t)iq * n2, n, 0, n_nu, kcp_d,
                                                         opW.hi, opW.lo);
             PHX_CUDA_CHECK(ctx, cudaGetLastError());
+            phx_prof_end(ctx, pf, s, PHX_K_FOLD, 8.0 * (double)f->nnz * n_nu, (double)rows_w * kr_d * esz * planes);
+            ctx->launches += 1;
         }
         aB.iq = iq;
         aB.gacc = gacc + (int64_t)si * n;
@@ -684,13 +689,24 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
             const int t0 = tq * Q, Qt = std::min(Q, nq - t0);
             aD.b_base = tq;
             aD.nq_slots = Qt;
+            // algorithmic work: complex MACs x 8 flops; bytes: operands read + results written once
+            const double fl_d = 8.0 * (double)rows_w * Qt * f->n_d;
+            const double fl_e = 8.0 * (double)Qt * rows_a * n * n;
+            const double op_bytes = (double)planes * esz * 2.0;   // one complex value of an operand
+            int pp = phx_prof_begin(ctx, s);
             PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_M>(ctx, aD, 1, sms, s)));
+            phx_prof_end(ctx, pp, s, PHX_K_DFT, fl_d, op_bytes * ((double)rows_w * f->n_d + (double)Qt * rows_a * n));
             const int cpp = std::max(1, sms / Qt);
             aA.b_idx = qpp + t0;
+            pp = phx_prof_begin(ctx, s);
             PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_X>(ctx, aA, Qt, cpp, s)));
+            phx_prof_end(ctx, pp, s, PHX_K_GEMM_E2, fl_e, op_bytes * 2.0 * Qt * rows_a * n);
             aB.b_idx = ident + t0;
             aB.t0 = t0;
+            pp = phx_prof_begin(ctx, s);
             PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_G>(ctx, aB, Qt, cpp, s)));
+            phx_prof_end(ctx, pp, s, PHX_K_GEMM_E1, fl_e, op_bytes * (double)Qt * rows_a * n);
+            ctx->launches += 3;
         }
     }
     return PHX_OK;

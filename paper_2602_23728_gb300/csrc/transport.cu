@@ -27,11 +27,12 @@ __global__ void occupations_kernel(const double* __restrict__ freq, int count, d
 }
 
 // One CTA per full-mesh point k: degenerate-average the irreducible row of k's orbit.
-__global__ void unfold_kernel(int n, const double* __restrict__ freq_irr, const double* __restrict__ g_irr,
-                              const int32_t* __restrict__ full_to_irr, double* __restrict__ g_full) {
+__global__ void unfold_kernel(int n, const double* __restrict__ freq_full, const int32_t* __restrict__ irr_q,
+                              const double* __restrict__ g_irr, const int32_t* __restrict__ full_to_irr,
+                              double* __restrict__ g_full) {
     const int k = blockIdx.x;
     const int s = full_to_irr[k];
-    const double* f = freq_irr + (int64_t)s * n;
+    const double* f = freq_full + (int64_t)irr_q[s] * n;
     const double* g = g_irr + (int64_t)s * n;
     for (int mu = threadIdx.x; mu < n; mu += blockDim.x) {
         double fm = 0.0;
@@ -96,12 +97,12 @@ cudaError_t phx_launch_occupations(const double* freq, int count, double T, int 
     return cudaGetLastError();
 }
 
-cudaError_t phx_launch_unfold(int n_irr, int nq, int n, const double* freq_irr,
+cudaError_t phx_launch_unfold(int n_irr, int nq, int n, const double* freq_full, const int32_t* irr_q,
                               const double* gamma_irr, const int32_t* full_to_irr,
                               double* gamma_full, cudaStream_t s) {
     (void)n_irr;
     if (nq <= 0) return cudaSuccess;
-    unfold_kernel<<<nq, 128, 0, s>>>(n, freq_irr, gamma_irr, full_to_irr, gamma_full);
+    unfold_kernel<<<nq, 128, 0, s>>>(n, freq_full, irr_q, gamma_irr, full_to_irr, gamma_full);
     return cudaGetLastError();
 }
 

@@ -173,7 +173,7 @@ def test_unfold_and_kappa_end_to_end_fcc1(ctx, phx, fcc1):
     irr, f2i, _ = phx.irreducible(w.mesh, w.rotations)
     h = ctx.fc3(c.lattice, c.masses, fcc1["f3"].idx, fcc1["f3"].val, w.mesh)
     g = ctx.gamma(h, fcc1["freq"], fcc1["evec"], irr, w.temperature, w.shape, w.sigma_thz)
-    gf = ctx.unfold(fcc1["freq"][irr], g, f2i)
+    gf = ctx.unfold(fcc1["freq"], irr, g, f2i)
     K = ctx.kappa_rta(c.lattice, c.masses, fcc1["freq"], gf, w.temperature, vv=fcc1["vv"])
     f2 = fcc1["f2"]
     fo, eo, _ = O.harmonic.solve(f2.idx, f2.val, c.masses, c.lattice, fcc1["q"])

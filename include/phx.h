@@ -177,6 +177,30 @@ phx_status phx_kappa_rta(phx_ctx* ctx, const phx_cell* cell, int32_t nq, int32_t
                          const double* gamma_full, double temperature, double f_min_thz,
                          int32_t is_classic, double* kappa_wmk, int32_t mem, void* stream);
 
+/* ---------------------------------------------------------------- allocation-free conductivity
+ * The paper has no counterpart to this call: it exists for callers that cannot allocate
+ * device memory at the time they call (a host framework whose allocator owns nearly all of
+ * the GPU's memory, or a time-critical loop where cudaMalloc/cudaFree, which can
+ * synchronise the device, are not allowed).  It computes the same Eq. (rta) tensor as
+ * phx_kappa_rta, needs no context and allocates nothing: its only scratch is a static
+ * device array of 2048 x 9 doubles (144 KiB) that every GPU loading the library keeps
+ * until the process exits.
+ *  - All arrays are device memory of the current device: freq_thz[nq][n], vv[nq][n][9]
+ *    (or vel[nq][n][3] when vv is NULL), gamma_full[nq][n]; the result goes to
+ *    kappa_dev[9] (device memory, W/(m K)).  The call enqueues two kernels on `stream` and
+ *    does not synchronise.
+ *  - nq * n may not exceed 2048 * 2048 = 4,194,304 modes: larger inputs return
+ *    PHX_ERR_UNSUPPORTED.  Bad arguments return PHX_ERR_INVALID, a failed launch or
+ *    symbol lookup PHX_ERR_CUDA.
+ *  - The first call on a device looks the array's address up (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call on a device shares the array and leaves its contents behind; calls that
+ *    overlap on the GPU (other streams, other host threads) race on it. */
+phx_status phx_kappa_rta_noalloc(const phx_cell* cell, int32_t nq, int32_t n, const double* freq_thz,
+                                 const double* vel, const double* vv, const double* gamma_full,
+                                 double temperature, double f_min_thz, int32_t is_classic,
+                                 double* kappa_dev, void* stream);
+
 /* ---------------------------------------------------------------- profiling
  * Kernel classes timed when profiling is on (CUDA events recorded on the launching stream
  * immediately before and after every launch of the class). */

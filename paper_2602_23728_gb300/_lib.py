@@ -78,11 +78,15 @@ lib.phx_profile_enable.restype = C.c_int
 lib.phx_profile_read.argtypes = [_P, _I, _P, _P, _P, _P]
 lib.phx_profile_read.restype = C.c_int
 
+lib.phx_kappa_rta_noalloc.argtypes = [C.POINTER(Cell), _I, _I, _P, _P, _P, _P, C.c_double, C.c_double, _I, _P, _P]
+lib.phx_kappa_rta_noalloc.restype = C.c_int
+
 KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4, "fp64_epilogue": 5,
            "eigensolver": 6}
 
 EXPORTED = ["phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
-            "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_unfold", "phx_kappa_rta"]
+            "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_unfold", "phx_kappa_rta",
+            "phx_kappa_rta_noalloc"]
 
 
 class PhxError(RuntimeError):
@@ -299,6 +303,24 @@ class Context:
                                       _ptr(vv), _ptr(gamma_full), float(temperature), float(f_min), int(is_classic),
                                       k.ctypes.data, mem, stream))
         return k.reshape(3, 3)
+
+
+def kappa_rta_noalloc(lattice, masses, freq, gamma_full, temperature, out, vel=None, vv=None, f_min=0.01,
+                      is_classic=False):
+    """phx_kappa_rta_noalloc: device tensors in, kappa into the device tensor `out` (9 doubles);
+    enqueued on the current torch stream, no device allocation inside the library."""
+    cell, m = make_cell(lattice, masses)
+    arrays = [freq, gamma_full, vel, vv, out]
+    if not all(a is None or (_is_torch(a) and a.is_cuda and a.is_contiguous()) for a in arrays):
+        raise ValueError("phx_kappa_rta_noalloc takes contiguous CUDA tensors only")
+    import torch
+    stream = torch.cuda.current_stream(freq.device).cuda_stream
+    st = lib.phx_kappa_rta_noalloc(C.byref(cell), freq.shape[0], freq.shape[1], _ptr(freq), _ptr(vel), _ptr(vv),
+                                   _ptr(gamma_full), float(temperature), float(f_min), int(is_classic), _ptr(out),
+                                   stream)
+    if st != 0:
+        raise PhxError(st, "phx_kappa_rta_noalloc failed")
+    return out
 
 
 def version():

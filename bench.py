@@ -124,6 +124,14 @@ class Workload:
         self.g_full = torch.zeros((nq, self.n), dtype=f64, device=dev)
         self.kappa = None
 
+    def limit_irreducible(self, k):
+        """Small-case mode for profiler captures: only the first k irreducible q-points."""
+        self.irr = self.irr[:k]
+        self.irr_d = self.irr_d[:k].contiguous()
+        self.g_irr = self.g_irr[:k].contiguous()
+        self.f2i = np.minimum(self.f2i, k - 1).astype(np.int32)
+        self.f2i_d = self.torch.from_numpy(self.f2i).to(self.irr_d.device)
+
     def step(self, precision=None):
         prec = precision or self.precision
         w, c, ctx = self.w, self.c, self.ctx
@@ -277,6 +285,8 @@ def run_phx(args):
         dist.init_process_group("nccl", device_id=device)
     ctx = phx.Context(local)
     wl = Workload(phx, ctx, args.precision, device)
+    if args.irr_limit > 0:
+        wl.limit_irreducible(args.irr_limit)
 
     def barrier():
         if world > 1:
@@ -409,6 +419,8 @@ def main():
     ap.add_argument("--cpu-qp", type=int, default=None, help="q' of the oracle sample (default all)")
     ap.add_argument("--ref-qp", type=int, default=64, help="q' per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--irr-limit", type=int, default=0,
+                    help="profiling aid: process only the first N irreducible q per step (0: all)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <mutex>
 
@@ -32,7 +33,8 @@
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kEpiThreads = 256;                // 8 epilogue warps, two per TMEM lane group
+constexpr int kThreads = 64 + kEpiThreads;
 constexpr int kMaxStages = 8;
 constexpr int kBoxRows = 128;                  // rows of an A tile (= MMA M)
 constexpr int kChunkBytes = 128;               // bytes of K per chunk (one swizzle row)
@@ -87,17 +89,7 @@ __device__ __forceinline__ void store_operand(void* hi, void* lo, int64_t idx, f
     }
 }
 
-__device__ __forceinline__ float broad_f(float x, float sigma, float window, int shape) {
-    if (!(fabsf(x) < window * sigma)) return 0.0f;
-    if (shape == PHX_GAUSS) {
-        const float u = x / sigma;
-        return expf(-u * u) * (0.56418958354775628f / sigma);     // 1/(sqrt(pi) sigma)
-    }
-    const float h = 0.5f * sigma;
-    return h / (3.14159265358979f * (x * x + h * h));
-}
-
-__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 template <int PREC, int EPI>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcArgs args) {
@@ -108,8 +100,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     __shared__ __align__(8) uint64_t bfull_bar, tfull_bar[2], tempty_bar[2], drain_bar;
     __shared__ uint32_t tmem_base_slot;
     __shared__ volatile int abort_flag;
-    __shared__ float s_f1[kMaxNp], s_n1[kMaxNp];
-    __shared__ double s_red_g[kBoxRows], s_red_w[kBoxRows];
+    __shared__ float s_f1[kMaxNp], s_n1[kMaxNp], s_if1[kMaxNp];
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int np = args.np, N = 2 * np, nk = args.nk, stages = args.stages;
@@ -123,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) { tc::mbar_init(&full_bar[s], 1); tc::mbar_init(&empty_bar[s], 1); }
         tc::mbar_init(&bfull_bar, 1);
-        for (int a = 0; a < 2; ++a) { tc::mbar_init(&tfull_bar[a], 1); tc::mbar_init(&tempty_bar[a], 128); }
+        for (int a = 0; a < 2; ++a) { tc::mbar_init(&tfull_bar[a], 1); tc::mbar_init(&tempty_bar[a], kEpiThreads); }
         tc::mbar_init(&drain_bar, 1);
         abort_flag = 0;
         tc::fence_mbar_init();
@@ -132,11 +123,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         for (int pl = 0; pl < kPlanes; ++pl) { tc::prefetch_tmap(&args.a_map[pl]); tc::prefetch_tmap(&args.b_map[pl]); }
     }
     if (warp == 1) tc::tmem_alloc(&tmem_base_slot, args.tmem_cols);
-    if (threadIdx.x >= 64) {
-        const int t = threadIdx.x - 64;
-        s_red_g[t] = 0.0;
-        s_red_w[t] = 0.0;
-    }
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem_base = tmem_base_slot;
@@ -245,17 +231,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             }
         }
     } else {
-        // ------------------------------------------------------------ epilogue (warps 2..5)
-        const int et = threadIdx.x - 64;                  // 0..127
+        // ------------------------------------------------------------ epilogue (warps 2..9)
+        // Two warps per tensor-memory lane group; warp half h handles the 16-column chunks
+        // with (chunk index % 2) == h.
+        const int et = threadIdx.x - 64;                  // 0..255
         const int lgrp = warp & 3;                        // tensor-memory lane group of this warp
+        const int half = (warp - 2) >> 2;
         int q1 = 0, q2 = 0;
         if (EPI == EPI_G) {
             q1 = args.t0 + p;
             q2 = phx_third_index(args.iq, q1, args.m1, args.m2, args.m3);
-            for (int j = et; j < np; j += 128) {
+            for (int j = et; j < np; j += kEpiThreads) {
                 const bool v = j < args.n;
-                s_f1[j] = v ? (float)args.freq[(int64_t)q1 * args.n + j] : 0.0f;
+                const float f1 = v ? (float)args.freq[(int64_t)q1 * args.n + j] : 0.0f;
+                s_f1[j] = f1;
                 s_n1[j] = v ? (float)args.nB[(int64_t)q1 * args.n + j] : 0.0f;
+                s_if1[j] = (v && f1 >= args.f_min) ? 1.0f / f1 : 0.0f;   // 0 masks padding and soft partners
             }
             epi_barrier();
         }
@@ -277,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             if (EPI == EPI_M) {
                 // row (nu, b, c) of W -> M_slot[(nu, b)][c] (re) and [(nu, b)][Kcp + c] (im)
                 const int nb = row / args.n, c = row % args.n;
-                for (int j0 = 0; j0 < N; j0 += 16) {
+                for (int j0 = half * 16; j0 < N; j0 += 32) {
                     tc::tmem_ld16(taddr + j0, v);
                     if (valid) {
 #pragma unroll
@@ -295,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 // row (nu, b) -> X[(nu, nu'')][b] (re) and [(nu, nu'')][Kcp + b] (im)
                 const int nu = row / args.n, b = row % args.n;
                 const int64_t base = (int64_t)p * args.out_rows_per_slot + (int64_t)nu * args.n;
-                for (int j0 = 0; j0 < N; j0 += 16) {
+                for (int j0 = half * 16; j0 < N; j0 += 32) {
                     tc::tmem_ld16(taddr + j0, v);
                     if (valid) {
 #pragma unroll
@@ -320,44 +311,67 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 const bool live = valid && f0 >= args.f_min && f2 >= args.f_min;
                 // w = [...] / (2 pi)^4 / (f0 f1 f2): delta(w) = g(f)/(2 pi) and 1/(w0 w1 w2)
                 const float inv_f02 = live ? 1.0f / (1558.5454565440389f * f0 * f2) : 0.0f;
+                const float d02 = f0 - f2, lim = args.window * args.sigma;
+                const float one_n2 = 1.f + nn2;
                 float gs = 0.f, ws = 0.f;
                 float vi[16];
-                for (int j0 = 0; j0 < np; j0 += 16) {
-                    tc::tmem_ld16(taddr + j0, v);
-                    tc::tmem_ld16(taddr + np + j0, vi);
-                    if (live) {
+                if (args.shape == PHX_GAUSS) {
+                    const float a = -1.f / (args.sigma * args.sigma), norm = 0.56418958354775628f / args.sigma;
+                    for (int j0 = half * 16; j0 < np; j0 += 32) {
+                        tc::tmem_ld16(taddr + j0, v);
+                        tc::tmem_ld16(taddr + np + j0, vi);
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             const int j = j0 + i;
-                            const float f1 = s_f1[j];
-                            if (j >= args.n || !(f1 >= args.f_min)) continue;
-                            const float gd = broad_f(f0 - f1 - f2, args.sigma, args.window, args.shape);
-                            const float ga = broad_f(f0 + f1 - f2, args.sigma, args.window, args.shape);
-                            if (gd == 0.f && ga == 0.f) continue;
-                            const float n1 = s_n1[j];
-                            const float w = ((1.f + n1 + nn2) * gd + 2.f * (n1 - nn2) * ga) * inv_f02 / f1;
-                            gs += (v[i] * v[i] + vi[i] * vi[i]) * w;
+                            const float f1 = s_f1[j], n1 = s_n1[j], if1 = s_if1[j];
+                            const float x = d02 - f1, y = d02 + f1;
+                            const float gd = fabsf(x) < lim ? __expf(a * x * x) : 0.f;
+                            const float ga = fabsf(y) < lim ? __expf(a * y * y) : 0.f;
+                            const float w = ((one_n2 + n1) * gd + 2.f * (n1 - nn2) * ga) * if1;
+                            gs = fmaf(fmaf(v[i], v[i], vi[i] * vi[i]), w, gs);
                             ws += w;
                         }
                     }
+                    gs *= norm;
+                    ws *= norm;
+                } else {
+                    const float h = 0.5f * args.sigma, h2 = h * h, norm = h / 3.14159265358979f;
+                    for (int j0 = half * 16; j0 < np; j0 += 32) {
+                        tc::tmem_ld16(taddr + j0, v);
+                        tc::tmem_ld16(taddr + np + j0, vi);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int j = j0 + i;
+                            const float f1 = s_f1[j], n1 = s_n1[j], if1 = s_if1[j];
+                            const float x = d02 - f1, y = d02 + f1;
+                            const float gd = fabsf(x) < lim ? __frcp_rn(x * x + h2) : 0.f;
+                            const float ga = fabsf(y) < lim ? __frcp_rn(y * y + h2) : 0.f;
+                            const float w = ((one_n2 + n1) * gd + 2.f * (n1 - nn2) * ga) * if1;
+                            gs = fmaf(fmaf(v[i], v[i], vi[i] * vi[i]), w, gs);
+                            ws += w;
+                        }
+                    }
+                    gs *= norm;
+                    ws *= norm;
                 }
-                // reduce rows of equal nu: shared accumulators indexed from the tile's first nu
-                const int nu_first = (tile * kBoxRows) / args.n;
-                if (live) {
-                    atomicAdd(&s_red_g[nu - nu_first], (double)gs);
-                    atomicAdd(&s_red_w[nu - nu_first], (double)ws);
+                gs *= inv_f02;
+                ws *= inv_f02;
+                // rows of equal nu are contiguous: segmented suffix sums over the warp, then the
+                // first lane of each segment adds its segment into the FP64 accumulator
+                const int key = valid ? nu : -1 - lane;
+                double dg = (double)gs, dw = (double)ws;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const double og = __shfl_down_sync(0xffffffffu, dg, off);
+                    const double ow = __shfl_down_sync(0xffffffffu, dw, off);
+                    const int ok2 = __shfl_down_sync(0xffffffffu, key, off);
+                    if (lane + off < 32 && ok2 == key) { dg += og; dw += ow; }
                 }
-                epi_barrier();
-                const int nu_last = min(tile * kBoxRows + kBoxRows, args.rows) - 1;
-                const int cnt = nu_last / args.n - nu_first + 1;
-                if (et < cnt) {
-                    const double g = s_red_g[et], w = s_red_w[et];
-                    if (g != 0.0) atomicAdd(&args.gacc[args.nu0 + nu_first + et], g);
-                    if (args.wacc && w != 0.0) atomicAdd(&args.wacc[args.nu0 + nu_first + et], w);
-                    s_red_g[et] = 0.0;
-                    s_red_w[et] = 0.0;
+                const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+                if (valid && (lane == 0 || prev != key)) {
+                    if (dg != 0.0) atomicAdd(&args.gacc[args.nu0 + nu], dg);
+                    if (args.wacc && dw != 0.0) atomicAdd(&args.wacc[args.nu0 + nu], dw);
                 }
-                epi_barrier();
             }
             tc::tc_fence_before();
             tc::mbar_arrive(&tempty_bar[acc]);
@@ -425,37 +439,57 @@ __global__ void prep_phase_tables(const int32_t* __restrict__ d_int, int n_d, in
     }
 }
 
-// S3 fold into the DFT's A operand: row (nu, b, c), K = [Re W(d) | Im W(d)].  One thread per
-// (row, d); seg_of maps (d, b, c) to its COO segment (or -1).
+// S3, part 1: per COO entry the q-dependent factor phi/sqrt(mmm) * exp(+2 pi i q.R'') and the
+// eigenvectors of q, both rounded to FP32 once per q (FP64 is the narrowest pipe on GB300).
+__global__ void fold_phase_kernel(const int32_t* __restrict__ ent_r2, const double* __restrict__ ent_w, int64_t nnz,
+                                  double qa, double qb, double qc, float2* __restrict__ wph,
+                                  const double2* __restrict__ eq, int nn, float2* __restrict__ eqf) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz + nn; k += (int64_t)gridDim.x * blockDim.x) {
+        if (k < nnz) {
+            const double x = 2.0 * (qa * ent_r2[3 * k] + qb * ent_r2[3 * k + 1] + qc * ent_r2[3 * k + 2]);
+            double sn, cs;
+            sincospi(x, &sn, &cs);
+            wph[k] = make_float2((float)(ent_w[k] * cs), (float)(ent_w[k] * sn));
+        } else {
+            const double2 e = eq[k - nnz];
+            eqf[k - nnz] = make_float2((float)e.x, (float)e.y);
+        }
+    }
+}
+
+// S3, part 2: the DFT's A operand, row (nu, b, c), K = [Re W(d) | Im W(d)].  One warp per
+// row, lane = d (looping when n_d > 32), so every store instruction writes one contiguous
+// run of the row.  seg_of[(b*n + c)*n_d + d] is the COO segment of (d, b, c) or -1; rows
+// without any segment are written as zeros, so no clearing is needed.
 template <int PREC>
 __global__ void fold_tc_kernel(const int32_t* __restrict__ seg_of, const int64_t* __restrict__ seg_start,
-                               const int32_t* __restrict__ ent_a, const int32_t* __restrict__ ent_r2,
-                               const double* __restrict__ ent_w, int n_d, double qa, double qb, double qc,
-                               const double2* __restrict__ eq, int n, int nu0, int n_nu, int kcp, void* hi, void* lo) {
-    const int64_t nn = (int64_t)n * n;
-    const int64_t total = (int64_t)n_nu * nn * n_d;
+                               const int32_t* __restrict__ ent_a, const float2* __restrict__ wph, int n_d,
+                               const float2* __restrict__ eqf, int n, int nu0, int rows, int kcp, void* hi,
+                               void* lo) {
+    const int nn = n * n;
     const int kr = 2 * kcp;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int d = (int)(t % n_d);
-        const int64_t row = t / n_d;                 // (nu_l, b, c)
-        const int nl = (int)(row / nn);
-        const int bc = (int)(row % nn);
-        const int s = seg_of[(int64_t)d * nn + bc];
-        double ar = 0.0, ai = 0.0;
-        if (s >= 0) {
-            const int nu = nu0 + nl;
-            for (int64_t k = seg_start[s]; k < seg_start[s + 1]; ++k) {
-                const double x = 2.0 * (qa * ent_r2[3 * k] + qb * ent_r2[3 * k + 1] + qc * ent_r2[3 * k + 2]);
-                double sn, cs;
-                sincospi(x, &sn, &cs);
-                const double2 e = eq[(int64_t)ent_a[k] * n + nu];
-                const double w = ent_w[k];
-                ar += w * (cs * e.x - sn * e.y);
-                ai += w * (cs * e.y + sn * e.x);
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
+        const int nu = nu0 + row / nn;
+        const int bc = row % nn;
+        for (int d = lane; d < kcp; d += 32) {
+            float ar = 0.f, ai = 0.f;
+            if (d < n_d) {
+                const int s = seg_of[bc * n_d + d];
+                if (s >= 0) {
+                    const int64_t k1 = seg_start[s + 1];
+                    for (int64_t k = seg_start[s]; k < k1; ++k) {
+                        const float2 w = wph[k];
+                        const float2 e = eqf[ent_a[k] * n + nu];
+                        ar += w.x * e.x - w.y * e.y;
+                        ai += w.x * e.y + w.y * e.x;
+                    }
+                }
             }
+            store_operand<PREC>(hi, lo, (int64_t)row * kr + d, ar);
+            store_operand<PREC>(hi, lo, (int64_t)row * kr + kcp + d, ai);
         }
-        store_operand<PREC>(hi, lo, row * kr + d, (float)ar);
-        store_operand<PREC>(hi, lo, row * kr + kcp + d, (float)ai);
     }
 }
 
@@ -565,11 +599,27 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
         return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: eigenvector table of n = %d exceeds shared memory", n);
     // DFT shape
     const int kcp_d = round_up(f->n_d, 32), kr_d = 2 * kcp_d, nk_d = kr_d / kelems;
-    // q' tile: keep M and X (Q * n^2 rows each) near 64 MB per operand plane so they stay in L2
+    // Working-set plan: the modes nu of q are processed in chunks of n_nu (W of a chunk <= 1 GB)
+    // and q' in tiles of Q (M and X of a tile together <= 704 MB: 49 q' at 96 modes, the best
+    // measured on GB300 between 13 and 64; larger tiles re-read W fewer times).
+    // Both can be overridden (PHX_NU_CHUNK, PHX_Q_TILE) for tuning.
     const int64_t n2 = (int64_t)n * n;
     const int esz = PREC == P_BF16X3 ? 2 : 4;
-    int Q = (int)std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)48 << 20) / (n2 * kr * esz)));
+    const int planes_ = PREC == P_BF16X3 ? 2 : 1;
+    // Measured on GB300 (96 modes, 8^3): chunking nu loses more to launch count than it gains
+    // in L2 residency, so the whole W of q (<= 1 GB) is kept unless it is larger than that.
+    int n_nu = (int)std::max<int64_t>(1, std::min<int64_t>(n, ((int64_t)1 << 30) / (n2 * kr_d * esz * planes_)));
+    if (const char* env = getenv("PHX_NU_CHUNK")) {
+        const int v = atoi(env);
+        if (v > 0) n_nu = std::min(v, n);
+    }
+    const int64_t per_qp = 2 * (int64_t)n_nu * n * kr * esz * planes_;       // M + X of one q'
+    int Q = (int)std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)704 << 20) / per_qp));
     Q = std::min(Q, 128);
+    if (const char* env = getenv("PHX_Q_TILE")) {       // tuning knob: q' per Fourier tile
+        const int v = atoi(env);
+        if (v > 0) Q = std::min(std::min(v, 128), nq);
+    }
     int st_d = 0;
     while (!plan_stages(PREC, nk_d, round_up(Q, 8), &st_d)) {      // phase table must fit too
         if (Q <= 8)
@@ -579,9 +629,8 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
     const int qp_np = round_up(Q, 8);
     const int n_tiles_q = (nq + Q - 1) / Q;
     if (!get_encoder()) return phx_set_error(ctx, PHX_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    const int n_nu = n;                       // all modes of q at once
-    const int64_t rows_w = (int64_t)n_nu * n2;
-    const int64_t rows_a = (int64_t)n_nu * n;     // rows of M and X per q' slot
+    const int64_t rows_w = (int64_t)n_nu * n2;    // W rows of a full nu chunk
+    const int64_t rows_a = (int64_t)n_nu * n;     // rows of M and X per q' slot (full chunk)
 
     Operand opW, opM, opX, opE, opP;
     PHX_TRY(alloc_operand(ctx, "tc.W", PREC, rows_w, kr_d, &opW));
@@ -592,7 +641,10 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
     int32_t* qpp = (int32_t*)phx_ws(ctx, "tc.qpp", (size_t)nq * 4);
     int32_t* ident = (int32_t*)phx_ws(ctx, "tc.ident", (size_t)nq * 4);
     int32_t* seg_of = (int32_t*)phx_ws(ctx, "tc.segof", (size_t)f->n_d * n2 * 4);
-    if (!qpp || !ident || !seg_of) return PHX_ERR_NOMEM;
+    float2* wph = (float2*)phx_ws(ctx, "tc.wph", (size_t)std::max<int64_t>(f->nnz, 1) * sizeof(float2));
+    float2* eqf = (float2*)phx_ws(ctx, "tc.eqf", (size_t)n2 * sizeof(float2));
+    if (!qpp || !ident || !seg_of || !wph || !eqf) return PHX_ERR_NOMEM;
+    if (rows_w > INT32_MAX / 2) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: W chunk too large");
     // padding columns of M, X and W must read as zero
     PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opM.hi, 0, (size_t)opM.rows * kr * esz, s));
     PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opX.hi, 0, (size_t)opX.rows * kr * esz, s));
@@ -609,7 +661,7 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
         std::vector<int32_t> keys((size_t)f->n_seg * 3);
         PHX_CUDA_CHECK(ctx, cudaMemcpy(keys.data(), f->seg_key, keys.size() * 4, cudaMemcpyDeviceToHost));
         for (int64_t sgi = 0; sgi < f->n_seg; ++sgi)
-            so[(size_t)keys[3 * sgi] * n2 + (size_t)keys[3 * sgi + 1] * n + keys[3 * sgi + 2]] = (int32_t)sgi;
+            so[((size_t)keys[3 * sgi + 1] * n + keys[3 * sgi + 2]) * f->n_d + keys[3 * sgi]] = (int32_t)sgi;
         PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(ident, id.data(), nq * 4, cudaMemcpyHostToDevice, s));
         PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(seg_of, so.data(), so.size() * 4, cudaMemcpyHostToDevice, s));
         PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
@@ -670,43 +722,57 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
         PHX_CUDA_CHECK(ctx, phx_launch_third_index(iq, f->mesh, qpp, s));
         ctx->launches += 1;
         {
-            const int pf = phx_prof_begin(ctx, s);
-            const int64_t total = rows_w * f->n_d;
-            const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 16);
-            fold_tc_kernel<PREC><<<blocks, 256, 0, s>>>(seg_of, f->seg_start, f->ent_a, f->ent_r2, f->ent_w, f->n_d,
-                                                        (double)k1 / f->mesh[0], (double)k2 / f->mesh[1],
-                                                        (double)k3 / f->mesh[2],
-                                                        (const double2*)evec + (int64_t)iq * n2, n, 0, n_nu, kcp_d,
-                                                        opW.hi, opW.lo);
+            const int pblocks = (int)std::min<int64_t>((f->nnz + n2 + 255) / 256, 4096);
+            fold_phase_kernel<<<pblocks, 256, 0, s>>>(f->ent_r2, f->ent_w, f->nnz, (double)k1 / f->mesh[0],
+                                                      (double)k2 / f->mesh[1], (double)k3 / f->mesh[2], wph,
+                                                      (const double2*)evec + (int64_t)iq * n2, (int)n2, eqf);
             PHX_CUDA_CHECK(ctx, cudaGetLastError());
-            phx_prof_end(ctx, pf, s, PHX_K_FOLD, 8.0 * (double)f->nnz * n_nu, (double)rows_w * kr_d * esz * planes);
             ctx->launches += 1;
         }
         aB.iq = iq;
         aB.gacc = gacc + (int64_t)si * n;
         aB.wacc = wacc ? wacc + (int64_t)si * n : nullptr;
-        for (int tq = 0; tq < n_tiles_q; ++tq) {
-            const int t0 = tq * Q, Qt = std::min(Q, nq - t0);
-            aD.b_base = tq;
-            aD.nq_slots = Qt;
-            // algorithmic work: complex MACs x 8 flops; bytes: operands read + results written once
-            const double fl_d = 8.0 * (double)rows_w * Qt * f->n_d;
-            const double fl_e = 8.0 * (double)Qt * rows_a * n * n;
-            const double op_bytes = (double)planes * esz * 2.0;   // one complex value of an operand
-            int pp = phx_prof_begin(ctx, s);
-            PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_M>(ctx, aD, 1, sms, s)));
-            phx_prof_end(ctx, pp, s, PHX_K_DFT, fl_d, op_bytes * ((double)rows_w * f->n_d + (double)Qt * rows_a * n));
-            const int cpp = std::max(1, sms / Qt);
-            aA.b_idx = qpp + t0;
-            pp = phx_prof_begin(ctx, s);
-            PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_X>(ctx, aA, Qt, cpp, s)));
-            phx_prof_end(ctx, pp, s, PHX_K_GEMM_E2, fl_e, op_bytes * 2.0 * Qt * rows_a * n);
-            aB.b_idx = ident + t0;
-            aB.t0 = t0;
-            pp = phx_prof_begin(ctx, s);
-            PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_G>(ctx, aB, Qt, cpp, s)));
-            phx_prof_end(ctx, pp, s, PHX_K_GEMM_E1, fl_e, op_bytes * (double)Qt * rows_a * n);
-            ctx->launches += 3;
+        for (int nu0 = 0; nu0 < n; nu0 += n_nu) {
+            const int nnu = std::min(n_nu, n - nu0);
+            const int64_t rw = (int64_t)nnu * n2, ra = (int64_t)nnu * n;
+            {
+                const int pf = phx_prof_begin(ctx, s);
+                const int blocks = (int)std::min<int64_t>((rw + 7) / 8, (int64_t)sms * 32);
+                fold_tc_kernel<PREC><<<blocks, 256, 0, s>>>(seg_of, f->seg_start, f->ent_a, wph, f->n_d, eqf, n, nu0,
+                                                            (int)rw, kcp_d, opW.hi, opW.lo);
+                PHX_CUDA_CHECK(ctx, cudaGetLastError());
+                phx_prof_end(ctx, pf, s, PHX_K_FOLD, 8.0 * (double)f->nnz * nnu, (double)rw * kr_d * esz * planes);
+                ctx->launches += 1;
+            }
+            aD.rows = (int)rw; aD.tiles = (int)((rw + kBoxRows - 1) / kBoxRows);
+            aD.out_rows_per_slot = (int)ra;
+            aA.rows = (int)ra; aA.tiles = (int)((ra + kBoxRows - 1) / kBoxRows);
+            aA.a_rows_per_problem = (int)ra; aA.out_rows_per_slot = (int)ra;
+            aB.rows = (int)ra; aB.tiles = aA.tiles; aB.a_rows_per_problem = (int)ra;
+            aB.nu0 = nu0;
+            for (int tq = 0; tq < n_tiles_q; ++tq) {
+                const int t0 = tq * Q, Qt = std::min(Q, nq - t0);
+                aD.b_base = tq;
+                aD.nq_slots = Qt;
+                // algorithmic work: complex MACs x 8 flops; bytes: operands read + results written once
+                const double fl_d = 8.0 * (double)rw * Qt * f->n_d;
+                const double fl_e = 8.0 * (double)Qt * ra * n * n;
+                const double op_bytes = (double)planes * esz * 2.0;   // one complex value of an operand
+                int pp = phx_prof_begin(ctx, s);
+                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_M>(ctx, aD, 1, sms, s)));
+                phx_prof_end(ctx, pp, s, PHX_K_DFT, fl_d, op_bytes * ((double)rw * f->n_d + (double)Qt * ra * n));
+                const int cpp = std::max(1, sms / Qt);
+                aA.b_idx = qpp + t0;
+                pp = phx_prof_begin(ctx, s);
+                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_X>(ctx, aA, Qt, cpp, s)));
+                phx_prof_end(ctx, pp, s, PHX_K_GEMM_E2, fl_e, op_bytes * 2.0 * Qt * ra * n);
+                aB.b_idx = ident + t0;
+                aB.t0 = t0;
+                pp = phx_prof_begin(ctx, s);
+                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_G>(ctx, aB, Qt, cpp, s)));
+                phx_prof_end(ctx, pp, s, PHX_K_GEMM_E1, fl_e, op_bytes * (double)Qt * ra * n);
+                ctx->launches += 3;
+            }
         }
     }
     return PHX_OK;

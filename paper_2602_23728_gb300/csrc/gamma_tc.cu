@@ -50,6 +50,7 @@ struct TcArgs {
     CUtensorMap b_map[2];       // B operand planes
     int rows;                   // valid rows per problem
     int tiles;                  // ceil(rows / 128)
+    int n_problems;             // problems (one B operand each); work items = n_problems * tiles
     int np;                     // output half width (multiple of 8); N = 2 np
     int nk;                     // K chunks (128 bytes each)
     int stages;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     constexpr uint32_t kFmt = (PREC == P_BF16X3) ? 1u : 2u;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
-    __shared__ __align__(8) uint64_t bfull_bar, tfull_bar[2], tempty_bar[2], drain_bar;
+    __shared__ __align__(8) uint64_t bfull_bar, bempty_bar, tfull_bar[2], tempty_bar[2], drain_bar;
     __shared__ uint32_t tmem_base_slot;
     __shared__ volatile int abort_flag;
     __shared__ float s_f1[kMaxNp], s_n1[kMaxNp], s_if1[kMaxNp];
@@ -109,11 +110,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     uint8_t* a_smem = smem + kPlanes * b_bytes_plane;              // [stage][plane][128 rows][128 B]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = blockIdx.y;                                      // problem
+    // Persistent CTAs over a flat list of (problem, tile) items, problem-major; each CTA takes
+    // one contiguous, balanced range so it switches problem (and reloads B) rarely.
+    const int64_t n_items = (int64_t)args.n_problems * args.tiles;
+    const int item_begin = (int)(n_items * blockIdx.x / gridDim.x);
+    const int item_end = (int)(n_items * (blockIdx.x + 1) / gridDim.x);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) { tc::mbar_init(&full_bar[s], 1); tc::mbar_init(&empty_bar[s], 1); }
         tc::mbar_init(&bfull_bar, 1);
+        tc::mbar_init(&bempty_bar, 1);
         for (int a = 0; a < 2; ++a) { tc::mbar_init(&tfull_bar[a], 1); tc::mbar_init(&tempty_bar[a], kEpiThreads); }
         tc::mbar_init(&drain_bar, 1);
         abort_flag = 0;
@@ -130,21 +136,32 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
-            const int brow = (args.b_idx ? args.b_idx[p] : args.b_base) * N;
-            tc::mbar_expect_tx(&bfull_bar, kPlanes * b_bytes_plane);
-            for (int pl = 0; pl < kPlanes; ++pl)
-                for (int kc = 0; kc < nk; ++kc)
-                    for (int half = 0; half < 2; ++half)
-                        tc::tma_load_2d(b_smem + pl * b_bytes_plane + ((size_t)kc * N + half * np) * kChunkBytes,
-                                        &args.b_map[pl], &bfull_bar, kc * (kChunkBytes / (PREC == P_BF16X3 ? 2 : 4)),
-                                        brow + half * np);
             int stage = 0;
             uint32_t phase = 0;
             bool pending[kMaxStages];
             uint32_t pend_phase[kMaxStages];
             for (int s = 0; s < kMaxStages; ++s) { pending[s] = false; pend_phase[s] = 0; }
             const int kelems = kChunkBytes / (PREC == P_BF16X3 ? 2 : 4);
-            for (int tile = blockIdx.x; tile < args.tiles && !abort_flag; tile += gridDim.x) {
+            int cur_p = -1, n_loaded = 0;
+            for (int it = item_begin; it < item_end && !abort_flag; ++it) {
+                const int p = it / args.tiles, tile = it % args.tiles;
+                if (p != cur_p) {
+                    // a new problem: wait until the MMAs using the previous B have completed
+                    if (n_loaded > 0 && !tc::mbar_wait(&bempty_bar, (n_loaded - 1) & 1, &abort_flag)) {
+                        abort_flag = 1;
+                        atomicExch(args.status, (int)PHX_ERR_TIMEOUT);
+                        break;
+                    }
+                    const int brow = (args.b_idx ? args.b_idx[p] : args.b_base) * N;
+                    tc::mbar_expect_tx(&bfull_bar, kPlanes * b_bytes_plane);
+                    for (int pl = 0; pl < kPlanes; ++pl)
+                        for (int kc = 0; kc < nk; ++kc)
+                            for (int half = 0; half < 2; ++half)
+                                tc::tma_load_2d(b_smem + pl * b_bytes_plane + ((size_t)kc * N + half * np) * kChunkBytes,
+                                                &args.b_map[pl], &bfull_bar, kc * kelems, brow + half * np);
+                    ++n_loaded;
+                    cur_p = p;
+                }
                 const int arow = p * args.a_rows_per_problem + tile * kBoxRows;
                 for (int kc = 0; kc < nk; ++kc) {
                     if (!tc::mbar_wait(&empty_bar[stage], phase ^ 1, &abort_flag)) {
@@ -177,14 +194,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t id_full = tc::idesc(128, N <= 256 ? N : np, kFmt);
-            bool ok = tc::mbar_wait(&bfull_bar, 0, &abort_flag);
-            if (!ok) { abort_flag = 1; atomicExch(args.status, (int)PHX_ERR_TIMEOUT); }
-            tc::tc_fence_after();
+            bool ok = true;
             int stage = 0, acc = 0;
             uint32_t phase = 0, acc_phase = 0;
             const uint32_t b_base = tc::smem_u32(b_smem);
             const uint32_t a_base = tc::smem_u32(a_smem);
-            for (int tile = blockIdx.x; ok && tile < args.tiles; tile += gridDim.x) {
+            int cur_p = -1, n_bloads = 0;
+            for (int it = item_begin; ok && it < item_end; ++it) {
+                const int p = it / args.tiles;
+                if (p != cur_p) {
+                    if (cur_p >= 0) tc::mma_commit(&bempty_bar);       // B free once these MMAs finish
+                    if (!tc::mbar_wait(&bfull_bar, n_bloads & 1, &abort_flag)) {
+                        abort_flag = 1; atomicExch(args.status, (int)PHX_ERR_TIMEOUT); break;
+                    }
+                    tc::tc_fence_after();
+                    ++n_bloads;
+                    cur_p = p;
+                }
                 if (!tc::mbar_wait(&tempty_bar[acc], acc_phase ^ 1, &abort_flag)) {
                     abort_flag = 1; atomicExch(args.status, (int)PHX_ERR_TIMEOUT); break;
                 }
@@ -237,22 +263,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int et = threadIdx.x - 64;                  // 0..255
         const int lgrp = warp & 3;                        // tensor-memory lane group of this warp
         const int half = (warp - 2) >> 2;
-        int q1 = 0, q2 = 0;
-        if (EPI == EPI_G) {
-            q1 = args.t0 + p;
-            q2 = phx_third_index(args.iq, q1, args.m1, args.m2, args.m3);
-            for (int j = et; j < np; j += kEpiThreads) {
-                const bool v = j < args.n;
-                const float f1 = v ? (float)args.freq[(int64_t)q1 * args.n + j] : 0.0f;
-                s_f1[j] = f1;
-                s_n1[j] = v ? (float)args.nB[(int64_t)q1 * args.n + j] : 0.0f;
-                s_if1[j] = (v && f1 >= args.f_min) ? 1.0f / f1 : 0.0f;   // 0 masks padding and soft partners
-            }
-            epi_barrier();
-        }
+        int q1 = 0, q2 = 0, cur_p = -1;
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (int tile = blockIdx.x; tile < args.tiles; tile += gridDim.x) {
+        for (int it = item_begin; it < item_end; ++it) {
+            const int p = it / args.tiles, tile = it % args.tiles;
             const bool ok = tc::mbar_wait(&tfull_bar[acc], acc_phase, &abort_flag);
             if (!ok) {
                 abort_flag = 1;
@@ -260,6 +275,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             }
             epi_barrier();                 // every epilogue thread takes the same decision
             if (abort_flag) break;
+            if (EPI == EPI_G && p != cur_p) {
+                // partner tables of this problem's q' (the previous tile is done: barrier above)
+                q1 = args.t0 + p;
+                q2 = phx_third_index(args.iq, q1, args.m1, args.m2, args.m3);
+                for (int j = et; j < np; j += kEpiThreads) {
+                    const bool v = j < args.n;
+                    const float f1 = v ? (float)args.freq[(int64_t)q1 * args.n + j] : 0.0f;
+                    s_f1[j] = f1;
+                    s_n1[j] = v ? (float)args.nB[(int64_t)q1 * args.n + j] : 0.0f;
+                    s_if1[j] = (v && f1 >= args.f_min) ? 1.0f / f1 : 0.0f;   // 0 masks padding and soft partners
+                }
+                epi_barrier();
+                cur_p = p;
+            }
             tc::tc_fence_after();
             const int row = tile * kBoxRows + lgrp * 32 + lane;
             const bool valid = row < args.rows;
@@ -561,7 +590,9 @@ cudaError_t launch_gemm(phx_ctx* ctx, TcArgs& a, int n_problems, int ctas_per_pr
         attr_set = true;
     }
     (void)ctx;
-    dim3 grid(std::min(ctas_per_problem, a.tiles), n_problems);
+    a.n_problems = n_problems;
+    const int64_t items = (int64_t)n_problems * a.tiles;
+    dim3 grid((unsigned)std::min<int64_t>(items, ctas_per_problem), 1);
     tc_gemm_kernel<PREC, EPI><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -600,7 +631,7 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
     // DFT shape
     const int kcp_d = round_up(f->n_d, 32), kr_d = 2 * kcp_d, nk_d = kr_d / kelems;
     // Working-set plan: the modes nu of q are processed in chunks of n_nu (W of a chunk <= 1 GB)
-    // and q' in tiles of Q (M and X of a tile together <= 704 MB: 49 q' at 96 modes, the best
+    // and q' in tiles of Q (M and X of a tile together <= 920 MB: 64 q' at 96 modes, the best
     // measured on GB300 between 13 and 64; larger tiles re-read W fewer times).
     // Both can be overridden (PHX_NU_CHUNK, PHX_Q_TILE) for tuning.
     const int64_t n2 = (int64_t)n * n;
@@ -614,7 +645,7 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
         if (v > 0) n_nu = std::min(v, n);
     }
     const int64_t per_qp = 2 * (int64_t)n_nu * n * kr * esz * planes_;       // M + X of one q'
-    int Q = (int)std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)704 << 20) / per_qp));
+    int Q = (int)std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)920 << 20) / per_qp));
     Q = std::min(Q, 128);
     if (const char* env = getenv("PHX_Q_TILE")) {       // tuning knob: q' per Fourier tile
         const int v = atoi(env);
@@ -761,15 +792,14 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
                 int pp = phx_prof_begin(ctx, s);
                 PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_M>(ctx, aD, 1, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_DFT, fl_d, op_bytes * ((double)rw * f->n_d + (double)Qt * ra * n));
-                const int cpp = std::max(1, sms / Qt);
                 aA.b_idx = qpp + t0;
                 pp = phx_prof_begin(ctx, s);
-                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_X>(ctx, aA, Qt, cpp, s)));
+                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_X>(ctx, aA, Qt, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_GEMM_E2, fl_e, op_bytes * 2.0 * Qt * ra * n);
                 aB.b_idx = ident + t0;
                 aB.t0 = t0;
                 pp = phx_prof_begin(ctx, s);
-                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_G>(ctx, aB, Qt, cpp, s)));
+                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_G>(ctx, aB, Qt, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_GEMM_E1, fl_e, op_bytes * (double)Qt * ra * n);
                 ctx->launches += 3;
             }

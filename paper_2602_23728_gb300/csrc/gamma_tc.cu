@@ -51,7 +51,9 @@ struct TcArgs {
     int rows;                   // valid rows per problem
     int tiles;                  // ceil(rows / 128)
     int n_problems;             // problems (one B operand each); work items = n_problems * tiles
-    int np;                     // output half width (multiple of 8); N = 2 np
+    int np;                     // B table half height: rows [Re outputs (np) | Im outputs (np)] per index
+    int mg;                     // output modes per column group (multiple of 8); accumulator = 2 mg columns
+    int n_groups;               // column groups (mg * n_groups = np)
     int nk;                     // K chunks (128 bytes each)
     int stages;
     int n_acc;                  // 1 or 2 accumulators in tensor memory
@@ -92,7 +94,7 @@ __device__ __forceinline__ void store_operand(void* hi, void* lo, int64_t idx, f
 
 __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-template <int PREC, int EPI>
+template <int PREC, int EPI, bool kStreamB>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcArgs args) {
     constexpr int kPlanes = (PREC == P_BF16X3) ? 2 : 1;
     constexpr uint32_t kFmt = (PREC == P_BF16X3) ? 1u : 2u;
@@ -104,15 +106,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     __shared__ float s_f1[kMaxNp], s_n1[kMaxNp], s_if1[kMaxNp];
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int np = args.np, N = 2 * np, nk = args.nk, stages = args.stages;
-    const uint32_t b_bytes_plane = (uint32_t)nk * N * kChunkBytes;
-    uint8_t* b_smem = smem;                                        // [plane][kc][N rows][128 B]
-    uint8_t* a_smem = smem + kPlanes * b_bytes_plane;              // [stage][plane][128 rows][128 B]
+    const int np = args.np, mg = args.mg, NA = 2 * mg, nk = args.nk, stages = args.stages;
+    // Resident B: [plane][kc][NA rows][128 B] once per problem.  Streamed B: every stage holds
+    // the A chunk planes followed by the B chunk planes (NA rows each).
+    const uint32_t b_bytes_plane = kStreamB ? 0u : (uint32_t)nk * NA * kChunkBytes;
+    const uint32_t stage_b_plane = kStreamB ? (uint32_t)NA * kChunkBytes : 0u;
+    const uint32_t stage_bytes = kPlanes * (kStageBytesPerPlane + stage_b_plane);
+    uint8_t* b_smem = smem;
+    uint8_t* a_smem = smem + kPlanes * b_bytes_plane;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // Persistent CTAs over a flat list of (problem, tile) items, problem-major; each CTA takes
     // one contiguous, balanced range so it switches problem (and reloads B) rarely.
-    const int64_t n_items = (int64_t)args.n_problems * args.tiles;
+    const int per_p = args.tiles * args.n_groups;                  // items per problem (group innermost)
+    const int64_t n_items = (int64_t)args.n_problems * per_p;
     const int item_begin = (int)(n_items * blockIdx.x / gridDim.x);
     const int item_end = (int)(n_items * (blockIdx.x + 1) / gridDim.x);
 
@@ -144,20 +151,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             const int kelems = kChunkBytes / (PREC == P_BF16X3 ? 2 : 4);
             int cur_p = -1, n_loaded = 0;
             for (int it = item_begin; it < item_end && !abort_flag; ++it) {
-                const int p = it / args.tiles, tile = it % args.tiles;
-                if (p != cur_p) {
+                const int p = it / per_p, tile = (it % per_p) / args.n_groups, g = it % args.n_groups;
+                const int brow = (args.b_idx ? args.b_idx[p] : args.b_base) * (2 * np) + g * mg;
+                if (!kStreamB && p != cur_p) {
                     // a new problem: wait until the MMAs using the previous B have completed
                     if (n_loaded > 0 && !tc::mbar_wait(&bempty_bar, (n_loaded - 1) & 1, &abort_flag)) {
                         abort_flag = 1;
                         atomicExch(args.status, (int)PHX_ERR_TIMEOUT);
                         break;
                     }
-                    const int brow = (args.b_idx ? args.b_idx[p] : args.b_base) * N;
                     tc::mbar_expect_tx(&bfull_bar, kPlanes * b_bytes_plane);
                     for (int pl = 0; pl < kPlanes; ++pl)
                         for (int kc = 0; kc < nk; ++kc)
                             for (int half = 0; half < 2; ++half)
-                                tc::tma_load_2d(b_smem + pl * b_bytes_plane + ((size_t)kc * N + half * np) * kChunkBytes,
+                                tc::tma_load_2d(b_smem + pl * b_bytes_plane + ((size_t)kc * NA + half * mg) * kChunkBytes,
                                                 &args.b_map[pl], &bfull_bar, kc * kelems, brow + half * np);
                     ++n_loaded;
                     cur_p = p;
@@ -170,10 +177,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                         break;
                     }
                     pending[stage] = false;
-                    tc::mbar_expect_tx(&full_bar[stage], kPlanes * kStageBytesPerPlane);
+                    uint8_t* st_base = a_smem + (size_t)stage * stage_bytes;
+                    tc::mbar_expect_tx(&full_bar[stage], stage_bytes);
                     for (int pl = 0; pl < kPlanes; ++pl)
-                        tc::tma_load_2d(a_smem + ((size_t)stage * kPlanes + pl) * kStageBytesPerPlane, &args.a_map[pl],
-                                        &full_bar[stage], kc * kelems, arow);
+                        tc::tma_load_2d(st_base + (size_t)pl * kStageBytesPerPlane, &args.a_map[pl], &full_bar[stage],
+                                        kc * kelems, arow);
+                    if (kStreamB) {
+                        uint8_t* sb = st_base + (size_t)kPlanes * kStageBytesPerPlane;
+                        for (int pl = 0; pl < kPlanes; ++pl)
+                            for (int half = 0; half < 2; ++half)
+                                tc::tma_load_2d(sb + (size_t)pl * stage_b_plane + (size_t)half * mg * kChunkBytes,
+                                                &args.b_map[pl], &full_bar[stage], kc * kelems, brow + half * np);
+                    }
                     pending[stage] = true;
                     pend_phase[stage] = phase;
                     if (++stage == stages) { stage = 0; phase ^= 1; }
@@ -193,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t id_full = tc::idesc(128, N <= 256 ? N : np, kFmt);
+            const uint32_t id_full = tc::idesc(128, NA, kFmt);
             bool ok = true;
             int stage = 0, acc = 0;
             uint32_t phase = 0, acc_phase = 0;
@@ -201,8 +216,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             const uint32_t a_base = tc::smem_u32(a_smem);
             int cur_p = -1, n_bloads = 0;
             for (int it = item_begin; ok && it < item_end; ++it) {
-                const int p = it / args.tiles;
-                if (p != cur_p) {
+                const int p = it / per_p;
+                if (!kStreamB && p != cur_p) {
                     if (cur_p >= 0) tc::mma_commit(&bempty_bar);       // B free once these MMAs finish
                     if (!tc::mbar_wait(&bfull_bar, n_bloads & 1, &abort_flag)) {
                         abort_flag = 1; atomicExch(args.status, (int)PHX_ERR_TIMEOUT); break;
@@ -215,32 +230,31 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     abort_flag = 1; atomicExch(args.status, (int)PHX_ERR_TIMEOUT); break;
                 }
                 tc::tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * N);
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * NA);
                 for (int kc = 0; kc < nk; ++kc) {
                     if (!tc::mbar_wait(&full_bar[stage], phase, &abort_flag)) {
                         abort_flag = 1; atomicExch(args.status, (int)PHX_ERR_TIMEOUT); ok = false; break;
                     }
                     tc::tc_fence_after();
+                    const uint32_t st_a = a_base + (uint32_t)stage * stage_bytes;
+                    const uint32_t st_b = kStreamB ? st_a + kPlanes * kStageBytesPerPlane
+                                                   : b_base + (uint32_t)kc * NA * kChunkBytes;
+                    const uint32_t b_lo = kStreamB ? stage_b_plane : b_bytes_plane;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {                      // 4 x 32 bytes per chunk
                         const uint32_t koff = (uint32_t)k * 32;
-                        const uint32_t a0 = a_base + (uint32_t)(stage * kPlanes) * kStageBytesPerPlane + koff;
                         const uint32_t acc_flag = (kc | k) ? 1u : 0u;
-                        for (int part = 0; part < (N <= 256 ? 1 : 2); ++part) {
-                            const uint32_t bo = (uint32_t)((size_t)kc * N + part * np) * kChunkBytes + koff;
-                            const uint32_t dcol = d_tmem + (uint32_t)(part * np);
-                            if (PREC == P_BF16X3) {
-                                const uint64_t ah = tc::sdesc_sw128(a0);
-                                const uint64_t al = tc::sdesc_sw128(a0 + kStageBytesPerPlane);
-                                const uint64_t bh = tc::sdesc_sw128(b_base + bo);
-                                const uint64_t bl = tc::sdesc_sw128(b_base + b_bytes_plane + bo);
-                                tc::mma_f16(dcol, ah, bh, id_full, acc_flag);
-                                tc::mma_f16(dcol, ah, bl, id_full, 1u);
-                                tc::mma_f16(dcol, al, bh, id_full, 1u);
-                            } else {
-                                tc::mma_tf32(dcol, tc::sdesc_sw128(a0), tc::sdesc_sw128(b_base + bo), id_full,
-                                             acc_flag);
-                            }
+                        if (PREC == P_BF16X3) {
+                            const uint64_t ah = tc::sdesc_sw128(st_a + koff);
+                            const uint64_t al = tc::sdesc_sw128(st_a + kStageBytesPerPlane + koff);
+                            const uint64_t bh = tc::sdesc_sw128(st_b + koff);
+                            const uint64_t bl = tc::sdesc_sw128(st_b + b_lo + koff);
+                            tc::mma_f16(d_tmem, ah, bh, id_full, acc_flag);
+                            tc::mma_f16(d_tmem, ah, bl, id_full, 1u);
+                            tc::mma_f16(d_tmem, al, bh, id_full, 1u);
+                        } else {
+                            tc::mma_tf32(d_tmem, tc::sdesc_sw128(st_a + koff), tc::sdesc_sw128(st_b + koff), id_full,
+                                         acc_flag);
                         }
                     }
                     tc::mma_commit(&empty_bar[stage]);
@@ -267,7 +281,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int it = item_begin; it < item_end; ++it) {
-            const int p = it / args.tiles, tile = it % args.tiles;
+            const int p = it / per_p, tile = (it % per_p) / args.n_groups, g = it % args.n_groups;
+            const int m0 = g * mg;                        // first output mode of this column group
             const bool ok = tc::mbar_wait(&tfull_bar[acc], acc_phase, &abort_flag);
             if (!ok) {
                 abort_flag = 1;
@@ -292,21 +307,21 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             tc::tc_fence_after();
             const int row = tile * kBoxRows + lgrp * 32 + lane;
             const bool valid = row < args.rows;
-            const uint32_t taddr = tmem_base + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)(acc * N);
+            const uint32_t taddr = tmem_base + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)(acc * NA);
             float v[16];
             if (EPI == EPI_M) {
                 // row (nu, b, c) of W -> M_slot[(nu, b)][c] (re) and [(nu, b)][Kcp + c] (im)
                 const int nb = row / args.n, c = row % args.n;
-                for (int j0 = half * 16; j0 < N; j0 += 32) {
+                for (int j0 = half * 16; j0 < NA; j0 += 32) {
                     tc::tmem_ld16(taddr + j0, v);
                     if (valid) {
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             const int j = j0 + i;
-                            const int slot = j < np ? j : j - np;
+                            const int slot = m0 + (j < mg ? j : j - mg);
                             if (slot >= args.nq_slots) continue;
                             const int64_t idx = ((int64_t)slot * args.out_rows_per_slot + nb) * args.out_kr +
-                                                (j < np ? 0 : args.out_kcp) + c;
+                                                (j < mg ? 0 : args.out_kcp) + c;
                             store_operand<PREC>(args.out_hi, args.out_lo, idx, v[i]);
                         }
                     }
@@ -315,15 +330,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 // row (nu, b) -> X[(nu, nu'')][b] (re) and [(nu, nu'')][Kcp + b] (im)
                 const int nu = row / args.n, b = row % args.n;
                 const int64_t base = (int64_t)p * args.out_rows_per_slot + (int64_t)nu * args.n;
-                for (int j0 = half * 16; j0 < N; j0 += 32) {
+                for (int j0 = half * 16; j0 < NA; j0 += 32) {
                     tc::tmem_ld16(taddr + j0, v);
                     if (valid) {
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             const int j = j0 + i;
-                            const int mode = j < np ? j : j - np;
+                            const int mode = m0 + (j < mg ? j : j - mg);
                             if (mode >= args.n) continue;
-                            const int64_t idx = (base + mode) * args.out_kr + (j < np ? 0 : args.out_kcp) + b;
+                            const int64_t idx = (base + mode) * args.out_kr + (j < mg ? 0 : args.out_kcp) + b;
                             store_operand<PREC>(args.out_hi, args.out_lo, idx, v[i]);
                         }
                     }
@@ -346,12 +361,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 float vi[16];
                 if (args.shape == PHX_GAUSS) {
                     const float a = -1.f / (args.sigma * args.sigma), norm = 0.56418958354775628f / args.sigma;
-                    for (int j0 = half * 16; j0 < np; j0 += 32) {
+                    for (int j0 = half * 16; j0 < mg; j0 += 32) {
                         tc::tmem_ld16(taddr + j0, v);
-                        tc::tmem_ld16(taddr + np + j0, vi);
+                        tc::tmem_ld16(taddr + mg + j0, vi);
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
-                            const int j = j0 + i;
+                            const int j = m0 + j0 + i;
                             const float f1 = s_f1[j], n1 = s_n1[j], if1 = s_if1[j];
                             const float x = d02 - f1, y = d02 + f1;
                             const float gd = fabsf(x) < lim ? __expf(a * x * x) : 0.f;
@@ -365,12 +380,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     ws *= norm;
                 } else {
                     const float h = 0.5f * args.sigma, h2 = h * h, norm = h / 3.14159265358979f;
-                    for (int j0 = half * 16; j0 < np; j0 += 32) {
+                    for (int j0 = half * 16; j0 < mg; j0 += 32) {
                         tc::tmem_ld16(taddr + j0, v);
-                        tc::tmem_ld16(taddr + np + j0, vi);
+                        tc::tmem_ld16(taddr + mg + j0, vi);
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
-                            const int j = j0 + i;
+                            const int j = m0 + j0 + i;
                             const float f1 = s_f1[j], n1 = s_n1[j], if1 = s_if1[j];
                             const float x = d02 - f1, y = d02 + f1;
                             const float gd = fabsf(x) < lim ? __frcp_rn(x * x + h2) : 0.f;
@@ -577,34 +592,45 @@ phx_status alloc_operand(phx_ctx* ctx, const char* name, int prec, int64_t rows,
     return PHX_OK;
 }
 
-template <int PREC, int EPI>
-cudaError_t launch_gemm(phx_ctx* ctx, TcArgs& a, int n_problems, int ctas_per_problem, cudaStream_t s) {
-    constexpr int planes = PREC == P_BF16X3 ? 2 : 1;
-    const size_t b_bytes = (size_t)planes * a.nk * 2 * a.np * kChunkBytes;
-    const size_t smem = 1024 + b_bytes + (size_t)a.stages * planes * kStageBytesPerPlane;
+size_t smem_bytes(int prec, bool stream_b, int nk, int mg, int stages) {
+    const int planes = prec == P_BF16X3 ? 2 : 1;
+    const size_t b_bytes = stream_b ? 0 : (size_t)planes * nk * 2 * mg * kChunkBytes;
+    const size_t stage = (size_t)planes * (kStageBytesPerPlane + (stream_b ? 2 * (size_t)mg * kChunkBytes : 0));
+    return 1024 + b_bytes + (size_t)stages * stage;
+}
+
+template <int PREC, int EPI, bool STREAM>
+cudaError_t launch_gemm(phx_ctx* ctx, TcArgs& a, int n_problems, int ctas, cudaStream_t s) {
+    const size_t smem = smem_bytes(PREC, STREAM, a.nk, a.mg, a.stages);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<PREC, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kSmemLimit - 8192));
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<PREC, EPI, STREAM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSmemLimit - 8192));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     (void)ctx;
     a.n_problems = n_problems;
-    const int64_t items = (int64_t)n_problems * a.tiles;
-    dim3 grid((unsigned)std::min<int64_t>(items, ctas_per_problem), 1);
-    tc_gemm_kernel<PREC, EPI><<<grid, kThreads, smem, s>>>(a);
+    const int64_t items = (int64_t)n_problems * a.tiles * a.n_groups;
+    dim3 grid((unsigned)std::min<int64_t>(items, ctas), 1);
+    tc_gemm_kernel<PREC, EPI, STREAM><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-// Shared-memory plan: B resident + as many A stages as fit (at least 2).
-bool plan_stages(int prec, int nk, int np, int* stages) {
-    const int planes = prec == P_BF16X3 ? 2 : 1;
-    const size_t b_bytes = (size_t)planes * nk * 2 * np * kChunkBytes;
-    const size_t avail = kSmemLimit - 8192 - 1024;   // static shared + alignment slack
-    if (b_bytes + 2 * (size_t)planes * kStageBytesPerPlane > avail) return false;
-    int st = (int)((avail - b_bytes) / ((size_t)planes * kStageBytesPerPlane));
-    *stages = std::min(st, kMaxStages);
+template <int PREC, int EPI>
+cudaError_t launch_gemm_any(phx_ctx* ctx, TcArgs& a, bool stream_b, int n_problems, int ctas, cudaStream_t s) {
+    return stream_b ? launch_gemm<PREC, EPI, true>(ctx, a, n_problems, ctas, s)
+                    : launch_gemm<PREC, EPI, false>(ctx, a, n_problems, ctas, s);
+}
+
+// Shared-memory plan: as many stages as fit next to a resident B (stream_b = false) or with B
+// streamed in every stage; at least 2 stages or the plan fails.
+bool plan_stages(int prec, bool stream_b, int nk, int mg, int* stages) {
+    const size_t avail = kSmemLimit - 8192;   // static shared memory headroom
+    if (smem_bytes(prec, stream_b, nk, mg, 2) > avail) return false;
+    int st = 2;
+    while (st < kMaxStages && smem_bytes(prec, stream_b, nk, mg, st + 1) <= avail) ++st;
+    *stages = st;
     return true;
 }
 
@@ -619,15 +645,28 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
                   const int32_t* irr_host, int n_irr, const GammaParams& gp, double* gacc, double* wacc,
                   cudaStream_t s) {
     const int n = f->n, nq = f->nq;
-    const int np = round_up(n, 16);
-    if (np > kMaxNp) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: n = %d > %d", n, kMaxNp);
     const int kcp = round_up(n, 32), kr = 2 * kcp;
     const int kelems = kChunkBytes / (PREC == P_BF16X3 ? 2 : 4);
     const int nk = kr / kelems;
+    // Output columns: the eigenvector B table keeps the whole matrix resident in shared memory
+    // when it fits (one column group); otherwise the modes are split into groups of mg <= 128
+    // whose Re/Im halves share one accumulator and B is streamed with every A chunk.
+    int np = round_up(n, 16), mg = np, n_groups = 1, st_e = 0;
+    bool stream_b = false;
+    if (np > 128 || !plan_stages(PREC, false, nk, mg, &st_e)) {
+        stream_b = true;
+        n_groups = (np + 127) / 128;
+        while (true) {
+            mg = round_up((np + n_groups - 1) / n_groups, 16);
+            if (plan_stages(PREC, true, nk, mg, &st_e)) break;
+            if (mg <= 16)
+                return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: n = %d does not fit", n);
+            ++n_groups;
+        }
+        np = mg * n_groups;
+    }
+    if (np > kMaxNp) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: n = %d > %d", n, kMaxNp);
     const int N = 2 * np;
-    int st_e = 0;
-    if (!plan_stages(PREC, nk, np, &st_e))
-        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: eigenvector table of n = %d exceeds shared memory", n);
     // DFT shape
     const int kcp_d = round_up(f->n_d, 32), kr_d = 2 * kcp_d, nk_d = kr_d / kelems;
     // Working-set plan: the modes nu of q are processed in chunks of n_nu (W of a chunk <= 1 GB)
@@ -652,7 +691,7 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
         if (v > 0) Q = std::min(std::min(v, 128), nq);
     }
     int st_d = 0;
-    while (!plan_stages(PREC, nk_d, round_up(Q, 8), &st_d)) {      // phase table must fit too
+    while (!plan_stages(PREC, false, nk_d, round_up(Q, 8), &st_d)) {      // phase table must fit too
         if (Q <= 8)
             return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: %d lattice differences exceed shared memory", f->n_d);
         Q = std::max(8, Q / 2);
@@ -716,15 +755,15 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
         bool ok = make_map(&aD.a_map[pl], w, PREC, opW.rows, kr_d, kBoxRows) &&
                   make_map(&aD.b_map[pl], ph, PREC, opP.rows, kr_d, qp_np) &&
                   make_map(&aA.a_map[pl], m, PREC, opM.rows, kr, kBoxRows) &&
-                  make_map(&aA.b_map[pl], e, PREC, opE.rows, kr, np) &&
+                  make_map(&aA.b_map[pl], e, PREC, opE.rows, kr, mg) &&
                   make_map(&aB.a_map[pl], x, PREC, opX.rows, kr, kBoxRows) &&
-                  make_map(&aB.b_map[pl], e, PREC, opE.rows, kr, np);
+                  make_map(&aB.b_map[pl], e, PREC, opE.rows, kr, mg);
         if (!ok) return phx_set_error(ctx, PHX_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
     const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
     // DFT: W rows x (2 qp_np) ; epilogue scatters into M
     aD.rows = (int)rows_w; aD.tiles = (int)((rows_w + kBoxRows - 1) / kBoxRows);
-    aD.np = qp_np; aD.nk = nk_d; aD.stages = st_d; aD.n_acc = (4 * qp_np <= 512) ? 2 : 1;
+    aD.np = qp_np; aD.mg = qp_np; aD.n_groups = 1; aD.nk = nk_d; aD.stages = st_d; aD.n_acc = (4 * qp_np <= 512) ? 2 : 1;
     aD.tmem_cols = tmem_cols_for(2 * qp_np, aD.n_acc);
     aD.a_rows_per_problem = 0; aD.b_idx = nullptr;
     aD.status = (int32_t*)ctx->status_word;
@@ -732,15 +771,17 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
     aD.n = n;
     // GEMM with e_q'': rows (nu, b), K = c ; epilogue writes X
     aA.rows = (int)rows_a; aA.tiles = (int)((rows_a + kBoxRows - 1) / kBoxRows);
-    aA.np = np; aA.nk = nk; aA.stages = st_e; aA.n_acc = (4 * np <= 512) ? 2 : 1;
-    aA.tmem_cols = tmem_cols_for(N, aA.n_acc);
+    aA.np = np; aA.mg = mg; aA.n_groups = n_groups; aA.nk = nk; aA.stages = st_e;
+    aA.n_acc = (4 * mg <= 512) ? 2 : 1;
+    aA.tmem_cols = tmem_cols_for(2 * mg, aA.n_acc);
     aA.a_rows_per_problem = (int)rows_a;
     aA.status = aD.status;
     aA.out_hi = opX.hi; aA.out_lo = opX.lo; aA.out_rows_per_slot = (int)rows_a; aA.out_kr = kr; aA.out_kcp = kcp;
     aA.n = n;
     // GEMM with e_q': rows (nu, nu''), K = b ; fused linewidth epilogue
     aB.rows = (int)rows_a; aB.tiles = aA.tiles;
-    aB.np = np; aB.nk = nk; aB.stages = st_e; aB.n_acc = aA.n_acc; aB.tmem_cols = aA.tmem_cols;
+    aB.np = np; aB.mg = mg; aB.n_groups = n_groups; aB.nk = nk; aB.stages = st_e; aB.n_acc = aA.n_acc;
+    aB.tmem_cols = aA.tmem_cols;
     aB.a_rows_per_problem = (int)rows_a;
     aB.status = aD.status;
     aB.n = n; aB.freq = freq; aB.nB = nB; aB.nu0 = 0;
@@ -790,16 +831,16 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
                 const double fl_e = 8.0 * (double)Qt * ra * n * n;
                 const double op_bytes = (double)planes * esz * 2.0;   // one complex value of an operand
                 int pp = phx_prof_begin(ctx, s);
-                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_M>(ctx, aD, 1, sms, s)));
+                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_M, false>(ctx, aD, 1, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_DFT, fl_d, op_bytes * ((double)rw * f->n_d + (double)Qt * ra * n));
                 aA.b_idx = qpp + t0;
                 pp = phx_prof_begin(ctx, s);
-                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_X>(ctx, aA, Qt, sms, s)));
+                PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_X>(ctx, aA, stream_b, Qt, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_GEMM_E2, fl_e, op_bytes * 2.0 * Qt * ra * n);
                 aB.b_idx = ident + t0;
                 aB.t0 = t0;
                 pp = phx_prof_begin(ctx, s);
-                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_G>(ctx, aB, Qt, sms, s)));
+                PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_G>(ctx, aB, stream_b, Qt, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_GEMM_E1, fl_e, op_bytes * (double)Qt * ra * n);
                 ctx->launches += 3;
             }

@@ -92,3 +92,24 @@ def test_tc_fcc32_sampled_vs_golden(ctx, phx, prec):
     ref = rows[:, 3].reshape(len(qs), -1)
     print(f"{prec}: fcc32 gamma max rel err {_err(g, ref):.3e}")
     assert _err(g, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("mult,prec", [((4, 3, 3), "bf16x3"), ((4, 4, 4), "bf16x3"), ((4, 4, 4), "tf32")])
+def test_tc_large_cells_streamed_b(ctx, phx, mult, prec):
+    """108 and 192 modes: the eigenvector operand no longer fits in shared memory and is streamed
+    with the A chunks, in one or two column groups."""
+    c = P.random_masses(P.fcc_primitive_multiple(5.26, mult), 39.95, 83.8, seed=11)
+    mesh = (2, 1, 1)
+    pot = P.LennardJones()
+    f2, f3 = P.ifc2_lj(c, pot), P.ifc3_lj(c, pot)
+    q = O.grid.mesh_qred(mesh)
+    freq, evec, _, _ = ctx.harmonic(c.lattice, c.masses, f2.idx, f2.val.reshape(-1, 9), q, want_vel=False,
+                                    want_vv=False)
+    irr = np.array([0, 1], dtype=np.int32)
+    h = ctx.fc3(c.lattice, c.masses, f3.idx, f3.val, mesh)
+    g = ctx.gamma(h, freq, evec, irr, 60.0, "gauss", 0.2, precision=prec)
+    fc3 = O.anharmonic.FC3(f3.idx, f3.val, c.masses)
+    go = O.anharmonic.gamma(fc3, mesh, freq, evec, irr, 60.0, "gauss", 0.2)
+    print(f"{prec}: {3 * c.n_atoms} modes gamma max rel err {_err(g, go):.3e}")
+    assert go.max() > 0
+    assert _err(g, go) < TOL[prec]

@@ -158,6 +158,42 @@ phx_status phx_gamma(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz,
                      double temperature, phx_broadening br, double f_min_thz,
                      int32_t prec, double* gamma, double* wp2, int32_t mem, void* stream);
 
+/* ---------------------------------------------------------------- batched scattering
+ * Many crystals (of any size up to 192 modes and any mesh) in one call: every job's
+ * linewidths (as phx_gamma) and, when vv is given, its unfolded linewidths and RTA
+ * conductivity (as phx_unfold + phx_kappa_rta) are enqueued as one CUDA graph, captured on the
+ * first call and replayed by later calls with the same job list (same pointers and
+ * parameters).  Job arrays are device memory except irr_q (host).  Precision PHX_BF16X3 or
+ * PHX_TF32.  The q' tile of each job class (modes, mesh, lattice differences) is taken from
+ * tune[j].q_tile when tune is given and > 0, else chosen by timing the candidates 8..128 on
+ * one irreducible q-point of the first job of the class (cached per context).
+ * The call enqueues on `stream` (ordered after work already on it) and returns without
+ * synchronising.  Errors: as phx_gamma; PHX_ERR_UNSUPPORTED for PHX_FP64. */
+typedef struct {
+    const phx_fc3* fc3;            /* prepared Phi3 of this crystal and mesh              */
+    const double* freq_thz;        /* [nq][n] device                                      */
+    const double* evec;            /* [nq][n][n] complex, device                          */
+    const int32_t* irr_q;          /* [n_irr] host: irreducible mesh indices              */
+    int32_t n_irr;
+    double temperature;
+    phx_broadening br;
+    double f_min_thz;
+    double* gamma;                 /* [n_irr][n] device, output (1/ps)                    */
+    const int32_t* irr_q_dev;      /* [n_irr] device copy of irr_q (conductivity only)    */
+    const int32_t* full_to_irr;    /* [nq] device (conductivity only)                     */
+    const double* vv;              /* [nq][n][9] device; NULL: no conductivity            */
+    double* gamma_full;            /* [nq][n] device, output (conductivity only)          */
+    double volume;                 /* unit-cell volume in A^3 (conductivity only)         */
+    double* kappa;                 /* [9] device, output W/(m K) (conductivity only)      */
+} phx_job;
+
+typedef struct {
+    int32_t q_tile;                /* q' per Fourier tile; 0 = autotune                   */
+} phx_tune;
+
+phx_status phx_gamma_batched(phx_ctx* ctx, int32_t n_jobs, const phx_job* jobs, int32_t prec,
+                             const phx_tune* tune, void* stream);
+
 /* ---------------------------------------------------------------- transport
  * Map irreducible linewidths to the full mesh (Sec. "Overview of New Capabilities"):
  * gamma_full[k][nu] = gamma_irr[full_to_irr[k]][nu] after averaging gamma_irr over each

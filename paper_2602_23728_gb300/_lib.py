@@ -46,6 +46,17 @@ class Broadening(C.Structure):
     _fields_ = [("shape", C.c_int32), ("sigma_thz", C.c_double), ("window", C.c_double)]
 
 
+class Job(C.Structure):
+    _fields_ = [("fc3", C.c_void_p), ("freq_thz", C.c_void_p), ("evec", C.c_void_p), ("irr_q", C.c_void_p),
+                ("n_irr", C.c_int32), ("temperature", C.c_double), ("br", Broadening), ("f_min_thz", C.c_double),
+                ("gamma", C.c_void_p), ("irr_q_dev", C.c_void_p), ("full_to_irr", C.c_void_p), ("vv", C.c_void_p),
+                ("gamma_full", C.c_void_p), ("volume", C.c_double), ("kappa", C.c_void_p)]
+
+
+class Tune(C.Structure):
+    _fields_ = [("q_tile", C.c_int32)]
+
+
 _P = C.c_void_p
 _I = C.c_int32
 lib.phx_create.argtypes = [C.POINTER(_P), C.c_int]
@@ -81,12 +92,15 @@ lib.phx_profile_read.restype = C.c_int
 lib.phx_kappa_rta_noalloc.argtypes = [C.POINTER(Cell), _I, _I, _P, _P, _P, _P, C.c_double, C.c_double, _I, _P, _P]
 lib.phx_kappa_rta_noalloc.restype = C.c_int
 
+lib.phx_gamma_batched.argtypes = [_P, _I, _P, _I, _P, _P]
+lib.phx_gamma_batched.restype = C.c_int
+
 KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4, "fp64_epilogue": 5,
            "eigensolver": 6}
 
 EXPORTED = ["phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
             "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_unfold", "phx_kappa_rta",
-            "phx_kappa_rta_noalloc"]
+            "phx_kappa_rta_noalloc", "phx_gamma_batched"]
 
 
 class PhxError(RuntimeError):
@@ -273,6 +287,43 @@ class Context:
                                   float(temperature), br, float(f_min), PRECISIONS[precision], _ptr(gamma),
                                   _ptr(wp2), mem, stream))
         return (gamma, wp2) if want_wp2 or wp2 is not None else gamma
+
+    def gamma_batched(self, jobs, precision="bf16x3", q_tiles=None):
+        """phx_gamma_batched.  jobs: list of dicts with keys fc3 (FC3), freq, evec (CUDA tensors),
+        irr (numpy int32), irr_dev (CUDA int32), T, shape, sigma, window, f_min, gamma (CUDA out),
+        and optionally vv, full_to_irr, gamma_full, kappa (CUDA) and volume for the conductivity.
+        q_tiles: None (autotune) or a list of q' tiles per job."""
+        import torch
+        arr = (Job * len(jobs))()
+        keep = []
+        for k, j in enumerate(jobs):
+            irr = _host(j["irr"], np.int32)
+            keep.append(irr)
+            a = arr[k]
+            a.fc3 = j["fc3"].h
+            a.freq_thz = _ptr(j["freq"])
+            a.evec = _ptr(j["evec"])
+            a.irr_q = irr.ctypes.data
+            a.n_irr = irr.shape[0]
+            a.temperature = float(j["T"])
+            a.br = Broadening(SHAPES[j.get("shape", "gauss")], float(j.get("sigma", 0.1)), float(j.get("window", 2.0)))
+            a.f_min_thz = float(j.get("f_min", 0.01))
+            a.gamma = _ptr(j["gamma"])
+            a.irr_q_dev = _ptr(j["irr_dev"])
+            a.full_to_irr = _ptr(j.get("full_to_irr"))
+            a.vv = _ptr(j.get("vv"))
+            a.gamma_full = _ptr(j.get("gamma_full"))
+            a.volume = float(j.get("volume", 0.0))
+            a.kappa = _ptr(j.get("kappa"))
+        tune = None
+        if q_tiles is not None:
+            tune = (Tune * len(jobs))()
+            for k, q in enumerate(q_tiles):
+                tune[k].q_tile = int(q)
+        dev = jobs[0]["freq"].device if jobs else torch.device("cuda", self.device)
+        stream = torch.cuda.current_stream(dev).cuda_stream
+        self._check(lib.phx_gamma_batched(self.h, len(jobs), C.addressof(arr), PRECISIONS[precision],
+                                          C.addressof(tune) if tune is not None else None, stream))
 
     # ------------------------------------------------------------------ transport
     def unfold(self, freq_full, irr_q, gamma_irr, full_to_irr, out=None):

@@ -37,6 +37,11 @@ void* phx_ws(phx_ctx* ctx, const char* name, size_t bytes) {
         cudaDeviceSynchronize();            // the old buffer may still be in use by queued work
         cudaFree(it->second.first);
         ctx->ws.erase(it);
+        if (ctx->graph_exec) {              // a cached batch graph points at the old buffer
+            cudaGraphExecDestroy(ctx->graph_exec);
+            ctx->graph_exec = nullptr;
+            ctx->graph_key.clear();
+        }
     }
     void* p = nullptr;
     size_t sz = std::max<size_t>(bytes, 256);
@@ -95,6 +100,19 @@ __global__ void finalize_gamma_kernel(int count, int n, const int32_t* irr, cons
     }
 }
 
+}  // namespace
+
+cudaError_t phx_launch_finalize(int count, int n, const int32_t* irr, const double* freq, const double* gacc,
+                                const double* wacc, double pref, double inv_nq, double f_min, double* gamma,
+                                double* wp2, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    finalize_gamma_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, n, irr, freq, gacc, wacc, pref, inv_nq, f_min,
+                                                            gamma, wp2);
+    return cudaGetLastError();
+}
+
+namespace {
+
 cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
 bool finite_all(const double* p, size_t n) {
@@ -142,6 +160,12 @@ void phx_destroy(phx_ctx* ctx) {
     cudaDeviceSynchronize();
     for (auto& kv : ctx->ws) cudaFree(kv.second.first);
     cudaFree(ctx->status_word);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -471,6 +495,7 @@ void phx_fc3_destroy(phx_fc3* h) {
     if (!h) return;
     cudaFree(h->d_int); cudaFree(h->seg_key); cudaFree(h->seg_start);
     cudaFree(h->ent_a); cudaFree(h->ent_r2); cudaFree(h->ent_w);
+    cudaFree(h->tc_seg_of); cudaFree(h->tc_ident);
     delete h;
 }
 

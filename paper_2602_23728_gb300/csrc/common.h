@@ -43,6 +43,13 @@ struct phx_ctx {
     int64_t prof_n[PHX_K_COUNT] = {0};
     double prof_flops[PHX_K_COUNT] = {0}, prof_bytes[PHX_K_COUNT] = {0};
     int64_t launches = 0;            // kernels launched since the last profile enable
+    // batched path: capture stream, cached graph of the last job list, q'-tile autotune table
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<uint8_t> graph_key;
+    int64_t graph_launches = 0;
+    std::map<std::vector<int>, int> tune_q;
 };
 
 // Profiling helpers: begin returns a record slot (or -1 when profiling is off).
@@ -64,6 +71,9 @@ struct phx_fc3 {
     int32_t* ent_a = nullptr;       // [nnz] component index a of each entry (sorted)
     int32_t* ent_r2 = nullptr;      // [nnz][3] R'' of each entry
     double* ent_w = nullptr;        // [nnz] Phi3 / sqrt(m_a m_b m_c)
+    // tensor-core path tables, built on first use (before any capture)
+    int32_t* tc_seg_of = nullptr;   // [n][n][n_d] segment of (d, b, c) or -1
+    int32_t* tc_ident = nullptr;    // [nq] 0..nq-1
 };
 
 // ---------------------------------------------------------------- host helpers
@@ -153,6 +163,10 @@ cudaError_t phx_launch_kappa(int nq, int n, const double* freq, const double* ve
                              int is_classic, double* acc9, cudaStream_t s);
 
 cudaError_t phx_launch_third_index(int iq, const int* mesh, int32_t* qpp, cudaStream_t s);
+cudaError_t phx_launch_finalize(int count, int n, const int32_t* irr, const double* freq, const double* gacc,
+                                const double* wacc, double pref, double inv_nq, double f_min, double* gamma,
+                                double* wp2, cudaStream_t s);
+cudaError_t phx_launch_scale9(const double* acc, double scale, double* out, cudaStream_t s);
 
 // gamma path shared parameters
 struct GammaParams {

@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <cmath>
 #include <mutex>
 
@@ -640,167 +641,218 @@ uint32_t tmem_cols_for(int N, int n_acc) {
     return c;
 }
 
-template <int PREC>
-phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec, const double* nB,
-                  const int32_t* irr_host, int n_irr, const GammaParams& gp, double* gacc, double* wacc,
-                  cudaStream_t s) {
-    const int n = f->n, nq = f->nq;
-    const int kcp = round_up(n, 32), kr = 2 * kcp;
-    const int kelems = kChunkBytes / (PREC == P_BF16X3 ? 2 : 4);
-    const int nk = kr / kelems;
-    // Output columns: the eigenvector B table keeps the whole matrix resident in shared memory
-    // when it fits (one column group); otherwise the modes are split into groups of mg <= 128
-    // whose Re/Im halves share one accumulator and B is streamed with every A chunk.
-    int np = round_up(n, 16), mg = np, n_groups = 1, st_e = 0;
+// ---------------------------------------------------------------- plan / prepare / enqueue
+
+// Shapes of one tensor-core linewidth job (pure arithmetic; no device work).
+struct TcPlan {
+    int prec = P_BF16X3;
+    int n = 0, nq = 0;
+    int kcp = 0, kr = 0, nk = 0;            // eigenvector contractions: K layout
+    int np = 0, mg = 0, n_groups = 1, st_e = 0;
     bool stream_b = false;
-    if (np > 128 || !plan_stages(PREC, false, nk, mg, &st_e)) {
-        stream_b = true;
-        n_groups = (np + 127) / 128;
+    int kcp_d = 0, kr_d = 0, nk_d = 0, st_d = 0;   // Fourier GEMM
+    int n_nu = 0, Q = 0, qp_np = 0, n_tiles_q = 0;
+    int64_t rows_w = 0, rows_a = 0;
+    // workspace bytes per operand plane
+    size_t bytes_w = 0, bytes_m = 0, bytes_e = 0, bytes_p = 0;
+};
+
+phx_status tc_plan(phx_ctx* ctx, const phx_fc3* f, int prec, int q_override, TcPlan* pl) {
+    TcPlan P;
+    P.prec = prec;
+    const int n = f->n, nq = f->nq;
+    P.n = n;
+    P.nq = nq;
+    const int esz = prec == P_BF16X3 ? 2 : 4;
+    const int planes = prec == P_BF16X3 ? 2 : 1;
+    P.kcp = round_up(n, 32);
+    P.kr = 2 * P.kcp;
+    const int kelems = kChunkBytes / esz;
+    P.nk = P.kr / kelems;
+    // Output columns: the eigenvector B table stays resident in shared memory when it fits
+    // (one column group); otherwise the modes are split into groups of mg <= 128 whose Re/Im
+    // halves share one accumulator and B is streamed with every A chunk.
+    P.np = round_up(n, 16);
+    P.mg = P.np;
+    if (P.np > 128 || !plan_stages(prec, false, P.nk, P.mg, &P.st_e)) {
+        P.stream_b = true;
+        P.n_groups = (P.np + 127) / 128;
         while (true) {
-            mg = round_up((np + n_groups - 1) / n_groups, 16);
-            if (plan_stages(PREC, true, nk, mg, &st_e)) break;
-            if (mg <= 16)
-                return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: n = %d does not fit", n);
-            ++n_groups;
+            P.mg = round_up((P.np + P.n_groups - 1) / P.n_groups, 16);
+            if (plan_stages(prec, true, P.nk, P.mg, &P.st_e)) break;
+            if (P.mg <= 16) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: n = %d does not fit", n);
+            ++P.n_groups;
         }
-        np = mg * n_groups;
+        P.np = P.mg * P.n_groups;
     }
-    if (np > kMaxNp) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: n = %d > %d", n, kMaxNp);
-    const int N = 2 * np;
-    // DFT shape
-    const int kcp_d = round_up(f->n_d, 32), kr_d = 2 * kcp_d, nk_d = kr_d / kelems;
-    // Working-set plan: the modes nu of q are processed in chunks of n_nu (W of a chunk <= 1 GB)
-    // and q' in tiles of Q (M and X of a tile together <= 920 MB: 64 q' at 96 modes, the best
-    // measured on GB300 between 13 and 64; larger tiles re-read W fewer times).
-    // Both can be overridden (PHX_NU_CHUNK, PHX_Q_TILE) for tuning.
+    if (P.np > kMaxNp) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: n = %d > %d", n, kMaxNp);
+    P.kcp_d = round_up(f->n_d, 32);
+    P.kr_d = 2 * P.kcp_d;
+    P.nk_d = P.kr_d / kelems;
+    // Working set: modes of q in chunks of n_nu (W of a chunk <= 1 GB; measured on GB300 at 96
+    // modes, chunking for L2 residency loses more to launch count than it gains) and q' in
+    // tiles of Q (M and X of a tile together <= 920 MB: 64 q' at 96 modes, the best measured
+    // between 13 and 64; larger tiles re-read W fewer times).  PHX_NU_CHUNK / PHX_Q_TILE or
+    // the autotuner override the defaults.
     const int64_t n2 = (int64_t)n * n;
-    const int esz = PREC == P_BF16X3 ? 2 : 4;
-    const int planes_ = PREC == P_BF16X3 ? 2 : 1;
-    // Measured on GB300 (96 modes, 8^3): chunking nu loses more to launch count than it gains
-    // in L2 residency, so the whole W of q (<= 1 GB) is kept unless it is larger than that.
-    int n_nu = (int)std::max<int64_t>(1, std::min<int64_t>(n, ((int64_t)1 << 30) / (n2 * kr_d * esz * planes_)));
+    P.n_nu = (int)std::max<int64_t>(1, std::min<int64_t>(n, ((int64_t)1 << 30) / (n2 * P.kr_d * esz * planes)));
     if (const char* env = getenv("PHX_NU_CHUNK")) {
         const int v = atoi(env);
-        if (v > 0) n_nu = std::min(v, n);
+        if (v > 0) P.n_nu = std::min(v, n);
     }
-    const int64_t per_qp = 2 * (int64_t)n_nu * n * kr * esz * planes_;       // M + X of one q'
+    const int64_t per_qp = 2 * (int64_t)P.n_nu * n * P.kr * esz * planes;   // M + X of one q'
     int Q = (int)std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)920 << 20) / per_qp));
     Q = std::min(Q, 128);
-    if (const char* env = getenv("PHX_Q_TILE")) {       // tuning knob: q' per Fourier tile
+    if (const char* env = getenv("PHX_Q_TILE")) {
         const int v = atoi(env);
         if (v > 0) Q = std::min(std::min(v, 128), nq);
     }
-    int st_d = 0;
-    while (!plan_stages(PREC, false, nk_d, round_up(Q, 8), &st_d)) {      // phase table must fit too
+    if (q_override > 0) Q = std::min(std::min(q_override, 128), nq);
+    while (!plan_stages(prec, false, P.nk_d, round_up(Q, 8), &P.st_d)) {   // phase table must fit too
         if (Q <= 8)
             return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: %d lattice differences exceed shared memory", f->n_d);
         Q = std::max(8, Q / 2);
     }
-    const int qp_np = round_up(Q, 8);
-    const int n_tiles_q = (nq + Q - 1) / Q;
-    if (!get_encoder()) return phx_set_error(ctx, PHX_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    const int64_t rows_w = (int64_t)n_nu * n2;    // W rows of a full nu chunk
-    const int64_t rows_a = (int64_t)n_nu * n;     // rows of M and X per q' slot (full chunk)
+    P.Q = Q;
+    P.qp_np = round_up(Q, 8);
+    P.n_tiles_q = (nq + Q - 1) / Q;
+    P.rows_w = (int64_t)P.n_nu * n2;
+    P.rows_a = (int64_t)P.n_nu * n;
+    if (P.rows_w > INT32_MAX / 2) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: W chunk too large");
+    P.bytes_w = (size_t)P.rows_w * P.kr_d * esz;
+    P.bytes_m = (size_t)Q * P.rows_a * P.kr * esz;
+    P.bytes_e = (size_t)nq * 2 * P.np * P.kr * esz;
+    P.bytes_p = (size_t)P.n_tiles_q * 2 * P.qp_np * P.kr_d * esz;
+    *pl = P;
+    return PHX_OK;
+}
 
-    Operand opW, opM, opX, opE, opP;
-    PHX_TRY(alloc_operand(ctx, "tc.W", PREC, rows_w, kr_d, &opW));
-    PHX_TRY(alloc_operand(ctx, "tc.M", PREC, (int64_t)Q * rows_a, kr, &opM));
-    PHX_TRY(alloc_operand(ctx, "tc.X", PREC, (int64_t)Q * rows_a, kr, &opX));
-    PHX_TRY(alloc_operand(ctx, "tc.E", PREC, (int64_t)nq * N, kr, &opE));
-    PHX_TRY(alloc_operand(ctx, "tc.P", PREC, (int64_t)n_tiles_q * 2 * qp_np, kr_d, &opP));
-    int32_t* qpp = (int32_t*)phx_ws(ctx, "tc.qpp", (size_t)nq * 4);
-    int32_t* ident = (int32_t*)phx_ws(ctx, "tc.ident", (size_t)nq * 4);
-    int32_t* seg_of = (int32_t*)phx_ws(ctx, "tc.segof", (size_t)f->n_d * n2 * 4);
-    float2* wph = (float2*)phx_ws(ctx, "tc.wph", (size_t)std::max<int64_t>(f->nnz, 1) * sizeof(float2));
-    float2* eqf = (float2*)phx_ws(ctx, "tc.eqf", (size_t)n2 * sizeof(float2));
-    if (!qpp || !ident || !seg_of || !wph || !eqf) return PHX_ERR_NOMEM;
-    if (rows_w > INT32_MAX / 2) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: W chunk too large");
-    // padding columns of M, X and W must read as zero
-    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opM.hi, 0, (size_t)opM.rows * kr * esz, s));
-    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opX.hi, 0, (size_t)opX.rows * kr * esz, s));
-    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opW.hi, 0, (size_t)opW.rows * kr_d * esz, s));
-    if (PREC == P_BF16X3) {
-        PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opM.lo, 0, (size_t)opM.rows * kr * esz, s));
-        PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opX.lo, 0, (size_t)opX.rows * kr * esz, s));
-        PHX_CUDA_CHECK(ctx, cudaMemsetAsync(opW.lo, 0, (size_t)opW.rows * kr_d * esz, s));
+// Per-crystal device tables (kept with the Phi3 handle): dense segment map [b][c][d] and the
+// identity index list of the mesh.  Host work; must run before any stream capture.
+phx_status tc_prepare_fc3(phx_ctx* ctx, phx_fc3* f) {
+    if (f->tc_seg_of) return PHX_OK;
+    const int n = f->n, nq = f->nq;
+    const int64_t n2 = (int64_t)n * n;
+    std::vector<int32_t> id(nq);
+    for (int i = 0; i < nq; ++i) id[i] = i;
+    std::vector<int32_t> so((size_t)f->n_d * n2, -1);
+    std::vector<int32_t> keys((size_t)f->n_seg * 3);
+    PHX_CUDA_CHECK(ctx, cudaMemcpy(keys.data(), f->seg_key, keys.size() * 4, cudaMemcpyDeviceToHost));
+    for (int64_t sgi = 0; sgi < f->n_seg; ++sgi)
+        so[((size_t)keys[3 * sgi + 1] * n + keys[3 * sgi + 2]) * f->n_d + keys[3 * sgi]] = (int32_t)sgi;
+    int32_t *dso = nullptr, *did = nullptr;
+    if (cudaMalloc(&dso, std::max<size_t>(so.size() * 4, 16)) != cudaSuccess ||
+        cudaMalloc(&did, std::max<size_t>(id.size() * 4, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dso);
+        return phx_set_error(ctx, PHX_ERR_NOMEM, "tensor-core tables: allocation failed");
     }
-    {
-        std::vector<int32_t> id(nq);
-        for (int i = 0; i < nq; ++i) id[i] = i;
-        std::vector<int32_t> so((size_t)f->n_d * n2, -1);
-        std::vector<int32_t> keys((size_t)f->n_seg * 3);
-        PHX_CUDA_CHECK(ctx, cudaMemcpy(keys.data(), f->seg_key, keys.size() * 4, cudaMemcpyDeviceToHost));
-        for (int64_t sgi = 0; sgi < f->n_seg; ++sgi)
-            so[((size_t)keys[3 * sgi + 1] * n + keys[3 * sgi + 2]) * f->n_d + keys[3 * sgi]] = (int32_t)sgi;
-        PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(ident, id.data(), nq * 4, cudaMemcpyHostToDevice, s));
-        PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(seg_of, so.data(), so.size() * 4, cudaMemcpyHostToDevice, s));
-        PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
+    PHX_CUDA_CHECK(ctx, cudaMemcpy(dso, so.data(), so.size() * 4, cudaMemcpyHostToDevice));
+    PHX_CUDA_CHECK(ctx, cudaMemcpy(did, id.data(), id.size() * 4, cudaMemcpyHostToDevice));
+    f->tc_seg_of = dso;
+    f->tc_ident = did;
+    return PHX_OK;
+}
+
+struct TcBuffers {
+    Operand W, M, X, E, P;
+    int32_t* qpp = nullptr;
+    float2* wph = nullptr;
+    float2* eqf = nullptr;
+};
+
+// Workspace large enough for the given byte counts (per plane) and element counts.
+phx_status tc_alloc(phx_ctx* ctx, int prec, size_t bw, size_t bm, size_t be, size_t bp, int64_t max_nq,
+                    int64_t max_nnz, int64_t max_n2, TcBuffers* b) {
+    const int planes = prec == P_BF16X3 ? 2 : 1;
+    auto get = [&](const char* name, size_t bytes, Operand* o) -> bool {
+        std::string nh = std::string(name) + ".hi", nl = std::string(name) + ".lo";
+        o->hi = phx_ws(ctx, nh.c_str(), bytes);
+        o->lo = planes == 2 ? phx_ws(ctx, nl.c_str(), bytes) : nullptr;
+        return o->hi && (planes == 1 || o->lo);
+    };
+    if (!get("tc.W", bw, &b->W) || !get("tc.M", bm, &b->M) || !get("tc.X", bm, &b->X) || !get("tc.E", be, &b->E) ||
+        !get("tc.P", bp, &b->P))
+        return PHX_ERR_NOMEM;
+    b->qpp = (int32_t*)phx_ws(ctx, "tc.qpp", (size_t)max_nq * 4);
+    b->wph = (float2*)phx_ws(ctx, "tc.wph", (size_t)std::max<int64_t>(max_nnz, 1) * sizeof(float2));
+    b->eqf = (float2*)phx_ws(ctx, "tc.eqf", (size_t)max_n2 * sizeof(float2));
+    if (!b->qpp || !b->wph || !b->eqf) return PHX_ERR_NOMEM;
+    return PHX_OK;
+}
+
+// Enqueue the whole linewidth computation of one job on `s` (kernel launches and memsets
+// only, so it can be captured into a graph).  gacc/wacc: [n_irr][n] accumulators, zeroed.
+template <int PREC>
+phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcBuffers& B, const double* freq,
+                      const double* evec, const double* nB, const int32_t* irr_host, int n_irr, const GammaParams& gp,
+                      double* gacc, double* wacc, cudaStream_t s) {
+    const int n = P.n, nq = P.nq, kr = P.kr, kcp = P.kcp, kr_d = P.kr_d, kcp_d = P.kcp_d;
+    const int np = P.np, mg = P.mg, Q = P.Q, qp_np = P.qp_np, n_nu = P.n_nu;
+    const int64_t n2 = (int64_t)n * n;
+    const int esz = PREC == P_BF16X3 ? 2 : 4;
+    const int planes = PREC == P_BF16X3 ? 2 : 1;
+    if (!get_encoder()) return phx_set_error(ctx, PHX_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    // padding columns of M, X and W must read as zero for this job's layout
+    for (int pl = 0; pl < planes; ++pl) {
+        PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.M.lo : B.M.hi, 0, P.bytes_m, s));
+        PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.X.lo : B.X.hi, 0, P.bytes_m, s));
+        PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.W.lo : B.W.hi, 0, P.bytes_w, s));
     }
-    prep_evec_tables<PREC><<<2048, 256, 0, s>>>((const double2*)evec, nq, n, np, kcp, opE.hi, opE.lo);
+    prep_evec_tables<PREC><<<2048, 256, 0, s>>>((const double2*)evec, nq, n, np, kcp, B.E.hi, B.E.lo);
+    PHX_CUDA_CHECK(ctx, cudaGetLastError());
+    prep_phase_tables<PREC><<<256, 256, 0, s>>>(f->d_int, f->n_d, f->mesh[0], f->mesh[1], f->mesh[2], Q,
+                                                P.n_tiles_q, qp_np, kcp_d, B.P.hi, B.P.lo);
     PHX_CUDA_CHECK(ctx, cudaGetLastError());
     ctx->launches += 2;
-    prep_phase_tables<PREC><<<256, 256, 0, s>>>(f->d_int, f->n_d, f->mesh[0], f->mesh[1], f->mesh[2], Q, n_tiles_q,
-                                                qp_np, kcp_d, opP.hi, opP.lo);
-    PHX_CUDA_CHECK(ctx, cudaGetLastError());
 
-    // tensor maps (operand buffers are fixed for the whole call)
     TcArgs aD{}, aA{}, aB{};
-    const int planes = PREC == P_BF16X3 ? 2 : 1;
+    const int64_t m_rows = (int64_t)Q * P.rows_a;
     for (int pl = 0; pl < planes; ++pl) {
-        const void* w = pl ? opW.lo : opW.hi;
-        const void* m = pl ? opM.lo : opM.hi;
-        const void* x = pl ? opX.lo : opX.hi;
-        const void* e = pl ? opE.lo : opE.hi;
-        const void* ph = pl ? opP.lo : opP.hi;
-        bool ok = make_map(&aD.a_map[pl], w, PREC, opW.rows, kr_d, kBoxRows) &&
-                  make_map(&aD.b_map[pl], ph, PREC, opP.rows, kr_d, qp_np) &&
-                  make_map(&aA.a_map[pl], m, PREC, opM.rows, kr, kBoxRows) &&
-                  make_map(&aA.b_map[pl], e, PREC, opE.rows, kr, mg) &&
-                  make_map(&aB.a_map[pl], x, PREC, opX.rows, kr, kBoxRows) &&
-                  make_map(&aB.b_map[pl], e, PREC, opE.rows, kr, mg);
+        const void* w = pl ? B.W.lo : B.W.hi;
+        const void* m = pl ? B.M.lo : B.M.hi;
+        const void* x = pl ? B.X.lo : B.X.hi;
+        const void* e = pl ? B.E.lo : B.E.hi;
+        const void* ph = pl ? B.P.lo : B.P.hi;
+        bool ok = make_map(&aD.a_map[pl], w, PREC, P.rows_w, kr_d, kBoxRows) &&
+                  make_map(&aD.b_map[pl], ph, PREC, (int64_t)P.n_tiles_q * 2 * qp_np, kr_d, qp_np) &&
+                  make_map(&aA.a_map[pl], m, PREC, m_rows, kr, kBoxRows) &&
+                  make_map(&aA.b_map[pl], e, PREC, (int64_t)nq * 2 * np, kr, mg) &&
+                  make_map(&aB.a_map[pl], x, PREC, m_rows, kr, kBoxRows) &&
+                  make_map(&aB.b_map[pl], e, PREC, (int64_t)nq * 2 * np, kr, mg);
         if (!ok) return phx_set_error(ctx, PHX_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
     const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
-    // DFT: W rows x (2 qp_np) ; epilogue scatters into M
-    aD.rows = (int)rows_w; aD.tiles = (int)((rows_w + kBoxRows - 1) / kBoxRows);
-    aD.np = qp_np; aD.mg = qp_np; aD.n_groups = 1; aD.nk = nk_d; aD.stages = st_d; aD.n_acc = (4 * qp_np <= 512) ? 2 : 1;
+    aD.np = qp_np; aD.mg = qp_np; aD.n_groups = 1; aD.nk = P.nk_d; aD.stages = P.st_d;
+    aD.n_acc = (4 * qp_np <= 512) ? 2 : 1;
     aD.tmem_cols = tmem_cols_for(2 * qp_np, aD.n_acc);
     aD.a_rows_per_problem = 0; aD.b_idx = nullptr;
     aD.status = (int32_t*)ctx->status_word;
-    aD.out_hi = opM.hi; aD.out_lo = opM.lo; aD.out_rows_per_slot = (int)rows_a; aD.out_kr = kr; aD.out_kcp = kcp;
+    aD.out_hi = B.M.hi; aD.out_lo = B.M.lo; aD.out_kr = kr; aD.out_kcp = kcp;
     aD.n = n;
-    // GEMM with e_q'': rows (nu, b), K = c ; epilogue writes X
-    aA.rows = (int)rows_a; aA.tiles = (int)((rows_a + kBoxRows - 1) / kBoxRows);
-    aA.np = np; aA.mg = mg; aA.n_groups = n_groups; aA.nk = nk; aA.stages = st_e;
+    aA.np = np; aA.mg = mg; aA.n_groups = P.n_groups; aA.nk = P.nk; aA.stages = P.st_e;
     aA.n_acc = (4 * mg <= 512) ? 2 : 1;
     aA.tmem_cols = tmem_cols_for(2 * mg, aA.n_acc);
-    aA.a_rows_per_problem = (int)rows_a;
     aA.status = aD.status;
-    aA.out_hi = opX.hi; aA.out_lo = opX.lo; aA.out_rows_per_slot = (int)rows_a; aA.out_kr = kr; aA.out_kcp = kcp;
+    aA.out_hi = B.X.hi; aA.out_lo = B.X.lo; aA.out_kr = kr; aA.out_kcp = kcp;
     aA.n = n;
-    // GEMM with e_q': rows (nu, nu''), K = b ; fused linewidth epilogue
-    aB.rows = (int)rows_a; aB.tiles = aA.tiles;
-    aB.np = np; aB.mg = mg; aB.n_groups = n_groups; aB.nk = nk; aB.stages = st_e; aB.n_acc = aA.n_acc;
+    aB.np = np; aB.mg = mg; aB.n_groups = P.n_groups; aB.nk = P.nk; aB.stages = P.st_e; aB.n_acc = aA.n_acc;
     aB.tmem_cols = aA.tmem_cols;
-    aB.a_rows_per_problem = (int)rows_a;
     aB.status = aD.status;
-    aB.n = n; aB.freq = freq; aB.nB = nB; aB.nu0 = 0;
+    aB.n = n; aB.freq = freq; aB.nB = nB;
     aB.m1 = f->mesh[0]; aB.m2 = f->mesh[1]; aB.m3 = f->mesh[2];
     aB.sigma = (float)gp.sigma; aB.window = (float)gp.window; aB.f_min = (float)gp.f_min; aB.shape = gp.shape;
 
     for (int si = 0; si < n_irr; ++si) {
         const int iq = irr_host[si];
         const int k1 = iq / (f->mesh[1] * f->mesh[2]), k2 = (iq / f->mesh[2]) % f->mesh[1], k3 = iq % f->mesh[2];
-        PHX_CUDA_CHECK(ctx, phx_launch_third_index(iq, f->mesh, qpp, s));
-        ctx->launches += 1;
-        {
-            const int pblocks = (int)std::min<int64_t>((f->nnz + n2 + 255) / 256, 4096);
-            fold_phase_kernel<<<pblocks, 256, 0, s>>>(f->ent_r2, f->ent_w, f->nnz, (double)k1 / f->mesh[0],
-                                                      (double)k2 / f->mesh[1], (double)k3 / f->mesh[2], wph,
-                                                      (const double2*)evec + (int64_t)iq * n2, (int)n2, eqf);
-            PHX_CUDA_CHECK(ctx, cudaGetLastError());
-            ctx->launches += 1;
-        }
+        PHX_CUDA_CHECK(ctx, phx_launch_third_index(iq, f->mesh, B.qpp, s));
+        const int pblocks = (int)std::min<int64_t>((f->nnz + n2 + 255) / 256, 4096);
+        fold_phase_kernel<<<pblocks, 256, 0, s>>>(f->ent_r2, f->ent_w, f->nnz, (double)k1 / f->mesh[0],
+                                                  (double)k2 / f->mesh[1], (double)k3 / f->mesh[2], B.wph,
+                                                  (const double2*)evec + (int64_t)iq * n2, (int)n2, B.eqf);
+        PHX_CUDA_CHECK(ctx, cudaGetLastError());
+        ctx->launches += 2;
         aB.iq = iq;
         aB.gacc = gacc + (int64_t)si * n;
         aB.wacc = wacc ? wacc + (int64_t)si * n : nullptr;
@@ -810,8 +862,8 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
             {
                 const int pf = phx_prof_begin(ctx, s);
                 const int blocks = (int)std::min<int64_t>((rw + 7) / 8, (int64_t)sms * 32);
-                fold_tc_kernel<PREC><<<blocks, 256, 0, s>>>(seg_of, f->seg_start, f->ent_a, wph, f->n_d, eqf, n, nu0,
-                                                            (int)rw, kcp_d, opW.hi, opW.lo);
+                fold_tc_kernel<PREC><<<blocks, 256, 0, s>>>(f->tc_seg_of, f->seg_start, f->ent_a, B.wph, f->n_d, B.eqf,
+                                                            n, nu0, (int)rw, kcp_d, B.W.hi, B.W.lo);
                 PHX_CUDA_CHECK(ctx, cudaGetLastError());
                 phx_prof_end(ctx, pf, s, PHX_K_FOLD, 8.0 * (double)f->nnz * nnu, (double)rw * kr_d * esz * planes);
                 ctx->launches += 1;
@@ -822,7 +874,7 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
             aA.a_rows_per_problem = (int)ra; aA.out_rows_per_slot = (int)ra;
             aB.rows = (int)ra; aB.tiles = aA.tiles; aB.a_rows_per_problem = (int)ra;
             aB.nu0 = nu0;
-            for (int tq = 0; tq < n_tiles_q; ++tq) {
+            for (int tq = 0; tq < P.n_tiles_q; ++tq) {
                 const int t0 = tq * Q, Qt = std::min(Q, nq - t0);
                 aD.b_base = tq;
                 aD.nq_slots = Qt;
@@ -833,20 +885,32 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
                 int pp = phx_prof_begin(ctx, s);
                 PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_M, false>(ctx, aD, 1, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_DFT, fl_d, op_bytes * ((double)rw * f->n_d + (double)Qt * ra * n));
-                aA.b_idx = qpp + t0;
+                aA.b_idx = B.qpp + t0;
                 pp = phx_prof_begin(ctx, s);
-                PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_X>(ctx, aA, stream_b, Qt, sms, s)));
+                PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_X>(ctx, aA, P.stream_b, Qt, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_GEMM_E2, fl_e, op_bytes * 2.0 * Qt * ra * n);
-                aB.b_idx = ident + t0;
+                aB.b_idx = f->tc_ident + t0;
                 aB.t0 = t0;
                 pp = phx_prof_begin(ctx, s);
-                PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_G>(ctx, aB, stream_b, Qt, sms, s)));
+                PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_G>(ctx, aB, P.stream_b, Qt, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_GEMM_E1, fl_e, op_bytes * (double)Qt * ra * n);
                 ctx->launches += 3;
             }
         }
     }
     return PHX_OK;
+}
+
+template <int PREC>
+phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec, const double* nB,
+                  const int32_t* irr_host, int n_irr, const GammaParams& gp, double* gacc, double* wacc,
+                  cudaStream_t s) {
+    TcPlan P;
+    PHX_TRY(tc_plan(ctx, f, PREC, 0, &P));
+    PHX_TRY(tc_prepare_fc3(ctx, const_cast<phx_fc3*>(f)));
+    TcBuffers B;
+    PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.bytes_e, P.bytes_p, P.nq, f->nnz, (int64_t)P.n * P.n, &B));
+    return tc_enqueue<PREC>(ctx, P, f, B, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s);
 }
 
 }  // namespace
@@ -858,4 +922,206 @@ phx_status phx_gamma_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, cons
         return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path needs a Blackwell (sm_10x) device");
     if (prec == PHX_BF16X3) return run_tc<P_BF16X3>(ctx, f, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s);
     return run_tc<P_TF32>(ctx, f, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s);
+}
+
+// ---------------------------------------------------------------- batched jobs (one CUDA graph)
+
+namespace {
+
+template <int PREC>
+phx_status autotune_q(phx_ctx* ctx, const phx_job& job, cudaStream_t s, int* best_q) {
+    const phx_fc3* f = job.fc3;
+    const int iq = job.irr_q[job.n_irr > 1 ? 1 : 0];
+    GammaParams gp{};
+    gp.n = f->n; gp.nq = f->nq; gp.T = job.temperature; gp.shape = job.br.shape; gp.sigma = job.br.sigma_thz;
+    gp.window = job.br.window; gp.f_min = job.f_min_thz;
+    double* nB = (double*)phx_ws(ctx, "b.nB", (size_t)f->nq * f->n * 8);
+    double* gacc = (double*)phx_ws(ctx, "b.gacc", (size_t)f->n * 8);
+    if (!nB || !gacc) return PHX_ERR_NOMEM;
+    PHX_CUDA_CHECK(ctx, phx_launch_occupations(job.freq_thz, f->nq * f->n, job.temperature, 0, nB, nullptr, s));
+    float best_ms = 1e30f;
+    int last_q = -1;
+    *best_q = 0;
+    for (int cand : {8, 16, 32, 64, 128}) {
+        TcPlan P;
+        if (tc_plan(ctx, f, PREC, cand, &P) != PHX_OK) continue;
+        if (P.Q == last_q) continue;                 // clamped to the mesh size already tried
+        last_q = P.Q;
+        TcBuffers B;
+        PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.bytes_e, P.bytes_p, P.nq, f->nnz, (int64_t)P.n * P.n, &B));
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_in, s));
+            PHX_TRY(tc_enqueue<PREC>(ctx, P, f, B, job.freq_thz, job.evec, nB, &iq, 1, gp, gacc, nullptr, s));
+            PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_out, s));
+            PHX_CUDA_CHECK(ctx, cudaEventSynchronize(ctx->ev_out));
+            PHX_CUDA_CHECK(ctx, cudaEventElapsedTime(&ms, ctx->ev_in, ctx->ev_out));
+        }
+        if (ms < best_ms) { best_ms = ms; *best_q = P.Q; }
+    }
+    if (*best_q == 0) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "autotune: no q' tile fits");
+    return PHX_OK;
+}
+
+template <int PREC>
+phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, const phx_tune* tune, cudaStream_t user) {
+    if (!ctx->cap_stream) {
+        PHX_CUDA_CHECK(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        PHX_CUDA_CHECK(ctx, cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDefault));
+        PHX_CUDA_CHECK(ctx, cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDefault));
+    }
+    cudaStream_t cs = ctx->cap_stream;
+    // the batch starts after the work already queued on the caller's stream
+    PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_in, user));
+    PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(cs, ctx->ev_in, 0));
+
+    // plans (q' tile from the caller, the autotune table, or a fresh tuning run)
+    std::vector<TcPlan> plans(n_jobs);
+    std::vector<int> qtiles(n_jobs, 0);
+    for (int j = 0; j < n_jobs; ++j) {
+        const phx_job& jb = jobs[j];
+        PHX_TRY(tc_prepare_fc3(ctx, const_cast<phx_fc3*>(jb.fc3)));
+        int q = (tune && tune[j].q_tile > 0) ? tune[j].q_tile : 0;
+        if (q == 0) {
+            const std::vector<int> key = {PREC, jb.fc3->n, jb.fc3->mesh[0], jb.fc3->mesh[1], jb.fc3->mesh[2], jb.fc3->n_d};
+            auto it = ctx->tune_q.find(key);
+            if (it == ctx->tune_q.end()) {
+                PHX_TRY(autotune_q<PREC>(ctx, jb, cs, &q));
+                ctx->tune_q[key] = q;
+            } else {
+                q = it->second;
+            }
+        }
+        qtiles[j] = q;
+        PHX_TRY(tc_plan(ctx, jb.fc3, PREC, q, &plans[j]));
+    }
+    // workspace for the largest job, allocated before any capture
+    size_t bw = 0, bm = 0, be = 0, bp = 0;
+    int64_t mnq = 1, mnnz = 1, mn2 = 1, mnb = 1, mg = 1;
+    for (int j = 0; j < n_jobs; ++j) {
+        const TcPlan& P = plans[j];
+        bw = std::max(bw, P.bytes_w); bm = std::max(bm, P.bytes_m); be = std::max(be, P.bytes_e);
+        bp = std::max(bp, P.bytes_p);
+        mnq = std::max<int64_t>(mnq, P.nq); mnnz = std::max<int64_t>(mnnz, jobs[j].fc3->nnz);
+        mn2 = std::max<int64_t>(mn2, (int64_t)P.n * P.n);
+        mnb = std::max<int64_t>(mnb, (int64_t)P.nq * P.n);
+        mg = std::max<int64_t>(mg, (int64_t)jobs[j].n_irr * P.n);
+    }
+    TcBuffers B;
+    PHX_TRY(tc_alloc(ctx, PREC, bw, bm, be, bp, mnq, mnnz, mn2, &B));
+    double* nB = (double*)phx_ws(ctx, "b.nB", (size_t)mnb * 8);
+    double* gacc = (double*)phx_ws(ctx, "b.gacc", (size_t)mg * 8);
+    double* acc9 = (double*)phx_ws(ctx, "b.acc9", (size_t)n_jobs * 9 * 8);
+    if (!nB || !gacc || !acc9) return PHX_ERR_NOMEM;
+
+    // graph key: the job list, the precision and the tiles
+    std::vector<uint8_t> key(sizeof(phx_job) * n_jobs + sizeof(int) * (n_jobs + 1));
+    std::memcpy(key.data(), jobs, sizeof(phx_job) * n_jobs);
+    std::memcpy(key.data() + sizeof(phx_job) * n_jobs, qtiles.data(), sizeof(int) * n_jobs);
+    const int prec_v = PREC;
+    std::memcpy(key.data() + sizeof(phx_job) * n_jobs + sizeof(int) * n_jobs, &prec_v, sizeof(int));
+    // host irr lists are part of the key by content
+    for (int j = 0; j < n_jobs; ++j) {
+        const uint8_t* b = (const uint8_t*)jobs[j].irr_q;
+        key.insert(key.end(), b, b + sizeof(int32_t) * jobs[j].n_irr);
+    }
+    if (!ctx->graph_exec || key != ctx->graph_key) {
+        if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+        const bool prof = ctx->prof;
+        ctx->prof = false;                     // event records are not captured
+        const int64_t l0 = ctx->launches;
+        PHX_CUDA_CHECK(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        phx_status st = PHX_OK;
+        for (int j = 0; j < n_jobs && st == PHX_OK; ++j) {
+            const phx_job& jb = jobs[j];
+            const TcPlan& P = plans[j];
+            const phx_fc3* f = jb.fc3;
+            GammaParams gp{};
+            gp.n = f->n; gp.nq = f->nq; gp.T = jb.temperature; gp.shape = jb.br.shape; gp.sigma = jb.br.sigma_thz;
+            gp.window = jb.br.window; gp.f_min = jb.f_min_thz;
+            if (phx_launch_occupations(jb.freq_thz, f->nq * f->n, jb.temperature, 0, nB, nullptr, cs) != cudaSuccess ||
+                cudaMemsetAsync(gacc, 0, (size_t)jb.n_irr * f->n * 8, cs) != cudaSuccess) {
+                st = phx_set_error(ctx, PHX_ERR_CUDA, "batched: launch failed during capture");
+                break;
+            }
+            ctx->launches += 1;
+            st = tc_enqueue<PREC>(ctx, P, f, B, jb.freq_thz, jb.evec, nB, jb.irr_q, jb.n_irr, gp, gacc, nullptr, cs);
+            if (st != PHX_OK) break;
+            const double conv = phx::kEvA2AmuToPs2;
+            const double pref = phx::kPi * phx::kHbarEvPs * conv * conv * conv / (8.0 * f->nq);
+            // the irreducible list also has to be on the device for the finalize kernel
+            const int32_t* irr_dev = jb.irr_q_dev;
+            if (!irr_dev) { st = phx_set_error(ctx, PHX_ERR_INVALID, "batched: job %d has no irr_q_dev", j); break; }
+            if (phx_launch_finalize(jb.n_irr * f->n, f->n, irr_dev, jb.freq_thz, gacc, nullptr, pref, 1.0 / f->nq,
+                                    jb.f_min_thz, jb.gamma, nullptr, cs) != cudaSuccess) {
+                st = phx_set_error(ctx, PHX_ERR_CUDA, "batched: finalize launch failed");
+                break;
+            }
+            ctx->launches += 1;
+            if (jb.vv) {
+                double* a9 = acc9 + 9 * j;
+                if (phx_launch_unfold(jb.n_irr, f->nq, f->n, jb.freq_thz, irr_dev, jb.gamma, jb.full_to_irr,
+                                      jb.gamma_full, cs) != cudaSuccess ||
+                    cudaMemsetAsync(a9, 0, 72, cs) != cudaSuccess ||
+                    phx_launch_kappa(f->nq, f->n, jb.freq_thz, nullptr, jb.vv, jb.gamma_full, jb.temperature,
+                                     jb.f_min_thz, 0, a9, cs) != cudaSuccess ||
+                    phx_launch_scale9(a9, phx::kEvPsAKToWmK / ((double)f->nq * jb.volume), jb.kappa, cs) !=
+                        cudaSuccess) {
+                    st = phx_set_error(ctx, PHX_ERR_CUDA, "batched: conductivity launch failed");
+                    break;
+                }
+                ctx->launches += 3;
+            }
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+        ctx->prof = prof;
+        if (st != PHX_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (ec != cudaSuccess) return phx_set_error(ctx, PHX_ERR_CUDA, "batched: capture failed: %s", cudaGetErrorString(ec));
+        const cudaError_t ei = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            ctx->graph_exec = nullptr;
+            return phx_set_error(ctx, PHX_ERR_CUDA, "batched: instantiate failed: %s", cudaGetErrorString(ei));
+        }
+        ctx->graph_key = key;
+        ctx->graph_launches = ctx->launches - l0;
+        ctx->launches = l0;
+    }
+    PHX_CUDA_CHECK(ctx, cudaGraphLaunch(ctx->graph_exec, cs));
+    ctx->launches += ctx->graph_launches;
+    PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_out, cs));
+    PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(user, ctx->ev_out, 0));
+    return PHX_OK;
+}
+
+}  // namespace
+
+extern "C" phx_status phx_gamma_batched(phx_ctx* ctx, int32_t n_jobs, const phx_job* jobs, int32_t prec,
+                                        const phx_tune* tune, void* stream) {
+    if (!ctx) return PHX_ERR_INVALID;
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_batched: bad job list");
+    if (n_jobs == 0) return PHX_OK;
+    if (prec != PHX_BF16X3 && prec != PHX_TF32)
+        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "phx_gamma_batched: tensor-core precisions only");
+    if (ctx->cc_major != 10)
+        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path needs a Blackwell (sm_10x) device");
+    for (int j = 0; j < n_jobs; ++j) {
+        const phx_job& jb = jobs[j];
+        if (!jb.fc3 || jb.fc3->ctx != ctx || !jb.freq_thz || !jb.evec || !jb.gamma || jb.n_irr <= 0 || !jb.irr_q ||
+            !jb.irr_q_dev)
+            return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_batched: job %d incomplete", j);
+        if (!(jb.temperature > 0.0) || !(jb.br.sigma_thz > 0.0) || !(jb.br.window > 0.0) || !(jb.f_min_thz > 0.0) ||
+            (jb.br.shape != PHX_GAUSS && jb.br.shape != PHX_LORENTZ))
+            return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_batched: job %d parameters", j);
+        for (int i = 0; i < jb.n_irr; ++i)
+            if (jb.irr_q[i] < 0 || jb.irr_q[i] >= jb.fc3->nq)
+                return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_batched: job %d irr_q[%d] outside the mesh", j, i);
+        if (jb.vv && (!jb.full_to_irr || !jb.gamma_full || !jb.kappa || !(jb.volume > 0.0)))
+            return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_batched: job %d conductivity arguments", j);
+    }
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == PHX_BF16X3) return run_batched<P_BF16X3>(ctx, n_jobs, jobs, tune, s);
+    return run_batched<P_TF32>(ctx, n_jobs, jobs, tune, s);
 }

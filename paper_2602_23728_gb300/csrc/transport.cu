@@ -87,7 +87,16 @@ __global__ void kappa_kernel(int count, const double* __restrict__ freq, const d
     }
 }
 
+__global__ void scale9_kernel(const double* __restrict__ acc, double scale, double* __restrict__ out) {
+    if (threadIdx.x < 9) out[threadIdx.x] = acc[threadIdx.x] * scale;
+}
+
 }  // namespace
+
+cudaError_t phx_launch_scale9(const double* acc, double scale, double* out, cudaStream_t s) {
+    scale9_kernel<<<1, 32, 0, s>>>(acc, scale, out);
+    return cudaGetLastError();
+}
 
 cudaError_t phx_launch_occupations(const double* freq, int count, double T, int is_classic,
                                    double* nB, double* cV, cudaStream_t s) {

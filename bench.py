@@ -408,6 +408,83 @@ def run_phx(args):
     return 0
 
 
+def run_batched(args):
+    """Many crystals in one captured graph: the first 16 jobs of the seeded 64-cell sweep (or
+    all 64 with --workload batched64).  Prints its own JSON line."""
+    import torch
+    import paper_2602_23728_gb300 as phx
+    import phx_inputs as P
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctx = phx.Context(0)
+    n_take = 64 if args.workload == "batched64" else 16
+    sweep = P.batched_sweep()[:n_take]
+    jobs, trip = [], 0
+    t_setup = time.perf_counter()
+    for w in sweep:
+        c = w.crystal
+        f2, f3 = w.ifc2(), w.ifc3()
+        n = c.n_modes
+        nq = int(np.prod(w.mesh))
+        m = w.mesh
+        qh = np.array([(i // (m[1] * m[2]) / m[0], (i // m[2]) % m[1] / m[1], i % m[2] / m[2]) for i in range(nq)])
+        q = torch.from_numpy(qh).to(dev)
+        freq = torch.zeros((nq, n), dtype=torch.float64, device=dev)
+        evec = torch.zeros((nq, n, n), dtype=torch.complex128, device=dev)
+        vv = torch.zeros((nq, n, 3, 3), dtype=torch.float64, device=dev)
+        ctx.harmonic(c.lattice, c.masses, f2.idx, f2.val.reshape(-1, 9), q, freq=freq, evec=evec, vv=vv,
+                     want_vel=False)
+        irr, f2i, _ = phx.irreducible(w.mesh, w.rotations)
+        h = ctx.fc3(c.lattice, c.masses, f3.idx, f3.val, w.mesh)
+        fr = freq.cpu().numpy()
+        trip += int((fr[irr] >= w.f_min_thz).sum()) * nq * n * n
+        jobs.append(dict(fc3=h, freq=freq, evec=evec, irr=irr, irr_dev=torch.from_numpy(irr.astype(np.int32)).to(dev),
+                         T=w.temperature, shape=w.shape, sigma=w.sigma_thz, window=w.window, f_min=w.f_min_thz,
+                         gamma=torch.zeros((len(irr), n), dtype=torch.float64, device=dev), vv=vv,
+                         full_to_irr=torch.from_numpy(f2i.astype(np.int32)).to(dev),
+                         gamma_full=torch.zeros((nq, n), dtype=torch.float64, device=dev),
+                         kappa=torch.zeros(9, dtype=torch.float64, device=dev), volume=c.volume))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    t0 = time.perf_counter()
+    ctx.gamma_batched(jobs, precision=args.precision)            # autotune + capture + first run
+    torch.cuda.synchronize()
+    t_first = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.gamma_batched(jobs, precision=args.precision)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # the same jobs as sequential single-job calls (no graph, default tiles)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for j in jobs:
+        ctx.gamma(j["fc3"], j["freq"], j["evec"], j["irr_dev"], j["T"], j["shape"], j["sigma"], j["window"],
+                  j["f_min"], precision=args.precision, gamma=torch.zeros_like(j["gamma"]))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    sizes = [(3 * w.crystal.n_atoms, w.mesh[0]) for w in sweep]
+    line = {"metric": METRIC, "value": trip / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"batched sweep: first {n_take} of 64 seeded mass-disordered LJ fcc cells "
+                                   "(seed 3), (modes, mesh edge) = " + json.dumps(sizes),
+                       "triplets_per_step": trip, "jobs": n_take},
+            "sequential_single_job_calls": {"value": trip / (ms_seq / 1e3), "ms": ms_seq},
+            "first_call_s_incl_autotune_and_capture": t_first, "setup_s": t_setup}
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,11 +496,15 @@ def main():
     ap.add_argument("--cpu-qp", type=int, default=None, help="q' of the oracle sample (default all)")
     ap.add_argument("--ref-qp", type=int, default=64, help="q' per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="fcc32", choices=["fcc32", "batched16", "batched64"],
+                    help="fcc32: the headline workload; batched16/64: the many-crystal sweep (own JSON line)")
     ap.add_argument("--irr-limit", type=int, default=0,
                     help="profiling aid: process only the first N irreducible q per step (0: all)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("batched16", "batched64"):
+        return run_batched(args)
     return run_phx(args)
 
 

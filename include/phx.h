@@ -194,6 +194,45 @@ typedef struct {
 phx_status phx_gamma_batched(phx_ctx* ctx, int32_t n_jobs, const phx_job* jobs, int32_t prec,
                              const phx_tune* tune, void* stream);
 
+/* ---------------------------------------------------------------- learned linewidths
+ * No counterpart in the paper's equations: a small MLP ensemble that predicts log(gamma) on a
+ * dense mesh from per-mode descriptors, trained on exact linewidths of a coarse subgrid by the
+ * library's own forward/backward/Adam kernels (FP32).  All arrays are device memory.
+ *
+ * phx_features: descriptors of every band of the irreducible q-points irr_q[n_irr] of a mesh:
+ *   features[s][nu][4] = (w in rad/ps, |v| in A/ps, WP2 in ps^4, n_B), where WP2 is the sum of
+ *   Eq. (gamma) with |Phi|^2 -> 1 and without pi hbar/8 (same weights, window and f_min as
+ *   phx_gamma), over the full mesh.  freq_thz[nq][n], vel[nq][n][3] cover the full mesh.
+ *   n <= 192.  Enqueued on stream. */
+typedef struct phx_mlp phx_mlp;
+phx_status phx_features(phx_ctx* ctx, const int32_t mesh[3], int32_t n, const double* freq_thz,
+                        const double* vel, const int32_t* irr_q, int32_t n_irr, double temperature,
+                        phx_broadening br, double f_min_thz, double* features, void* stream);
+/* Ensemble of `ensemble` MLPs n_in -> width (x depth hidden layers, SiLU) -> 1, initialised
+ * from a counter-based generator seeded by `seed` (weights U(-sqrt(6/fan_in), +), biases 0).
+ * Inputs are log(max(x, 1e-12)) standardised per feature; the target is log(gamma),
+ * standardised; both standardisations are fixed by phx_mlp_train. */
+phx_status phx_mlp_create(phx_ctx* ctx, int32_t n_in, int32_t width, int32_t depth, int32_t ensemble,
+                          uint64_t seed, phx_mlp** out);
+void phx_mlp_destroy(phx_mlp* m);
+int64_t phx_mlp_num_params(const phx_mlp* m);      /* per ensemble member */
+/* Parameters [ensemble][n_params] (layer by layer: W [in][out] row-major, then b [out]) and the
+ * standardisation [mu_x (n_in), sd_x (n_in), mu_y, sd_y], host buffers (norm may be NULL). */
+phx_status phx_mlp_get_params(phx_mlp* m, float* params, float* norm);
+phx_status phx_mlp_set_params(phx_mlp* m, const float* params, const float* norm);
+/* Mean-squared loss of the standardised log(gamma) and its gradient for every member on one
+ * batch (X [rows][n_in], y [rows] device); loss [ensemble] and grad [ensemble][n_params] host
+ * (grad may be NULL).  Synchronises the stream. */
+phx_status phx_mlp_loss_grad(phx_mlp* m, const double* X, const double* y, int32_t rows, double* loss,
+                             float* grad, void* stream);
+/* Full-batch Adam (beta 0.9/0.999, eps 1e-8) for `epochs` steps at learning rate lr; sets the
+ * standardisation from this batch.  Final losses to loss[ensemble] (host, may be NULL). */
+phx_status phx_mlp_train(phx_mlp* m, const double* X, const double* y, int32_t rows, int32_t epochs,
+                         double lr, double* loss, void* stream);
+/* Ensemble mean and standard deviation of log(gamma) per row (device; stdv may be NULL). */
+phx_status phx_mlp_predict(phx_mlp* m, const double* X, int32_t rows, double* mean, double* stdv,
+                           void* stream);
+
 /* ---------------------------------------------------------------- transport
  * Map irreducible linewidths to the full mesh (Sec. "Overview of New Capabilities"):
  * gamma_full[k][nu] = gamma_irr[full_to_irr[k]][nu] after averaging gamma_irr over each

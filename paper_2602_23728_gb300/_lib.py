@@ -95,12 +95,33 @@ lib.phx_kappa_rta_noalloc.restype = C.c_int
 lib.phx_gamma_batched.argtypes = [_P, _I, _P, _I, _P, _P]
 lib.phx_gamma_batched.restype = C.c_int
 
+lib.phx_features.argtypes = [_P, _P, _I, _P, _P, _P, _I, C.c_double, Broadening, C.c_double, _P, _P]
+lib.phx_features.restype = C.c_int
+lib.phx_mlp_create.argtypes = [_P, _I, _I, _I, _I, C.c_uint64, C.POINTER(_P)]
+lib.phx_mlp_create.restype = C.c_int
+lib.phx_mlp_destroy.argtypes = [_P]
+lib.phx_mlp_destroy.restype = None
+lib.phx_mlp_num_params.argtypes = [_P]
+lib.phx_mlp_num_params.restype = C.c_int64
+lib.phx_mlp_get_params.argtypes = [_P, _P, _P]
+lib.phx_mlp_get_params.restype = C.c_int
+lib.phx_mlp_set_params.argtypes = [_P, _P, _P]
+lib.phx_mlp_set_params.restype = C.c_int
+lib.phx_mlp_loss_grad.argtypes = [_P, _P, _P, _I, _P, _P, _P]
+lib.phx_mlp_loss_grad.restype = C.c_int
+lib.phx_mlp_train.argtypes = [_P, _P, _P, _I, _I, C.c_double, _P, _P]
+lib.phx_mlp_train.restype = C.c_int
+lib.phx_mlp_predict.argtypes = [_P, _P, _I, _P, _P, _P]
+lib.phx_mlp_predict.restype = C.c_int
+
 KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4, "fp64_epilogue": 5,
            "eigensolver": 6}
 
 EXPORTED = ["phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
             "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_unfold", "phx_kappa_rta",
-            "phx_kappa_rta_noalloc", "phx_gamma_batched"]
+            "phx_kappa_rta_noalloc", "phx_gamma_batched", "phx_features", "phx_mlp_create", "phx_mlp_destroy",
+            "phx_mlp_num_params", "phx_mlp_get_params", "phx_mlp_set_params", "phx_mlp_loss_grad", "phx_mlp_train",
+            "phx_mlp_predict"]
 
 
 class PhxError(RuntimeError):
@@ -325,6 +346,24 @@ class Context:
         self._check(lib.phx_gamma_batched(self.h, len(jobs), C.addressof(arr), PRECISIONS[precision],
                                           C.addressof(tune) if tune is not None else None, stream))
 
+    # ------------------------------------------------------------------ learned linewidths
+    def features(self, mesh, freq, vel, irr_dev, temperature, shape="gauss", sigma=0.1, window=2.0, f_min=0.01,
+                 out=None):
+        """phx_features on CUDA tensors: out [n_irr][n][4] (created when None)."""
+        import torch
+        mesh_a = np.asarray(mesh, dtype=np.int32)
+        n = freq.shape[1]
+        if out is None:
+            out = torch.zeros((irr_dev.shape[0], n, 4), dtype=torch.float64, device=freq.device)
+        br = Broadening(SHAPES[shape], float(sigma), float(window))
+        stream = torch.cuda.current_stream(freq.device).cuda_stream
+        self._check(lib.phx_features(self.h, mesh_a.ctypes.data, n, _ptr(freq), _ptr(vel), _ptr(irr_dev),
+                                     int(irr_dev.shape[0]), float(temperature), br, float(f_min), _ptr(out), stream))
+        return out
+
+    def mlp(self, n_in=4, width=128, depth=3, ensemble=4, seed=0):
+        return MLP(self, n_in, width, depth, ensemble, seed)
+
     # ------------------------------------------------------------------ transport
     def unfold(self, freq_full, irr_q, gamma_irr, full_to_irr, out=None):
         """phx_unfold: irreducible linewidths (degenerate-averaged) onto the full mesh."""
@@ -354,6 +393,64 @@ class Context:
                                       _ptr(vv), _ptr(gamma_full), float(temperature), float(f_min), int(is_classic),
                                       k.ctypes.data, mem, stream))
         return k.reshape(3, 3)
+
+
+class MLP:
+    """Handle of a phx_mlp ensemble (device parameters; device inputs)."""
+
+    def __init__(self, ctx, n_in, width, depth, ensemble, seed):
+        h = _P()
+        ctx._check(lib.phx_mlp_create(ctx.h, n_in, width, depth, ensemble, int(seed), C.byref(h)))
+        self.ctx, self.h = ctx, h
+        self.n_in, self.width, self.depth, self.ensemble = n_in, width, depth, ensemble
+        self.n_params = int(lib.phx_mlp_num_params(h))
+
+    def _stream(self, x):
+        import torch
+        return torch.cuda.current_stream(x.device).cuda_stream
+
+    def get_params(self):
+        p = np.zeros((self.ensemble, self.n_params), np.float32)
+        nrm = np.zeros(2 * self.n_in + 2, np.float32)
+        self.ctx._check(lib.phx_mlp_get_params(self.h, p.ctypes.data, nrm.ctypes.data))
+        return p, nrm
+
+    def set_params(self, params, norm=None):
+        p = np.ascontiguousarray(params, np.float32)
+        nrm = None if norm is None else np.ascontiguousarray(norm, np.float32)
+        self.ctx._check(lib.phx_mlp_set_params(self.h, p.ctypes.data, None if nrm is None else nrm.ctypes.data))
+
+    def loss_grad(self, X, y):
+        loss = np.zeros(self.ensemble)
+        g = np.zeros((self.ensemble, self.n_params), np.float32)
+        self.ctx._check(lib.phx_mlp_loss_grad(self.h, _ptr(X), _ptr(y), int(X.shape[0]), loss.ctypes.data,
+                                              g.ctypes.data, self._stream(X)))
+        return loss, g
+
+    def train(self, X, y, epochs, lr=3e-3):
+        loss = np.zeros(self.ensemble)
+        self.ctx._check(lib.phx_mlp_train(self.h, _ptr(X), _ptr(y), int(X.shape[0]), int(epochs), float(lr),
+                                          loss.ctypes.data, self._stream(X)))
+        return loss
+
+    def predict(self, X, mean=None, std=None):
+        import torch
+        rows = X.shape[0]
+        mean = torch.zeros(rows, dtype=torch.float64, device=X.device) if mean is None else mean
+        std = torch.zeros(rows, dtype=torch.float64, device=X.device) if std is None else std
+        self.ctx._check(lib.phx_mlp_predict(self.h, _ptr(X), rows, _ptr(mean), _ptr(std), self._stream(X)))
+        return mean, std
+
+    def close(self):
+        if self.h:
+            lib.phx_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kappa_rta_noalloc(lattice, masses, freq, gamma_full, temperature, out, vel=None, vv=None, f_min=0.01,

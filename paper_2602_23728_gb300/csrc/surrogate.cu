@@ -1,0 +1,641 @@
+// Learned linewidths: descriptor kernel and a small MLP ensemble trained and evaluated with
+// the library's own kernels (no counterpart in the paper; the descriptors restate its
+// quantities: w, |v| (Eq. groupvel), the weighted two-phonon phase space of Eqs. (gamma) and
+// (broadening) with |Phi|^2 -> 1, and n_B (Eq. bose)).
+//
+//  features_kernel   per irreducible mode: sum over q' and partner bands of the occupation /
+//                    smearing weight without V3 (FP32, ALU bound)
+//  gemm_f32_kernel   C = op(A) op(B) (+ bias, SiLU), batched over ensemble members; the
+//                    forward, weight-gradient and input-gradient products of every layer
+//  small kernels     input transform, loss and its gradient, SiLU backward, bias gradient,
+//                    Adam, ensemble mean/std
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.h"
+#include "gamma_common.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------- descriptors
+
+// Block (s, chunk of q'): every thread takes one q' and loops over (nu, nu', nu''); the
+// per-band sums are reduced in shared memory and added once per block.
+__global__ void __launch_bounds__(256)
+features_kernel(const double* __restrict__ freq, const double* __restrict__ nB, const int32_t* __restrict__ irr,
+                int n, int m1, int m2, int m3, float sigma, float window, int shape, float f_min,
+                double* __restrict__ wsum) {
+    __shared__ float red[192];
+    const int nq = m1 * m2 * m3;
+    const int s = blockIdx.y;
+    const int iq = irr[s];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) red[j] = 0.f;
+    __syncthreads();
+    const float lim = window * sigma;
+    const int qp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qp < nq) {
+        const int q2 = phx_third_index(iq, qp, m1, m2, m3);
+        for (int nu = 0; nu < n; ++nu) {
+            const float f0 = (float)freq[(int64_t)iq * n + nu];
+            if (!(f0 >= f_min)) continue;
+            float acc = 0.f;
+            for (int j1 = 0; j1 < n; ++j1) {
+                const float f1 = (float)freq[(int64_t)qp * n + j1];
+                if (!(f1 >= f_min)) continue;
+                const float n1 = (float)nB[(int64_t)qp * n + j1];
+                for (int j2 = 0; j2 < n; ++j2) {
+                    const float f2 = (float)freq[(int64_t)q2 * n + j2];
+                    if (!(f2 >= f_min)) continue;
+                    const float x = f0 - f1 - f2, y = f0 + f1 - f2;
+                    float gd = 0.f, ga = 0.f;
+                    if (fabsf(x) < lim)
+                        gd = shape == PHX_GAUSS ? __expf(-(x / sigma) * (x / sigma)) * (0.56418958354775628f / sigma)
+                                                : (0.5f * sigma) / (3.14159265358979f * (x * x + 0.25f * sigma * sigma));
+                    if (fabsf(y) < lim)
+                        ga = shape == PHX_GAUSS ? __expf(-(y / sigma) * (y / sigma)) * (0.56418958354775628f / sigma)
+                                                : (0.5f * sigma) / (3.14159265358979f * (y * y + 0.25f * sigma * sigma));
+                    if (gd == 0.f && ga == 0.f) continue;
+                    const float n2 = (float)nB[(int64_t)q2 * n + j2];
+                    acc += ((1.f + n1 + n2) * gd + 2.f * (n1 - n2) * ga) / (f1 * f2);
+                }
+            }
+            if (acc != 0.f) atomicAdd(&red[nu], acc);
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+        if (red[j] != 0.f) atomicAdd(&wsum[(int64_t)s * n + j], (double)red[j]);
+}
+
+// features[s][nu] = (w rad/ps, |v| A/ps, WP2 ps^4, n_B)
+__global__ void features_finish_kernel(const double* __restrict__ freq, const double* __restrict__ vel,
+                                       const double* __restrict__ nB, const int32_t* __restrict__ irr, int n_irr,
+                                       int n, int nq, double f_min, const double* __restrict__ wsum,
+                                       double* __restrict__ out) {
+    const int total = n_irr * n;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int s = t / n, nu = t % n;
+        const int64_t m = (int64_t)irr[s] * n + nu;
+        const double f0 = freq[m];
+        const double w = f0 * phx::kTwoPi;
+        const double* v = vel + m * 3;
+        const bool ok = f0 >= f_min;
+        // WP2 = (1/N_q) sum [..] / (2 pi w0 w1 w2) with the f1 f2 of the sum already divided out
+        const double tp4 = phx::kTwoPi * phx::kTwoPi * phx::kTwoPi * phx::kTwoPi;
+        out[(int64_t)t * 4 + 0] = w;
+        out[(int64_t)t * 4 + 1] = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        out[(int64_t)t * 4 + 2] = ok ? wsum[t] / (tp4 * f0) / nq : 0.0;
+        out[(int64_t)t * 4 + 3] = nB[m];
+    }
+}
+
+// ---------------------------------------------------------------- MLP kernels
+
+constexpr int TM = 64, TN = 64, TK = 16;
+
+// C_e[M x N] = op(A_e) op(B_e) (+ bias_e, then optional SiLU; the pre-activation goes to Z_e).
+// op(A) = A [M x K] (lda) or A^T with A stored [K x M]; op(B) = B [K x N] or B^T with B [N x K].
+// Batched over ensemble members e (blockIdx.z) with element strides sA, sB, sC (0 = shared).
+__global__ void __launch_bounds__(256)
+gemm_f32_kernel(int M, int N, int K, const float* __restrict__ A, int lda, int64_t sA, int tA,
+                const float* __restrict__ B, int ldb, int64_t sB, int tB, float* __restrict__ C, int ldc,
+                int64_t sC, const float* __restrict__ bias, int64_t sBias, int act, float* __restrict__ Z,
+                int accumulate) {
+    __shared__ float As[TK][TM + 1], Bs[TK][TN + 1];
+    const int e = blockIdx.z;
+    A += e * sA;
+    B += e * sB;
+    C += e * sC;
+    if (Z) Z += e * sC;
+    if (bias) bias += e * sBias;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += TK) {
+        for (int i = threadIdx.x; i < TM * TK; i += 256) {
+            int m, k;
+            if (tA) { k = i / TM; m = i % TM; } else { m = i / TK; k = i % TK; }
+            const int gm = m0 + m, gk = k0 + k;
+            float v = 0.f;
+            if (gm < M && gk < K) v = tA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
+            As[k][m] = v;
+        }
+        for (int i = threadIdx.x; i < TK * TN; i += 256) {
+            int k, nn;
+            if (tB) { nn = i / TK; k = i % TK; } else { k = i / TN; nn = i % TN; }
+            const int gn = n0 + nn, gk = k0 + k;
+            float v = 0.f;
+            if (gn < N && gk < K) v = tB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
+            Bs[k][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + tx + 16 * j;
+            if (gn >= N) continue;
+            float z = acc[i][j] + (bias ? bias[gn] : 0.f);
+            if (accumulate) z += C[(int64_t)gm * ldc + gn];
+            if (Z) Z[(int64_t)gm * ldc + gn] = z;
+            C[(int64_t)gm * ldc + gn] = act ? z / (1.f + __expf(-z)) : z;
+        }
+    }
+}
+
+// x_in = (log(max(x, floor)) - mu) / sd per feature column.
+__global__ void input_kernel(const double* __restrict__ X, int M, int F, const float* __restrict__ mu,
+                             const float* __restrict__ sd, float* __restrict__ out) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M * F; t += gridDim.x * blockDim.x) {
+        const int f = t % F;
+        const double v = fmax(X[t], 1e-12);
+        out[t] = (float)((log(v) - mu[f]) / sd[f]);
+    }
+}
+
+// column mean / std of log(max(x, floor)) (one block per column); std floored at 1e-6
+__global__ void moments_kernel(const double* __restrict__ X, int M, int F, int take_log, float* __restrict__ mu,
+                               float* __restrict__ sd) {
+    __shared__ double s1[256], s2[256];
+    const int f = blockIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        double v = X[(int64_t)i * F + f];
+        if (take_log) v = log(fmax(v, 1e-12));
+        a += v;
+        b += v * v;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) { s1[threadIdx.x] += s1[threadIdx.x + o]; s2[threadIdx.x] += s2[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double m = s1[0] / M;
+        const double var = fmax(s2[0] / M - m * m, 0.0);
+        mu[f] = (float)m;
+        sd[f] = (float)fmax(sqrt(var), 1e-6);
+    }
+}
+
+// y_std = (log(gamma) - mu) / sd
+__global__ void target_kernel(const double* __restrict__ y, int M, const float* __restrict__ mu,
+                              const float* __restrict__ sd, float* __restrict__ out) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M; t += gridDim.x * blockDim.x)
+        out[t] = (float)((log(fmax(y[t], 1e-300)) - mu[0]) / sd[0]);
+}
+
+// dZ = dA * silu'(Z)
+__global__ void silu_back_kernel(float* __restrict__ d, const float* __restrict__ Z, int64_t count) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+        const float z = Z[t];
+        const float s = 1.f / (1.f + __expf(-z));
+        d[t] *= s * (1.f + z * (1.f - s));
+    }
+}
+
+// db_e[j] = sum_i dZ_e[i][j]
+__global__ void bias_grad_kernel(const float* __restrict__ dZ, int M, int N, int64_t sZ, float* __restrict__ db,
+                                 int64_t sDb) {
+    const int e = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+        float a = 0.f;
+        for (int i = 0; i < M; ++i) a += dZ[e * sZ + (int64_t)i * N + j];
+        db[e * sDb + j] = a;
+    }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t count, float lr, float b1, float b2, float eps,
+                            const int* __restrict__ step) {
+    // bias corrections of step t (a device counter, so one captured epoch serves every step)
+    const float tt = (float)(*step);
+    const float c1 = 1.f - powf(b1, tt), c2 = 1.f - powf(b2, tt);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+        const float gt = g[t];
+        const float mt = b1 * m[t] + (1.f - b1) * gt;
+        const float vt = b2 * v[t] + (1.f - b2) * gt * gt;
+        m[t] = mt;
+        v[t] = vt;
+        p[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
+    }
+}
+
+__global__ void step_kernel(int* step) { *step += 1; }
+
+// dY = 2 (Yhat - y) / M for every member (member stride L), loss[e] += sum (Yhat - y)^2 / M
+__global__ void loss_grad_all_kernel(const float* __restrict__ yhat, const float* __restrict__ y, int M, int E,
+                                     int64_t L, float* __restrict__ dy, double* __restrict__ loss) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M * E; t += gridDim.x * blockDim.x) {
+        const int e = t / M, i = t % M;
+        const float r = yhat[e * L + i] - y[i];
+        dy[e * L + i] = 2.f * r / M;
+        if (loss) atomicAdd(&loss[e], (double)(r * r) / M);
+    }
+}
+
+// ensemble statistics of log gamma (de-standardised): mean and std over members
+__global__ void ensemble_kernel(const float* __restrict__ yhat, int M, int E, const float* __restrict__ mu,
+                                const float* __restrict__ sd, double* __restrict__ mean, double* __restrict__ stdv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+        double a = 0.0, b = 0.0;
+        for (int e = 0; e < E; ++e) {
+            const double v = (double)yhat[(int64_t)e * M + i] * sd[0] + mu[0];
+            a += v;
+            b += v * v;
+        }
+        a /= E;
+        mean[i] = a;
+        if (stdv) stdv[i] = sqrt(fmax(b / E - a * a, 0.0));
+    }
+}
+
+// counter-based initialisation: splitmix64 of (seed, member, index) -> U(-a, a)
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__global__ void init_kernel(float* __restrict__ p, int64_t count, uint64_t seed, float a) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = splitmix64(seed ^ splitmix64((uint64_t)t));
+        const float u = (float)((r >> 11) * (1.0 / 9007199254740992.0));
+        p[t] = a * (2.f * u - 1.f);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- model object
+
+struct phx_mlp {
+    phx_ctx* ctx = nullptr;
+    int n_in = 4, width = 128, depth = 3, E = 4;
+    uint64_t seed = 0;
+    // per member parameter block: [W0 (in x w), b0 (w), W1 (w x w), b1, ..., Wd (w x 1), bd (1)]
+    std::vector<int64_t> w_off, b_off, w_rows, w_cols;
+    int64_t n_par = 0;                         // per member
+    float *par = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
+    float *mu = nullptr, *sd = nullptr;        // input (n_in) and target (1) standardisation
+    float *ymu = nullptr, *ysd = nullptr;
+    int64_t cap = 0;                           // activation buffers capacity (rows)
+    float *act = nullptr, *pre = nullptr;      // [depth+2][E][rows][width]
+    float *xin = nullptr, *ystd = nullptr, *dbuf0 = nullptr, *dbuf1 = nullptr;
+    double* loss = nullptr;
+    int* step = nullptr;                       // Adam step counter (device)
+};
+
+namespace {
+
+phx_status mlp_reserve(phx_mlp* m, int64_t rows) {
+    if (rows <= m->cap) return PHX_OK;
+    cudaFree(m->act); cudaFree(m->pre); cudaFree(m->xin); cudaFree(m->ystd); cudaFree(m->dbuf0); cudaFree(m->dbuf1);
+    const int64_t layer = (int64_t)m->E * rows * m->width;
+    bool ok = cudaMalloc(&m->act, sizeof(float) * layer * (m->depth + 2)) == cudaSuccess &&
+              cudaMalloc(&m->pre, sizeof(float) * layer * (m->depth + 2)) == cudaSuccess &&
+              cudaMalloc(&m->xin, sizeof(float) * rows * m->n_in) == cudaSuccess &&
+              cudaMalloc(&m->ystd, sizeof(float) * rows) == cudaSuccess &&
+              cudaMalloc(&m->dbuf0, sizeof(float) * layer) == cudaSuccess &&
+              cudaMalloc(&m->dbuf1, sizeof(float) * layer) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        m->cap = 0;
+        return phx_set_error(m->ctx, PHX_ERR_NOMEM, "mlp: activation buffers");
+    }
+    m->cap = rows;
+    return PHX_OK;
+}
+
+cudaError_t gemm(int M, int N, int K, const float* A, int lda, int64_t sA, int tA, const float* B, int ldb,
+                 int64_t sB, int tB, float* C, int ldc, int64_t sC, const float* bias, int64_t sBias, int act, float* Z,
+                 int E, int accumulate, cudaStream_t s) {
+    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, E);
+    gemm_f32_kernel<<<grid, 256, 0, s>>>(M, N, K, A, lda, sA, tA, B, ldb, sB, tB, C, ldc, sC, bias, sBias, act, Z,
+                                         accumulate);
+    return cudaGetLastError();
+}
+
+// layer l: input width in_l, output width out_l
+int in_w(const phx_mlp* m, int l) { return l == 0 ? m->n_in : m->width; }
+int out_w(const phx_mlp* m, int l) { return l == m->depth ? 1 : m->width; }
+
+}  // namespace
+
+// Forward pass of every member on rows of xin: act[l + 1] = layer-l output, pre[l + 1] its
+// pre-activation (act[0] is unused: layer 0 reads xin).
+static phx_status mlp_forward(phx_mlp* m, int rows, cudaStream_t s) {
+    const int64_t L = (int64_t)rows * m->width;
+    const int64_t layer = (int64_t)m->E * L;
+    for (int l = 0; l <= m->depth; ++l) {
+        const float* in = l == 0 ? m->xin : m->act + (int64_t)l * layer;
+        const int64_t s_in = l == 0 ? 0 : L;
+        float* out = m->act + (int64_t)(l + 1) * layer;
+        float* z = m->pre + (int64_t)(l + 1) * layer;
+        const int ow = out_w(m, l);
+        PHX_CUDA_CHECK(m->ctx, gemm(rows, ow, in_w(m, l), in, in_w(m, l), s_in, 0, m->par + m->w_off[l], ow, m->n_par,
+                                    0, out, ow, L, m->par + m->b_off[l], m->n_par, l < m->depth ? 1 : 0, z, m->E, 0,
+                                    s));
+    }
+    return PHX_OK;
+}
+
+// Backward pass for loss gradient dy [E][rows] (in dbuf); fills m->grad.
+static phx_status mlp_backward(phx_mlp* m, int rows, cudaStream_t s) {
+    const int64_t L = (int64_t)rows * m->width;
+    const int64_t layer = (int64_t)m->E * L;
+    float* d = m->dbuf0;    // gradient w.r.t. the output of layer l (post-activation)
+    float* dn = m->dbuf1;
+    for (int l = m->depth; l >= 0; --l) {
+        const int iw = in_w(m, l), ow = out_w(m, l);
+        if (l < m->depth) {
+            const int64_t cnt = (int64_t)m->E * rows * ow;
+            silu_back_kernel<<<(int)std::min<int64_t>((cnt + 255) / 256, 4096), 256, 0, s>>>(
+                d, m->pre + (int64_t)(l + 1) * layer, cnt);
+            PHX_CUDA_CHECK(m->ctx, cudaGetLastError());
+        }
+        // d is [E][rows][ow] with member stride L
+        const float* in = l == 0 ? m->xin : m->act + (int64_t)l * layer;
+        const int64_t s_in = l == 0 ? 0 : L;
+        // dW = in^T d : [iw x ow]
+        PHX_CUDA_CHECK(m->ctx, gemm(iw, ow, rows, in, iw, s_in, 1, d, ow, L, 0, m->grad + m->w_off[l], ow, m->n_par,
+                                    nullptr, 0, 0, nullptr, m->E, 0, s));
+        bias_grad_kernel<<<dim3((ow + 127) / 128, m->E), 128, 0, s>>>(d, rows, ow, L, m->grad + m->b_off[l], m->n_par);
+        PHX_CUDA_CHECK(m->ctx, cudaGetLastError());
+        if (l > 0) {
+            // d_in = d W^T : [rows x iw]
+            PHX_CUDA_CHECK(m->ctx, gemm(rows, iw, ow, d, ow, L, 0, m->par + m->w_off[l], ow, m->n_par, 1, dn, iw, L,
+                                        nullptr, 0, 0, nullptr, m->E, 0, s));
+            std::swap(d, dn);
+        }
+    }
+    return PHX_OK;
+}
+
+extern "C" {
+
+phx_status phx_mlp_create(phx_ctx* ctx, int32_t n_in, int32_t width, int32_t depth, int32_t ensemble, uint64_t seed,
+                          phx_mlp** out) {
+    if (!ctx || !out) return PHX_ERR_INVALID;
+    *out = nullptr;
+    if (n_in < 1 || n_in > 64 || width < 1 || width > 1024 || depth < 1 || depth > 16 || ensemble < 1 || ensemble > 64)
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_mlp_create: sizes out of range");
+    cudaSetDevice(ctx->device);
+    phx_mlp* m = new phx_mlp();
+    m->ctx = ctx; m->n_in = n_in; m->width = width; m->depth = depth; m->E = ensemble; m->seed = seed;
+    int64_t off = 0;
+    for (int l = 0; l <= depth; ++l) {
+        const int iw = in_w(m, l), ow = out_w(m, l);
+        m->w_off.push_back(off); m->w_rows.push_back(iw); m->w_cols.push_back(ow);
+        off += (int64_t)iw * ow;
+        m->b_off.push_back(off);
+        off += ow;
+    }
+    m->n_par = off;
+    const size_t pb = sizeof(float) * off * ensemble;
+    bool ok = cudaMalloc(&m->par, pb) == cudaSuccess && cudaMalloc(&m->grad, pb) == cudaSuccess &&
+              cudaMalloc(&m->m1, pb) == cudaSuccess && cudaMalloc(&m->m2, pb) == cudaSuccess &&
+              cudaMalloc(&m->mu, sizeof(float) * 64) == cudaSuccess && cudaMalloc(&m->sd, sizeof(float) * 64) == cudaSuccess &&
+              cudaMalloc(&m->ymu, sizeof(float)) == cudaSuccess && cudaMalloc(&m->ysd, sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->loss, sizeof(double) * ensemble) == cudaSuccess &&
+              cudaMalloc(&m->step, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        delete m;
+        return phx_set_error(ctx, PHX_ERR_NOMEM, "phx_mlp_create: allocation failed");
+    }
+    cudaMemset(m->par, 0, pb);
+    // weights U(-sqrt(6/fan_in)/.., ..) per layer and member (SiLU: He-style scale), biases 0
+    for (int e = 0; e < ensemble; ++e)
+        for (int l = 0; l <= depth; ++l) {
+            const int64_t cnt = m->w_rows[l] * m->w_cols[l];
+            const float a = sqrtf(6.f / (float)m->w_rows[l]);
+            init_kernel<<<(int)((cnt + 255) / 256), 256>>>(m->par + e * off + m->w_off[l], cnt,
+                                                        seed * 1000003ull + (uint64_t)(e * 131 + l), a);
+        }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        delete m;
+        return phx_set_error(ctx, PHX_ERR_CUDA, "phx_mlp_create: init failed");
+    }
+    float one = 1.f, zero = 0.f;
+    for (int f = 0; f < 64; ++f) { cudaMemcpy(m->mu + f, &zero, 4, cudaMemcpyHostToDevice); cudaMemcpy(m->sd + f, &one, 4, cudaMemcpyHostToDevice); }
+    cudaMemcpy(m->ymu, &zero, 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(m->ysd, &one, 4, cudaMemcpyHostToDevice);
+    *out = m;
+    return PHX_OK;
+}
+
+void phx_mlp_destroy(phx_mlp* m) {
+    if (!m) return;
+    cudaFree(m->par); cudaFree(m->grad); cudaFree(m->m1); cudaFree(m->m2);
+    cudaFree(m->mu); cudaFree(m->sd); cudaFree(m->ymu); cudaFree(m->ysd); cudaFree(m->loss); cudaFree(m->step);
+    cudaFree(m->act); cudaFree(m->pre); cudaFree(m->xin); cudaFree(m->ystd); cudaFree(m->dbuf0); cudaFree(m->dbuf1);
+    delete m;
+}
+
+int64_t phx_mlp_num_params(const phx_mlp* m) { return m ? m->n_par : -1; }
+
+phx_status phx_mlp_get_params(phx_mlp* m, float* host_params, float* host_norm) {
+    if (!m || !host_params) return PHX_ERR_INVALID;
+    PHX_CUDA_CHECK(m->ctx, cudaMemcpy(host_params, m->par, sizeof(float) * m->n_par * m->E, cudaMemcpyDeviceToHost));
+    if (host_norm) {
+        PHX_CUDA_CHECK(m->ctx, cudaMemcpy(host_norm, m->mu, sizeof(float) * m->n_in, cudaMemcpyDeviceToHost));
+        PHX_CUDA_CHECK(m->ctx, cudaMemcpy(host_norm + m->n_in, m->sd, sizeof(float) * m->n_in, cudaMemcpyDeviceToHost));
+        PHX_CUDA_CHECK(m->ctx, cudaMemcpy(host_norm + 2 * m->n_in, m->ymu, sizeof(float), cudaMemcpyDeviceToHost));
+        PHX_CUDA_CHECK(m->ctx, cudaMemcpy(host_norm + 2 * m->n_in + 1, m->ysd, sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    return PHX_OK;
+}
+
+phx_status phx_mlp_set_params(phx_mlp* m, const float* host_params, const float* host_norm) {
+    if (!m || !host_params) return PHX_ERR_INVALID;
+    PHX_CUDA_CHECK(m->ctx, cudaMemcpy(m->par, host_params, sizeof(float) * m->n_par * m->E, cudaMemcpyHostToDevice));
+    if (host_norm) {
+        PHX_CUDA_CHECK(m->ctx, cudaMemcpy(m->mu, host_norm, sizeof(float) * m->n_in, cudaMemcpyHostToDevice));
+        PHX_CUDA_CHECK(m->ctx, cudaMemcpy(m->sd, host_norm + m->n_in, sizeof(float) * m->n_in, cudaMemcpyHostToDevice));
+        PHX_CUDA_CHECK(m->ctx, cudaMemcpy(m->ymu, host_norm + 2 * m->n_in, sizeof(float), cudaMemcpyHostToDevice));
+        PHX_CUDA_CHECK(m->ctx, cudaMemcpy(m->ysd, host_norm + 2 * m->n_in + 1, sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return PHX_OK;
+}
+
+// Loss and gradient of every member on one batch (no update): loss[E] host, grad host
+// [E][n_par] (may be NULL).  X [rows][n_in] and y [rows] are device memory (raw features and
+// linewidths; the stored normalisation is applied).
+phx_status phx_mlp_loss_grad(phx_mlp* m, const double* X, const double* y, int32_t rows, double* loss, float* grad,
+                             void* stream) {
+    if (!m || !X || !y || rows <= 0) return PHX_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    PHX_TRY(mlp_reserve(m, rows));
+    input_kernel<<<256, 256, 0, s>>>(X, rows, m->n_in, m->mu, m->sd, m->xin);
+    target_kernel<<<64, 256, 0, s>>>(y, rows, m->ymu, m->ysd, m->ystd);
+    PHX_TRY(mlp_forward(m, rows, s));
+    const int64_t L = (int64_t)rows * m->width;
+    const int64_t layer = (int64_t)m->E * L;
+    const float* yhat = m->act + (int64_t)(m->depth + 1) * layer;
+    // outputs are [E][rows] with member stride L: compact them into dbuf0 as dy
+    PHX_CUDA_CHECK(m->ctx, cudaMemsetAsync(m->loss, 0, sizeof(double) * m->E, s));
+    loss_grad_all_kernel<<<64, 256, 0, s>>>(yhat, m->ystd, rows, m->E, L, m->dbuf0, m->loss);
+    PHX_CUDA_CHECK(m->ctx, cudaGetLastError());
+    PHX_TRY(mlp_backward(m, rows, s));
+    if (loss) PHX_CUDA_CHECK(m->ctx, cudaMemcpyAsync(loss, m->loss, sizeof(double) * m->E, cudaMemcpyDeviceToHost, s));
+    if (grad) PHX_CUDA_CHECK(m->ctx, cudaMemcpyAsync(grad, m->grad, sizeof(float) * m->n_par * m->E, cudaMemcpyDeviceToHost, s));
+    PHX_CUDA_CHECK(m->ctx, cudaStreamSynchronize(s));
+    return PHX_OK;
+}
+
+// Full-batch Adam training of every member on (X, log y): sets the input/target
+// standardisation from the batch, then `epochs` steps.  Final losses to loss[E] (host, may be
+// NULL).
+phx_status phx_mlp_train(phx_mlp* m, const double* X, const double* y, int32_t rows, int32_t epochs, double lr,
+                         double* loss, void* stream) {
+    if (!m || !X || !y || rows <= 0 || epochs < 0 || !(lr > 0.0)) return PHX_ERR_INVALID;
+    phx_ctx* ctx = m->ctx;
+    cudaStream_t user = (cudaStream_t)stream;
+    PHX_TRY(mlp_reserve(m, rows));
+    if (!ctx->cap_stream) {
+        PHX_CUDA_CHECK(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        PHX_CUDA_CHECK(ctx, cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDefault));
+        PHX_CUDA_CHECK(ctx, cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDefault));
+    }
+    cudaStream_t s = ctx->cap_stream;
+    PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_in, user));
+    PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(s, ctx->ev_in, 0));
+    moments_kernel<<<m->n_in, 256, 0, s>>>(X, rows, m->n_in, 1, m->mu, m->sd);
+    moments_kernel<<<1, 256, 0, s>>>(y, rows, 1, 1, m->ymu, m->ysd);
+    input_kernel<<<256, 256, 0, s>>>(X, rows, m->n_in, m->mu, m->sd, m->xin);
+    target_kernel<<<64, 256, 0, s>>>(y, rows, m->ymu, m->ysd, m->ystd);
+    PHX_CUDA_CHECK(ctx, cudaGetLastError());
+    const int64_t np_all = m->n_par * m->E;
+    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(m->m1, 0, sizeof(float) * np_all, s));
+    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(m->m2, 0, sizeof(float) * np_all, s));
+    const int one = 1;
+    PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(m->step, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
+    const int64_t L = (int64_t)rows * m->width;
+    const int64_t layer = (int64_t)m->E * L;
+    const float* yhat = m->act + (int64_t)(m->depth + 1) * layer;
+    // one epoch (forward, loss gradient, backward, Adam, step counter) as a graph
+    cudaGraphExec_t exec = nullptr;
+    if (epochs > 0) {
+        PHX_CUDA_CHECK(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        phx_status st = mlp_forward(m, rows, s);
+        if (st == PHX_OK) {
+            loss_grad_all_kernel<<<64, 256, 0, s>>>(yhat, m->ystd, rows, m->E, L, m->dbuf0, nullptr);
+            if (cudaGetLastError() != cudaSuccess) st = PHX_ERR_CUDA;
+        }
+        if (st == PHX_OK) st = mlp_backward(m, rows, s);
+        if (st == PHX_OK) {
+            adam_kernel<<<(int)std::min<int64_t>((np_all + 255) / 256, 4096), 256, 0, s>>>(
+                m->par, m->grad, m->m1, m->m2, np_all, (float)lr, 0.9f, 0.999f, 1e-8f, m->step);
+            step_kernel<<<1, 1, 0, s>>>(m->step);
+            if (cudaGetLastError() != cudaSuccess) st = PHX_ERR_CUDA;
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(s, &g);
+        if (st != PHX_OK || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return phx_set_error(ctx, st != PHX_OK ? st : PHX_ERR_CUDA, "phx_mlp_train: epoch capture failed");
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return phx_set_error(ctx, PHX_ERR_CUDA, "phx_mlp_train: instantiate failed");
+        for (int ep = 0; ep < epochs; ++ep) {
+            const cudaError_t el = cudaGraphLaunch(exec, s);
+            if (el != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
+                return phx_set_error(ctx, PHX_ERR_CUDA, "phx_mlp_train: %s", cudaGetErrorString(el));
+            }
+        }
+        ctx->launches += (int64_t)epochs * (6 + 4 * (m->depth + 1));
+    }
+    // final loss with the trained parameters
+    PHX_TRY(mlp_forward(m, rows, s));
+    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(m->loss, 0, sizeof(double) * m->E, s));
+    loss_grad_all_kernel<<<64, 256, 0, s>>>(yhat, m->ystd, rows, m->E, L, m->dbuf0, m->loss);
+    PHX_CUDA_CHECK(ctx, cudaGetLastError());
+    if (exec) {
+        PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
+        cudaGraphExecDestroy(exec);
+    }
+    PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_out, s));
+    PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(user, ctx->ev_out, 0));
+    if (loss) {
+        PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(loss, m->loss, sizeof(double) * m->E, cudaMemcpyDeviceToHost, s));
+        PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
+    }
+    return PHX_OK;
+}
+
+// Ensemble prediction of log(gamma): mean[rows] and std[rows] (device, std may be NULL).
+phx_status phx_mlp_predict(phx_mlp* m, const double* X, int32_t rows, double* mean, double* stdv, void* stream) {
+    if (!m || !X || !mean || rows <= 0) return PHX_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    PHX_TRY(mlp_reserve(m, rows));
+    input_kernel<<<256, 256, 0, s>>>(X, rows, m->n_in, m->mu, m->sd, m->xin);
+    PHX_TRY(mlp_forward(m, rows, s));
+    const int64_t L = (int64_t)rows * m->width;
+    const int64_t layer = (int64_t)m->E * L;
+    const float* yhat = m->act + (int64_t)(m->depth + 1) * layer;
+    // member outputs are L apart: gather through a strided view (compact into dbuf0 first)
+    for (int e = 0; e < m->E; ++e)
+        PHX_CUDA_CHECK(m->ctx, cudaMemcpyAsync(m->dbuf0 + (int64_t)e * rows, yhat + e * L, sizeof(float) * rows,
+                                               cudaMemcpyDeviceToDevice, s));
+    ensemble_kernel<<<(rows + 255) / 256, 256, 0, s>>>(m->dbuf0, rows, m->E, m->ymu, m->ysd, mean, stdv);
+    PHX_CUDA_CHECK(m->ctx, cudaGetLastError());
+    m->ctx->launches += 2 + (m->depth + 1);
+    return PHX_OK;
+}
+
+// Descriptors of every band of the irreducible q-points on a mesh (see the file header):
+// out[n_irr][n][4] = (w rad/ps, |v| A/ps, WP2 ps^4, n_B).  freq, vel over the full mesh.
+phx_status phx_features(phx_ctx* ctx, const int32_t mesh[3], int32_t n, const double* freq_thz, const double* vel,
+                        const int32_t* irr_q, int32_t n_irr, double temperature, phx_broadening br, double f_min_thz,
+                        double* features, void* stream) {
+    if (!ctx || !mesh || !freq_thz || !vel || !irr_q || !features || n <= 0 || n_irr <= 0)
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_features: bad argument");
+    if (!(temperature > 0.0) || !(br.sigma_thz > 0.0) || !(br.window > 0.0) || !(f_min_thz > 0.0))
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_features: T, sigma, window and f_min must be > 0");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nq = mesh[0] * mesh[1] * mesh[2];
+    double* nB = (double*)phx_ws(ctx, "s.nB", (size_t)nq * n * 8);
+    double* wsum = (double*)phx_ws(ctx, "s.wsum", (size_t)n_irr * n * 8);
+    if (!nB || !wsum) return PHX_ERR_NOMEM;
+    PHX_CUDA_CHECK(ctx, phx_launch_occupations(freq_thz, nq * n, temperature, 0, nB, nullptr, s));
+    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(wsum, 0, (size_t)n_irr * n * 8, s));
+    if (n > 192) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "phx_features: n = %d > 192", n);
+    if (n_irr > 65535) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "phx_features: n_irr > 65535");
+    features_kernel<<<dim3((nq + 255) / 256, n_irr), 256, 0, s>>>(freq_thz, nB, irr_q, n, mesh[0], mesh[1], mesh[2],
+                                                                  (float)br.sigma_thz, (float)br.window, br.shape,
+                                                                  (float)f_min_thz, wsum);
+    PHX_CUDA_CHECK(ctx, cudaGetLastError());
+    features_finish_kernel<<<(n_irr * n + 255) / 256, 256, 0, s>>>(freq_thz, vel, nB, irr_q, n_irr, n, nq, f_min_thz,
+                                                                  wsum, features);
+    PHX_CUDA_CHECK(ctx, cudaGetLastError());
+    ctx->launches += 3;
+    return PHX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+"""The learned-linewidth part: descriptor kernel against the oracle's weighted phase space,
+training-kernel gradients against the FP64 reference network, and the end-to-end gain of the
+trained ensemble over the same subgrid used without it."""
+import numpy as np
+import pytest
+
+import oracle as O
+import phx_inputs as P
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+
+@pytest.fixture(scope="module")
+def phx():
+    import paper_2602_23728_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(phx):
+    c = phx.Context(0)
+    yield c
+    c.close()
+
+
+def test_features_match_oracle_wp2(ctx, phx):
+    import torch
+    w = P.fcc_conventional_4(mesh=(4, 4, 4))
+    c = w.crystal
+    f2, f3 = w.ifc2(), w.ifc3()
+    q = O.grid.mesh_qred(w.mesh)
+    freq, evec, vel, _ = ctx.harmonic(c.lattice, c.masses, f2.idx, f2.val.reshape(-1, 9), q, want_vv=False)
+    irr, _, _ = phx.irreducible(w.mesh, w.rotations)
+    dev = torch.device("cuda:0")
+    F = ctx.features(w.mesh, torch.from_numpy(freq).to(dev), torch.from_numpy(vel).to(dev),
+                     torch.from_numpy(irr.astype(np.int32)).to(dev), w.temperature).cpu().numpy()
+    fc3 = O.anharmonic.FC3(f3.idx, f3.val, c.masses)
+    _, wp2 = O.anharmonic.gamma(fc3, w.mesh, freq, evec, irr, w.temperature, want_wp2=True)
+    nB = O.occupation.bose(freq[irr], w.temperature)
+    ok = freq[irr] >= 0.01
+    assert np.allclose(F[..., 0][ok], 2 * np.pi * freq[irr][ok], rtol=1e-12)
+    assert np.allclose(F[..., 1], np.linalg.norm(vel[irr], axis=-1), rtol=1e-12)
+    big = wp2 > 1e-3 * wp2.max()
+    assert (np.abs(F[..., 2] - wp2)[big] / wp2[big]).max() < 1e-5
+    assert np.allclose(F[..., 3][ok], nB[ok], rtol=1e-12)
+
+
+def test_mlp_gradients_match_fp64_reference(ctx):
+    import torch
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(9)
+    m = ctx.mlp(4, 32, 3, 2, seed=5)
+    X = np.exp(rng.normal(size=(300, 4)))
+    y = np.exp(rng.normal(size=300))
+    Xd, yd = torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev)
+    p, _ = m.get_params()
+    norm = np.concatenate([rng.normal(size=4), rng.uniform(0.5, 2, 4), [0.2, 1.3]]).astype(np.float32)
+    m.set_params(p, norm)
+    loss, g = m.loss_grad(Xd, yd)
+    for e in range(2):
+        lo, go = O.surrogate.loss_and_grad(p[e].astype(np.float64), norm.astype(np.float64), X, y, 4, 32, 3)
+        assert abs(loss[e] - lo) <= 1e-5 * lo
+        assert np.abs(g[e] - go).max() <= 1e-4 * np.abs(go).max()
+    # predictions: ensemble mean of the reference outputs
+    mean, std = m.predict(Xd)
+    ref = np.mean([O.surrogate.predict(p[e].astype(np.float64), norm.astype(np.float64), X, 4, 32, 3)
+                   for e in range(2)], axis=0)
+    assert np.abs(mean.cpu().numpy() - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+    # training lowers the loss
+    l0 = m.loss_grad(Xd, yd)[0]
+    lt = m.train(Xd, yd, 300, 3e-3)
+    assert np.all(lt < l0)
+    m.close()
+
+
+def test_surrogate_gain_over_coarse_mesh(ctx, phx):
+    """The trained ensemble on the dense 12^3 mesh (exact linewidths only on the 6^3 subgrid plus
+    a 5 % fallback) against the same exact kernel used without the network, on the 6^3 mesh."""
+    from paper_2602_23728_gb300 import surrogate
+    w = P.fcc_conventional_4(mesh=(12, 12, 12), temperature=40.0)
+    c = w.crystal
+    f2, f3 = w.ifc2(), w.ifc3()
+    r = surrogate.run(ctx, phx, c.lattice, c.masses, f2.idx, f2.val, f3.idx, f3.val, w.mesh, 2, w.rotations,
+                      w.temperature, epochs=3000, seed=1)
+    print({k: v for k, v in r.items() if not k.startswith("kappa_") or "err" in k})
+    assert r["kappa_rel_err_surrogate"] < r["kappa_rel_err_coarse"]
+    assert r["kappa_rel_err_surrogate"] < 0.05
+    assert r["heldout_median_rel_err"] < 0.25

@@ -420,3 +420,27 @@ def test_gamma_matches_self_energy_form(fcc1):
         ref = np.pi * 6.582119569e-4 * 9648.533212 ** 3 / (8 * 125) * acc
         got = O.anharmonic.gamma(fc3, w.mesh, freq, evec, [iq], w.temperature, "gauss", sig)[0]
         assert np.allclose(got, ref, rtol=1e-6)
+
+
+# ----------------------------------------------------------------------------- surrogate reference
+
+def test_surrogate_reference_gradient_matches_finite_differences():
+    """The FP64 reference network's backpropagated gradient against central differences."""
+    rng = np.random.default_rng(4)
+    n_in, width, depth = 4, 8, 3
+    shapes = O.surrogate.layer_shapes(n_in, width, depth)
+    n_par = sum(i * o + o for i, o in shapes)
+    p = rng.normal(scale=0.4, size=n_par)
+    norm = np.concatenate([rng.normal(size=n_in), rng.uniform(0.5, 2, n_in), [0.3, 1.7]])
+    X = np.exp(rng.normal(size=(13, n_in)))
+    y = np.exp(rng.normal(size=13))
+    loss, g = O.surrogate.loss_and_grad(p, norm, X, y, n_in, width, depth)
+    h = 1e-6
+    for k in rng.choice(n_par, 25, replace=False):
+        e = np.zeros(n_par); e[k] = h
+        lp, _ = O.surrogate.loss_and_grad(p + e, norm, X, y, n_in, width, depth)
+        lm, _ = O.surrogate.loss_and_grad(p - e, norm, X, y, n_in, width, depth)
+        assert abs((lp - lm) / (2 * h) - g[k]) <= 1e-7 * max(1.0, abs(g[k]))
+    # prediction is the de-standardised network output
+    pr = O.surrogate.predict(p, norm, X, n_in, width, depth)
+    assert pr.shape == (13,) and np.all(np.isfinite(pr))

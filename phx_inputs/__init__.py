@@ -388,3 +388,124 @@ def batched_sweep(n_jobs: int = 64, seed: int = 3) -> List[Workload]:
         jobs.append(Workload(f"job{k:02d}-na{na}-mesh{m}", c, LennardJones(), (m, m, m), T,
                              0.1, "gauss", identity_rotation()))
     return jobs
+
+
+# ----------------------------------------------------------------------------- large Gamma-only cell
+
+
+def _pairs_within(positions: np.ndarray, lattice: np.ndarray, rc: float):
+    """All ordered pairs (i, j, image shift) with 0 < |x_j + R - x_i| < rc (vectorised)."""
+    inv = np.linalg.inv(lattice)
+    frac = positions @ inv
+    span = frac.max(axis=0) - frac.min(axis=0)
+    # |frac(x_j + R - x_i)| <= rc |column of inv| bounds R_i within span_i of it
+    lim = np.ceil(rc * np.linalg.norm(inv, axis=0) + span).astype(int)
+    grid = np.array(list(itertools.product(*[range(-l, l + 1) for l in lim])), dtype=np.int64)
+    shifts = grid @ lattice
+    I, J, Rk, D = [], [], [], []
+    for k, sh in enumerate(shifts):
+        d = positions[None, :, :] + sh[None, None, :] - positions[:, None, :]      # (i, j, 3)
+        dist2 = (d * d).sum(axis=2)
+        ii, jj = np.nonzero((dist2 < rc * rc) & (dist2 > 1e-16))
+        I.append(ii); J.append(jj); Rk.append(np.full(ii.shape, k)); D.append(d[ii, jj])
+    I = np.concatenate(I); J = np.concatenate(J); Rk = np.concatenate(Rk); D = np.concatenate(D)
+    return I, J, grid[Rk], D
+
+
+def relax_lj(crystal: Crystal, pot: LennardJones, fmax: float = 1e-8, max_steps: int = 20000) -> Crystal:
+    """FIRE relaxation of the positions at fixed cell to max |F| < fmax (eV/A)."""
+    x = crystal.positions.copy()
+    lat = crystal.lattice
+    m = crystal.masses[:, None]
+    skin = 1.0
+    I, J, R, _ = _pairs_within(x, lat, pot.rc + skin)
+    x_ref = x.copy()
+
+    def forces(x):
+        nonlocal I, J, R, x_ref
+        if np.abs(x - x_ref).max() > 0.4 * skin:
+            I, J, R, _ = _pairs_within(x, lat, pot.rc + skin)
+            x_ref = x.copy()
+        d = x[J] + R @ lat - x[I]
+        r = np.linalg.norm(d, axis=1)
+        ok = r < pot.rc
+        _, f1, _, _ = pot.derivs(np.where(ok, r, 1.0))
+        fij = np.where(ok, f1 / r, 0.0)[:, None] * d           # force on i from pair (i, j)
+        return np.stack([np.bincount(I, weights=fij[:, k], minlength=x.shape[0]) for k in range(3)], axis=1)
+
+    v = np.zeros_like(x)
+    dt, dt_max, alpha, n_pos = 0.5, 2.0, 0.1, 0       # time unit sqrt(amu A^2 / eV)
+    F = forces(x)
+    for _ in range(max_steps):
+        if np.abs(F).max() < fmax:
+            break
+        P = (F * v).sum()
+        if P > 0:
+            vn, fn = np.linalg.norm(v), np.linalg.norm(F)
+            v = (1 - alpha) * v + alpha * F / max(fn, 1e-300) * vn
+            n_pos += 1
+            if n_pos > 5:
+                dt = min(dt * 1.1, dt_max)
+                alpha *= 0.99
+        else:
+            v[:] = 0.0
+            dt *= 0.5
+            alpha = 0.1
+            n_pos = 0
+        v = v + dt * F / m
+        x = x + dt * v
+        F = forces(x)
+    return Crystal(lat.copy(), x, crystal.masses.copy(), crystal.name + "-relaxed")
+
+
+def ifc_lj_vectorised(crystal: Crystal, pot: LennardJones, drop_rel: float = 1e-15):
+    """IFC2 blocks and IFC3 COO of a (large) cell, vectorised; the same construction as
+    ifc2_lj / ifc3_lj (duplicate entries summed)."""
+    ii, jj, RR, rv = _pairs_within(crystal.positions, crystal.lattice, pot.rc)
+    H, T = _pair_tensors(pot, rv)
+    na = crystal.n_atoms
+    # ---- IFC2: (i, j, R) -> -H ; (i, i, 0) -> sum H
+    keys2 = np.concatenate([np.stack([ii, jj, RR[:, 0], RR[:, 1], RR[:, 2]], 1),
+                            np.stack([ii, ii, 0 * ii, 0 * ii, 0 * ii], 1)])
+    vals2 = np.concatenate([-H, H])
+    u2, inv2 = np.unique(keys2, axis=0, return_inverse=True)
+    acc2 = np.zeros((u2.shape[0], 3, 3))
+    np.add.at(acc2, inv2.ravel(), vals2)
+    ifc2 = IFC2(u2.astype(np.int32), acc2)
+    # ---- IFC3 blocks: (i,i,j)+T, (i,j,i)+T, (i,j,j)-T, (i,i,i)-T ; key (a, b, Rb, c, Rc)
+    z = np.zeros_like(RR)
+    blocks_k = np.concatenate([
+        np.concatenate([ii[:, None], ii[:, None], z, jj[:, None], RR], 1),
+        np.concatenate([ii[:, None], jj[:, None], RR, ii[:, None], z], 1),
+        np.concatenate([ii[:, None], jj[:, None], RR, jj[:, None], RR], 1),
+        np.concatenate([ii[:, None], ii[:, None], z, ii[:, None], z], 1)])
+    blocks_v = np.concatenate([T, T, -T, -T])
+    u3, inv3 = np.unique(blocks_k, axis=0, return_inverse=True)
+    acc3 = np.zeros((u3.shape[0], 3, 3, 3))
+    np.add.at(acc3, inv3.ravel(), blocks_v)
+    vmax = np.abs(acc3).max()
+    a = u3[:, 0]; b = u3[:, 1]; Rb = u3[:, 2:5]; c = u3[:, 5]; Rc = u3[:, 6:9]
+    al, be, ga = np.meshgrid(np.arange(3), np.arange(3), np.arange(3), indexing="ij")
+    al, be, ga = al.ravel(), be.ravel(), ga.ravel()
+    vals = acc3.reshape(-1, 27)
+    keep = np.abs(vals) > drop_rel * vmax
+    blk, comp = np.nonzero(keep)
+    idx = np.stack([3 * a[blk] + al[comp], 3 * b[blk] + be[comp], 3 * c[blk] + ga[comp],
+                    Rb[blk, 0], Rb[blk, 1], Rb[blk, 2], Rc[blk, 0], Rc[blk, 1], Rc[blk, 2]], 1)
+    ifc3 = IFC3(idx.astype(np.int32), vals[blk, comp].astype(np.float64))
+    return ifc2, ifc3
+
+
+def gamma_disordered_1000(reps=(10, 10, 10), noise=0.05, seed=5, relax=True):
+    """Gamma-only disordered cell: reps x primitive fcc (1000 atoms for 10^3), Gaussian
+    positional noise (seeded) relaxed back to the LJ force minimum, 50/50 masses 39.95/83.8;
+    Lorentzian smearing (half width 0.05 THz, i.e. sigma = 0.1 THz in the broadening formula)."""
+    rng = np.random.default_rng(seed)
+    c = fcc_primitive_multiple(5.26, reps)
+    c = random_masses(c, 39.95, 83.8, seed=seed)
+    c.positions = c.positions + rng.normal(scale=noise, size=c.positions.shape)
+    pot = LennardJones()
+    if relax:
+        c = relax_lj(c, pot)
+    return Workload(f"gamma-disordered-{c.n_atoms}", c, pot, (1, 1, 1), 300.0, 0.1, "lorentz",
+                    identity_rotation())

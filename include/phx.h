@@ -123,8 +123,15 @@ phx_status phx_irreducible(const int32_t mesh[3], int32_t n_rot, const int32_t* 
  *   vv[nq][n][9]        basis-invariant v(x)v: within each degenerate set S
  *                       (|df| < 1e-5 max|f|) every mode gets
  *                       (1/|S|) sum_{m,m' in S} Re(V^a_{mm'} V^b_{m'm})/(4 w^2)         [mem, may be NULL]
- * n = 3 * cell->n_atoms, 3 <= n <= 192.
- * Errors: PHX_ERR_INVALID (block index out of range), PHX_ERR_NUMERIC (no convergence). */
+ * n = 3 * cell->n_atoms, 3 <= n <= 192 for any q.
+ * Larger cells (192 < n <= 16384; Eq. (eigenvalue), the real-space problem of a Gamma-only or
+ * disordered cell): every q must be a lattice vector (Gamma), vel and vv must be NULL, and D is
+ * real symmetric; it is solved in FP64 by Householder reduction to tridiagonal form, Sturm
+ * bisection, inverse iteration (eigenvalues closer than 1e-7 ||D|| orthogonalised as a
+ * cluster) and back-transformation.  evec then holds real columns (imaginary parts 0), largest
+ * component positive.  Device workspace ~49 n^2 bytes (441 MB at n = 3000).
+ * Errors: PHX_ERR_INVALID (block index out of range), PHX_ERR_UNSUPPORTED (q != Gamma or
+ * velocities requested for n > 192), PHX_ERR_NUMERIC (no convergence / non-finite result). */
 phx_status phx_harmonic(phx_ctx* ctx, const phx_cell* cell, const phx_ifc2* fc2,
                         const double* q_frac, int32_t nq,
                         double* freq_thz, double* evec, double* vel, double* vv,
@@ -157,6 +164,40 @@ phx_status phx_gamma(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz,
                      const double* evec, const int32_t* irr_q, int32_t n_irr,
                      double temperature, phx_broadening br, double f_min_thz,
                      int32_t prec, double* gamma, double* wp2, int32_t mem, void* stream);
+
+/* Several temperatures from one contraction (paper Sec. "Performance Optimization": the
+ * temperature-independent |Phi|^2 and deltas are shared, only the occupations change).
+ * temperatures[n_t] (host, K); gamma[n_t][n_irr][n] (1/ps) [mem]; other arguments as phx_gamma
+ * (no wp2).  Tensor-core precisions evaluate up to 4 temperatures per contraction pass (more
+ * are taken in groups of 4); PHX_FP64 and the Gamma-only large cell run one full evaluation
+ * per temperature.  Each gamma[t] equals phx_gamma at temperatures[t] (up to FP32 summation
+ * order on the tensor-core path).  Errors: as phx_gamma; PHX_ERR_INVALID for T <= 0. */
+phx_status phx_gamma_multi_t(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz,
+                             const double* evec, const int32_t* irr_q, int32_t n_irr,
+                             const double* temperatures, int32_t n_t, phx_broadening br,
+                             double f_min_thz, int32_t prec, double* gamma, int32_t mem, void* stream);
+
+/* ---------------------------------------------------------------- Gamma-only large cell
+ * Eq. (phi3_proj) at q = q' = q'' = 0 and Eq. (gamma) with N_q = 1 for every mode of a
+ * (disordered) cell of up to 16384/3 atoms: the real-space treatment of Gamma-only and
+ * amorphous systems.  fc3 must come from phx_fc3_create with mesh {1, 1, 1}; on creation its
+ * COO is summed over images and symmetrised over the permutations of (i, j, k) (a third
+ * derivative is symmetric; input that already is stays unchanged).
+ *   freq_thz[n] ascending or not, evec[n][n] complex with zero imaginary parts (columns are
+ *   modes; as phx_harmonic returns at Gamma) [mem]; gamma[n] (1/ps) [mem].
+ * The result equals the per-mode sum of phx_gamma (window, f_min and occupations alike).
+ * Each unordered triple of modes is evaluated once: sparse F.e_a and W_a E on the CUDA cores,
+ * E^T (W_a E) on the tensor cores (PHX_TF32, PHX_BF16X3) or FP64 CUDA cores (PHX_FP64), only
+ * over 128 x 128 tiles of (b, c) that can hold a triple inside the broadening window, with the
+ * three linewidth updates fused into the GEMM epilogue.  The call synchronises the stream once
+ * (the frequencies plan the tiles on the host); workspace grows to ~6 GB.
+ * phx_gamma with a 1x1x1-mesh handle, n > 192, n_irr = 1 and irr_q = {0} calls this.
+ * Errors: PHX_ERR_INVALID (handle not 1x1x1, complex eigenvectors, bad T/sigma/f_min),
+ * PHX_ERR_UNSUPPORTED (neighbour count beyond shared memory), PHX_ERR_TIMEOUT (a tensor-core
+ * pipeline wait gave up; the result is then invalid). */
+phx_status phx_gamma_cell(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz, const double* evec,
+                          double temperature, phx_broadening br, double f_min_thz, int32_t prec,
+                          double* gamma, int32_t mem, void* stream);
 
 /* ---------------------------------------------------------------- batched scattering
  * Many crystals (of any size up to 192 modes and any mesh) in one call: every job's
@@ -286,8 +327,11 @@ typedef enum {
     PHX_K_FOLD = 3,         /* Phi3 fold into the lattice-difference operand (S3)          */
     PHX_K_FP64_GEMM = 4,    /* FP64 complex GEMMs of the FP64 path                          */
     PHX_K_FP64_EPI = 5,     /* FP64 weight/reduction kernel                                 */
-    PHX_K_EIGEN = 6,        /* batched Jacobi eigensolver                                   */
-    PHX_K_COUNT = 7
+    PHX_K_EIGEN = 6,        /* eigensolvers (batched Jacobi; large-cell tridiagonal path)   */
+    PHX_K_CELL_SPARSE = 7,  /* Gamma-only cell: W_a = F e_a and X_a = W_a E (CUDA cores)      */
+    PHX_K_CELL_TRANSPOSE = 8, /* Gamma-only cell: operand layout transposes                   */
+    PHX_K_CELL_GEMM = 9,    /* Gamma-only cell: E^T X_a tiles + fused role-weight epilogue   */
+    PHX_K_COUNT = 10
 } phx_kernel_class;
 
 /* Turn profiling on (1) or off (0); turning it on clears the counters.  Off by default. */

@@ -79,6 +79,10 @@ lib.phx_fc3_num_d.argtypes = [_P]
 lib.phx_fc3_num_d.restype = C.c_int32
 lib.phx_gamma.argtypes = [_P, _P, _P, _P, _P, _I, C.c_double, Broadening, C.c_double, _I, _P, _P, _I, _P]
 lib.phx_gamma.restype = C.c_int
+lib.phx_gamma_multi_t.argtypes = [_P, _P, _P, _P, _P, _I, _P, _I, Broadening, C.c_double, _I, _P, _I, _P]
+lib.phx_gamma_multi_t.restype = C.c_int
+lib.phx_gamma_cell.argtypes = [_P, _P, _P, _P, C.c_double, Broadening, C.c_double, _I, _P, _I, _P]
+lib.phx_gamma_cell.restype = C.c_int
 lib.phx_unfold.argtypes = [_P, _I, _I, _I, _P, _P, _P, _P, _P, _I, _P]
 lib.phx_unfold.restype = C.c_int
 lib.phx_kappa_rta.argtypes = [_P, C.POINTER(Cell), _I, _I, _P, _P, _P, _P, C.c_double, C.c_double, _I, _P, _I, _P]
@@ -115,10 +119,10 @@ lib.phx_mlp_predict.argtypes = [_P, _P, _I, _P, _P, _P]
 lib.phx_mlp_predict.restype = C.c_int
 
 KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4, "fp64_epilogue": 5,
-           "eigensolver": 6}
+           "eigensolver": 6, "cell_sparse": 7, "cell_transpose": 8, "cell_gemm": 9}
 
 EXPORTED = ["phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
-            "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_unfold", "phx_kappa_rta",
+            "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta",
             "phx_kappa_rta_noalloc", "phx_gamma_batched", "phx_features", "phx_mlp_create", "phx_mlp_destroy",
             "phx_mlp_num_params", "phx_mlp_get_params", "phx_mlp_set_params", "phx_mlp_loss_grad", "phx_mlp_train",
             "phx_mlp_predict"]
@@ -308,6 +312,36 @@ class Context:
                                   float(temperature), br, float(f_min), PRECISIONS[precision], _ptr(gamma),
                                   _ptr(wp2), mem, stream))
         return (gamma, wp2) if want_wp2 or wp2 is not None else gamma
+
+    def gamma_multi_t(self, fc3, freq, evec, irr_q, temperatures, shape="gauss", sigma=0.1, window=2.0, f_min=0.01,
+                      precision="bf16x3", gamma=None):
+        """phx_gamma_multi_t: gamma[n_t][n_irr][n] for several temperatures from one contraction."""
+        br = Broadening(SHAPES[shape], float(sigma), float(window))
+        temps = _host(temperatures, np.float64).reshape(-1)
+        if not _is_torch(freq):
+            freq = _host(freq, np.float64)
+            evec = _host(evec, np.complex128)
+            irr_q = _host(irr_q, np.int32)
+            gamma = np.zeros((temps.shape[0], irr_q.shape[0], fc3.n)) if gamma is None else gamma
+        mem, stream = _mem_and_stream([freq, evec, irr_q, gamma])
+        self._check(lib.phx_gamma_multi_t(self.h, fc3.h, _ptr(freq), _ptr(evec), _ptr(irr_q), int(irr_q.shape[0]),
+                                          temps.ctypes.data, int(temps.shape[0]), br, float(f_min),
+                                          PRECISIONS[precision], _ptr(gamma), mem, stream))
+        return gamma
+
+    def gamma_cell(self, fc3, freq, evec, temperature, shape="lorentz", sigma=0.1, window=2.0, f_min=0.01,
+                   precision="bf16x3", gamma=None):
+        """phx_gamma_cell: Gamma-only linewidths of every mode of a large cell (fc3 made for a
+        1x1x1 mesh; freq [n], evec [n, n] complex with zero imaginary parts)."""
+        br = Broadening(SHAPES[shape], float(sigma), float(window))
+        if not _is_torch(freq):
+            freq = _host(freq, np.float64).reshape(-1)
+            evec = _host(evec, np.complex128)
+            gamma = np.zeros(fc3.n) if gamma is None else gamma
+        mem, stream = _mem_and_stream([freq, evec, gamma])
+        self._check(lib.phx_gamma_cell(self.h, fc3.h, _ptr(freq), _ptr(evec), float(temperature), br, float(f_min),
+                                       PRECISIONS[precision], _ptr(gamma), mem, stream))
+        return gamma
 
     def gamma_batched(self, jobs, precision="bf16x3", q_tiles=None):
         """phx_gamma_batched.  jobs: list of dicts with keys fc3 (FC3), freq, evec (CUDA tensors),

@@ -17,6 +17,10 @@ phx_status phx_gamma_fp64(phx_ctx* ctx, const phx_fc3* f, const double* freq, co
 phx_status phx_gamma_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec,
                         const double* nB, const int32_t* irr_host, int n_irr, const GammaParams& gp,
                         int prec, double* gacc, double* wacc, cudaStream_t s);
+phx_status phx_gamma_tc_multi_t(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec,
+                                const double* nB, int n_t, const int32_t* irr_host, int n_irr, const GammaParams& gp,
+                                int prec, double* gacc, cudaStream_t s);
+constexpr int kTPerPass = 4;     // temperatures per tensor-core pass (the epilogue's occupation tables)
 
 phx_status phx_set_error(phx_ctx* ctx, phx_status st, const char* fmt, ...) {
     if (ctx) {
@@ -299,10 +303,29 @@ phx_status phx_harmonic(phx_ctx* ctx, const phx_cell* cell, const phx_ifc2* fc2,
     if (mem != PHX_MEM_HOST && mem != PHX_MEM_DEVICE)
         return phx_set_error(ctx, PHX_ERR_INVALID, "phx_harmonic: bad mem flag %d", mem);
     const int na = cell->n_atoms, n = 3 * na;
-    if (na <= 0 || n > 192)
-        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "phx_harmonic: n_atoms=%d (need 1..64)", na);
+    if (na <= 0 || n > kPhxMaxLargeModes)
+        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "phx_harmonic: n_atoms=%d (need 1..%d)", na,
+                             kPhxMaxLargeModes / 3);
     if (nq < 0) return phx_set_error(ctx, PHX_ERR_INVALID, "phx_harmonic: nq < 0");
     if (nq == 0) return PHX_OK;
+    // cells above 64 atoms: the large real-symmetric solver, Gamma point only, no velocities
+    const bool large = n > 192;
+    if (large) {
+        if (vel || vv)
+            return phx_set_error(ctx, PHX_ERR_UNSUPPORTED,
+                                 "phx_harmonic: velocities need n_atoms <= 64 (larger cells are solved at Gamma)");
+        std::vector<double> hq((size_t)nq * 3);
+        if (mem == PHX_MEM_DEVICE) {
+            cudaSetDevice(ctx->device);
+            PHX_CUDA_CHECK(ctx, cudaMemcpy(hq.data(), q_frac, hq.size() * 8, cudaMemcpyDeviceToHost));
+        } else {
+            std::memcpy(hq.data(), q_frac, hq.size() * 8);
+        }
+        for (double v : hq)
+            if (!(std::fabs(v - std::nearbyint(v)) < 1e-12))
+                return phx_set_error(ctx, PHX_ERR_UNSUPPORTED,
+                                     "phx_harmonic: cells above 64 atoms are solved at Gamma only (q = %g)", v);
+    }
     for (int i = 0; i < na; ++i)
         if (!(cell->masses[i] > 0.0)) return phx_set_error(ctx, PHX_ERR_INVALID, "mass %d not positive", i);
     const int nb = fc2->n_blocks;
@@ -354,16 +377,21 @@ phx_status phx_harmonic(phx_ctx* ctx, const phx_cell* cell, const phx_ifc2* fc2,
     if (vv) PHX_TRY(phx_stage_out_buf(ctx, "h.ovv", vv, (size_t)nq * n * 9, mem, &o_vv));
     const bool want_v = vel || vv;
 
+    if (large) {
+        PHX_CUDA_CHECK(ctx, cudaMemsetAsync(ctx->status_word, 0, 4, s));
+        for (int q = 0; q < nq; ++q)
+            PHX_TRY(phx_eigh_gamma_large(ctx, na, d_val, d_ps, d_m, o_f + (int64_t)q * n, o_e + (int64_t)q * n2 * 2, s));
+    }
     // q chunks bounded to ~1 GB of work buffers
     const int64_t per_q = n2 * 16 * (want_v ? 8 : 2);
-    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)nq, ((int64_t)1 << 30) / per_q, (int64_t)16384}));
-    double* D = (double*)phx_ws(ctx, "h.D", (size_t)chunk * n2 * 16);
-    double* Vw = (double*)phx_ws(ctx, "h.V", (size_t)chunk * n2 * 16);
+    const int chunk = large ? 0 : (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)nq, ((int64_t)1 << 30) / per_q, (int64_t)16384}));
+    double* D = large ? nullptr : (double*)phx_ws(ctx, "h.D", (size_t)chunk * n2 * 16);
+    double* Vw = large ? nullptr : (double*)phx_ws(ctx, "h.V", (size_t)chunk * n2 * 16);
     double* dD = want_v ? (double*)phx_ws(ctx, "h.dD", (size_t)chunk * 3 * n2 * 16) : nullptr;
     double* Y = want_v ? (double*)phx_ws(ctx, "h.Y", (size_t)chunk * 3 * n2 * 16) : nullptr;
-    if (!D || !Vw || (want_v && (!dD || !Y))) return PHX_ERR_NOMEM;
-    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(ctx->status_word, 0, 4, s));
-    for (int q0 = 0; q0 < nq; q0 += chunk) {
+    if (!large && (!D || !Vw || (want_v && (!dD || !Y)))) return PHX_ERR_NOMEM;
+    if (!large) PHX_CUDA_CHECK(ctx, cudaMemsetAsync(ctx->status_word, 0, 4, s));
+    for (int q0 = 0; !large && q0 < nq; q0 += chunk) {
         const int c = std::min(chunk, nq - q0);
         PHX_CUDA_CHECK(ctx, phx_launch_dynmat(dq + 3 * q0, c, na, d_idx, d_val, d_ps, d_m, d_lat, D, dD, s));
         const int ps = phx_prof_begin(ctx, s);
@@ -487,6 +515,13 @@ phx_status phx_fc3_create(phx_ctx* ctx, const phx_cell* cell, const phx_ifc3* fc
         phx_fc3_destroy(h);
         return phx_set_error(ctx, PHX_ERR_NOMEM, "phx_fc3_create: device upload failed");
     }
+    if (m1 == 1 && m2 == 1 && m3 == 1) {
+        const phx_status st = phx_fc3_prepare_cell(ctx, cell, fc3, h);
+        if (st != PHX_OK) {
+            phx_fc3_destroy(h);
+            return st;
+        }
+    }
     *out = h;
     return PHX_OK;
 }
@@ -496,6 +531,8 @@ void phx_fc3_destroy(phx_fc3* h) {
     cudaFree(h->d_int); cudaFree(h->seg_key); cudaFree(h->seg_start);
     cudaFree(h->ent_a); cudaFree(h->ent_r2); cudaFree(h->ent_w);
     cudaFree(h->tc_seg_of); cudaFree(h->tc_ident);
+    cudaFree(h->g0_nbr_start); cudaFree(h->g0_nbr_atom); cudaFree(h->g0_seg_start);
+    cudaFree(h->g0_ent_i); cudaFree(h->g0_ent_w);
     delete h;
 }
 
@@ -520,6 +557,21 @@ phx_status phx_gamma(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz, c
         return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma: unknown precision %d", prec);
     if (mem != PHX_MEM_HOST && mem != PHX_MEM_DEVICE)
         return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma: bad mem flag %d", mem);
+    if (fc3->nq == 1 && fc3->n > 192) {
+        // cells above 64 atoms at Gamma: the large-cell path (one irreducible point, no WP2)
+        if (n_irr != 1 || wp2)
+            return phx_set_error(ctx, PHX_ERR_UNSUPPORTED,
+                                 "phx_gamma: a Gamma-only cell above 64 atoms takes n_irr = 1 and no wp2");
+        int32_t q0 = 0;
+        if (mem == PHX_MEM_HOST) {
+            q0 = irr_q[0];
+        } else {
+            cudaSetDevice(ctx->device);
+            PHX_CUDA_CHECK(ctx, cudaMemcpy(&q0, irr_q, 4, cudaMemcpyDeviceToHost));
+        }
+        if (q0 != 0) return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma: irr_q[0]=%d outside the mesh", q0);
+        return phx_gamma_cell(ctx, fc3, freq_thz, evec, temperature, br, f_min_thz, prec, gamma, mem, stream);
+    }
     cudaSetDevice(ctx->device);
     cudaStream_t s = as_stream(stream);
     const int n = fc3->n, nq = fc3->nq;
@@ -583,6 +635,96 @@ phx_status phx_gamma(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz, c
         PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(&st, ctx->status_word, 4, cudaMemcpyDeviceToHost, s));
         PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
         if (st != 0) return phx_set_error(ctx, (phx_status)st, "phx_gamma: a device wait gave up (status %d)", st);
+    }
+    return PHX_OK;
+}
+
+phx_status phx_gamma_multi_t(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_thz, const double* evec,
+                             const int32_t* irr_q, int32_t n_irr, const double* temperatures, int32_t n_t,
+                             phx_broadening br, double f_min_thz, int32_t prec, double* gamma, int32_t mem,
+                             void* stream) {
+    if (!ctx) return PHX_ERR_INVALID;
+    if (n_t < 0 || (n_t > 0 && !temperatures))
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_multi_t: bad temperature list");
+    if (n_t == 0 || n_irr == 0) return PHX_OK;
+    for (int t = 0; t < n_t; ++t)
+        if (!(temperatures[t] > 0.0) || !std::isfinite(temperatures[t]))
+            return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_multi_t: temperature %d not finite and > 0", t);
+    if (!fc3 || fc3->ctx != ctx) return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_multi_t: bad fc3 handle");
+    const int64_t per_t = (int64_t)n_irr * fc3->n;
+    const bool one_pass = prec != PHX_FP64 && !(fc3->nq == 1 && fc3->n > 192);
+    if (!one_pass) {
+        // FP64 reference and the Gamma-only cell: one full evaluation per temperature
+        for (int t = 0; t < n_t; ++t)
+            PHX_TRY(phx_gamma(ctx, fc3, freq_thz, evec, irr_q, n_irr, temperatures[t], br, f_min_thz, prec,
+                              gamma + t * per_t, nullptr, mem, stream));
+        return PHX_OK;
+    }
+    // argument checks of phx_gamma (first temperature), then the shared-contraction passes
+    if (n_irr < 0 || !freq_thz || !evec || !irr_q || !gamma)
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_multi_t: null argument");
+    if (!(br.sigma_thz > 0.0) || !(br.window > 0.0) || !(f_min_thz > 0.0) || !std::isfinite(f_min_thz))
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_multi_t: sigma, window and f_min must be > 0");
+    if (br.shape != PHX_GAUSS && br.shape != PHX_LORENTZ)
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_multi_t: unknown broadening shape %d", br.shape);
+    if (prec != PHX_TF32 && prec != PHX_BF16X3)
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_multi_t: unknown precision %d", prec);
+    if (mem != PHX_MEM_HOST && mem != PHX_MEM_DEVICE)
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_multi_t: bad mem flag %d", mem);
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    const int n = fc3->n, nq = fc3->nq;
+    const int64_t n2 = (int64_t)n * n;
+    std::vector<int32_t> irr_h(n_irr);
+    if (mem == PHX_MEM_HOST) {
+        std::memcpy(irr_h.data(), irr_q, n_irr * 4);
+    } else {
+        PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(irr_h.data(), irr_q, n_irr * 4, cudaMemcpyDeviceToHost, s));
+        PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
+    }
+    for (int i = 0; i < n_irr; ++i)
+        if (irr_h[i] < 0 || irr_h[i] >= nq)
+            return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_multi_t: irr_q[%d]=%d outside the mesh", i, irr_h[i]);
+    const double *d_f = nullptr, *d_e = nullptr;
+    const int32_t* d_irr = nullptr;
+    PHX_TRY(phx_stage_in(ctx, "g.f", freq_thz, (size_t)nq * n, mem, s, &d_f));
+    PHX_TRY(phx_stage_in(ctx, "g.e", evec, (size_t)nq * n2 * 2, mem, s, &d_e));
+    PHX_TRY(phx_stage_in(ctx, "g.irr", irr_q, (size_t)n_irr, mem, s, &d_irr));
+    double* o_g = nullptr;
+    PHX_TRY(phx_stage_out_buf(ctx, "g.og", gamma, (size_t)n_t * per_t, mem, &o_g));
+    double* nB = (double*)phx_ws(ctx, "g.nBt", (size_t)kTPerPass * nq * n * 8);
+    double* gacc = (double*)phx_ws(ctx, "g.gacct", (size_t)kTPerPass * per_t * 8);
+    if (!nB || !gacc) return PHX_ERR_NOMEM;
+    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(ctx->status_word, 0, 4, s));
+    GammaParams gp{};
+    gp.n = n;
+    gp.mesh[0] = fc3->mesh[0]; gp.mesh[1] = fc3->mesh[1]; gp.mesh[2] = fc3->mesh[2];
+    gp.nq = nq;
+    gp.shape = br.shape;
+    gp.sigma = br.sigma_thz;
+    gp.window = br.window;
+    gp.f_min = f_min_thz;
+    const double conv = phx::kEvA2AmuToPs2;
+    const double pref = phx::kPi * phx::kHbarEvPs * conv * conv * conv / (8.0 * nq);
+    for (int t0 = 0; t0 < n_t; t0 += kTPerPass) {
+        const int nt = std::min(kTPerPass, n_t - t0);
+        for (int t = 0; t < nt; ++t)
+            PHX_CUDA_CHECK(ctx, phx_launch_occupations(d_f, nq * n, temperatures[t0 + t], 0, nB + (int64_t)t * nq * n,
+                                                       nullptr, s));
+        PHX_CUDA_CHECK(ctx, cudaMemsetAsync(gacc, 0, (size_t)nt * per_t * 8, s));
+        gp.T = temperatures[t0];
+        PHX_TRY(phx_gamma_tc_multi_t(ctx, fc3, d_f, d_e, nB, nt, irr_h.data(), n_irr, gp, prec, gacc, s));
+        for (int t = 0; t < nt; ++t)
+            PHX_CUDA_CHECK(ctx, phx_launch_finalize((int)per_t, n, d_irr, d_f, gacc + t * per_t, nullptr, pref,
+                                                    1.0 / nq, f_min_thz, o_g + (t0 + t) * per_t, nullptr, s));
+        ctx->launches += 2 * nt;
+    }
+    if (mem == PHX_MEM_HOST) {
+        int32_t st = 0;
+        PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(gamma, o_g, (size_t)n_t * per_t * 8, cudaMemcpyDeviceToHost, s));
+        PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(&st, ctx->status_word, 4, cudaMemcpyDeviceToHost, s));
+        PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
+        if (st != 0) return phx_set_error(ctx, (phx_status)st, "phx_gamma_multi_t: a device wait gave up (status %d)", st);
     }
     return PHX_OK;
 }

@@ -74,7 +74,21 @@ struct phx_fc3 {
     // tensor-core path tables, built on first use (before any capture)
     int32_t* tc_seg_of = nullptr;   // [n][n][n_d] segment of (d, b, c) or -1
     int32_t* tc_ident = nullptr;    // [nq] 0..nq-1
+    // Gamma-only large-cell path (mesh 1x1x1): permutation-symmetrised F = Phi3/sqrt(mmm) with
+    // images summed, grouped by (row atom J, neighbour slot of atom K, gamma, beta) for
+    // W_a[3J+beta][3K+gamma] = sum_i F[i][3J+beta][3K+gamma] e_a[i]
+    bool g0_ready = false;
+    int g0_slots = 0;               // (J, K) atom pairs
+    int g0_max_slots = 0;           // largest neighbour count of one atom
+    int64_t g0_nnz = 0;
+    int32_t* g0_nbr_start = nullptr;   // [n_atoms + 1]
+    int32_t* g0_nbr_atom = nullptr;    // [g0_slots]
+    int64_t* g0_seg_start = nullptr;   // [9 g0_slots + 1]
+    int32_t* g0_ent_i = nullptr;       // [g0_nnz]
+    double* g0_ent_w = nullptr;        // [g0_nnz]
 };
+// gamma_cell.cu: builds the g0_* tables of a 1x1x1-mesh handle (host sort, upload)
+phx_status phx_fc3_prepare_cell(phx_ctx* ctx, const phx_cell* cell, const phx_ifc3* fc3, phx_fc3* h);
 
 // ---------------------------------------------------------------- host helpers
 
@@ -135,6 +149,10 @@ cudaError_t phx_launch_jacobi(double* A, double* V, int n, int nq, double* freq,
                               int32_t* status, cudaStream_t s);
 cudaError_t phx_launch_velocity(const double* evec, const double* Y, const double* freq, int n,
                                 int nq, double* vel, double* vv, cudaStream_t s);
+// eigh_large.cu: Gamma point of a cell with more than 64 atoms (device pair CSR in, device out)
+constexpr int kPhxMaxLargeModes = 16384;
+phx_status phx_eigh_gamma_large(phx_ctx* ctx, int na, const double* blk_val, const int32_t* pair_start,
+                                const double* masses, double* freq, double* evec, cudaStream_t s);
 
 // zgemm.cu: batched complex FP64 GEMM, row-major; see the kernel for the batch addressing.
 struct ZgemmBatch {

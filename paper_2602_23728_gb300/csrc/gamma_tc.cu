@@ -43,7 +43,8 @@ constexpr int kStageBytesPerPlane = kBoxRows * kChunkBytes;
 constexpr int kMaxNp = 192;                    // padded modes (or q' slots) per output half
 constexpr size_t kSmemLimit = 232448;          // 227 KB opt-in
 
-enum { EPI_M = 0, EPI_X = 1, EPI_G = 2 };
+enum { EPI_M = 0, EPI_X = 1, EPI_G = 2, EPI_GT = 3 };   // EPI_GT: EPI_G for up to kMaxT temperatures
+constexpr int kMaxT = 4;
 enum { P_BF16X3 = 0, P_TF32 = 1 };
 
 struct TcArgs {
@@ -79,6 +80,10 @@ struct TcArgs {
     int shape;
     double* gacc;               // [n] for this irreducible q (offset applied)
     double* wacc;               // may be null
+    // EPI_GT: n_t temperatures; nB holds n_t tables of nq * n, gacc n_t rows t_stride apart
+    int n_t;
+    int64_t nb_stride;
+    int64_t t_stride;
 };
 
 template <int PREC>
@@ -105,6 +110,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     __shared__ uint32_t tmem_base_slot;
     __shared__ volatile int abort_flag;
     __shared__ float s_f1[kMaxNp], s_n1[kMaxNp], s_if1[kMaxNp];
+    __shared__ float s_n1t[EPI == EPI_GT ? kMaxT * kMaxNp : 1];
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int np = args.np, mg = args.mg, NA = 2 * mg, nk = args.nk, stages = args.stages;
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             }
             epi_barrier();                 // every epilogue thread takes the same decision
             if (abort_flag) break;
-            if (EPI == EPI_G && p != cur_p) {
+            if ((EPI == EPI_G || EPI == EPI_GT) && p != cur_p) {
                 // partner tables of this problem's q' (the previous tile is done: barrier above)
                 q1 = args.t0 + p;
                 q2 = phx_third_index(args.iq, q1, args.m1, args.m2, args.m3);
@@ -301,6 +307,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     s_f1[j] = f1;
                     s_n1[j] = v ? (float)args.nB[(int64_t)q1 * args.n + j] : 0.0f;
                     s_if1[j] = (v && f1 >= args.f_min) ? 1.0f / f1 : 0.0f;   // 0 masks padding and soft partners
+                    if (EPI == EPI_GT)
+                        for (int t = 0; t < kMaxT; ++t)
+                            s_n1t[t * kMaxNp + j] =
+                                (v && t < args.n_t) ? (float)args.nB[t * args.nb_stride + (int64_t)q1 * args.n + j] : 0.0f;
                 }
                 epi_barrier();
                 cur_p = p;
@@ -343,6 +353,63 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                             store_operand<PREC>(args.out_hi, args.out_lo, idx, v[i]);
                         }
                     }
+                }
+            } else if (EPI == EPI_GT) {
+                // EPI_G for n_t temperatures: the deltas and |V|^2 are shared, only the
+                // occupations change (Sec. "Performance Optimization": multi-temperature split)
+                const int nu = row / args.n, n2i = row % args.n;
+                float f0 = 0.f, f2 = 0.f, nn2[kMaxT];
+#pragma unroll
+                for (int t = 0; t < kMaxT; ++t) nn2[t] = 0.f;
+                if (valid) {
+                    f0 = (float)args.freq[(int64_t)args.iq * args.n + args.nu0 + nu];
+                    f2 = (float)args.freq[(int64_t)q2 * args.n + n2i];
+#pragma unroll
+                    for (int t = 0; t < kMaxT; ++t)
+                        if (t < args.n_t) nn2[t] = (float)args.nB[t * args.nb_stride + (int64_t)q2 * args.n + n2i];
+                }
+                const bool live = valid && f0 >= args.f_min && f2 >= args.f_min;
+                const float inv_f02 = live ? 1.0f / (1558.5454565440389f * f0 * f2) : 0.0f;
+                const float d02 = f0 - f2, lim = args.window * args.sigma;
+                const bool gauss = args.shape == PHX_GAUSS;
+                const float a = -1.f / (args.sigma * args.sigma), h2 = 0.25f * args.sigma * args.sigma;
+                const float norm = gauss ? 0.56418958354775628f / args.sigma : 0.5f * args.sigma / 3.14159265358979f;
+                float gs[kMaxT];
+#pragma unroll
+                for (int t = 0; t < kMaxT; ++t) gs[t] = 0.f;
+                float vi[16];
+                for (int j0 = half * 16; j0 < mg; j0 += 32) {
+                    tc::tmem_ld16(taddr + j0, v);
+                    tc::tmem_ld16(taddr + mg + j0, vi);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int j = m0 + j0 + i;
+                        const float if1 = s_if1[j], f1 = s_f1[j];
+                        const float x = d02 - f1, y = d02 + f1;
+                        const float gd = fabsf(x) < lim ? (gauss ? __expf(a * x * x) : __frcp_rn(x * x + h2)) : 0.f;
+                        const float ga = fabsf(y) < lim ? (gauss ? __expf(a * y * y) : __frcp_rn(y * y + h2)) : 0.f;
+                        const float v2 = fmaf(v[i], v[i], vi[i] * vi[i]) * if1;
+#pragma unroll
+                        for (int t = 0; t < kMaxT; ++t) {
+                            const float n1 = s_n1t[t * kMaxNp + j];
+                            gs[t] = fmaf(v2, (1.f + nn2[t] + n1) * gd + 2.f * (n1 - nn2[t]) * ga, gs[t]);
+                        }
+                    }
+                }
+                const int key = valid ? nu : -1 - lane;
+#pragma unroll
+                for (int t = 0; t < kMaxT; ++t) {
+                    if (t >= args.n_t) break;
+                    double dg = (double)(gs[t] * norm * inv_f02);
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const double og = __shfl_down_sync(0xffffffffu, dg, off);
+                        const int ok2 = __shfl_down_sync(0xffffffffu, key, off);
+                        if (lane + off < 32 && ok2 == key) dg += og;
+                    }
+                    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+                    if (valid && (lane == 0 || prev != key) && dg != 0.0)
+                        atomicAdd(&args.gacc[t * args.t_stride + args.nu0 + nu], dg);
                 }
             } else {
                 // row (nu, nu'') holds V[nu'] = [Re | Im]; weight and reduce over nu'
@@ -783,10 +850,13 @@ phx_status tc_alloc(phx_ctx* ctx, int prec, size_t bw, size_t bm, size_t be, siz
 
 // Enqueue the whole linewidth computation of one job on `s` (kernel launches and memsets
 // only, so it can be captured into a graph).  gacc/wacc: [n_irr][n] accumulators, zeroed.
+// n_t > 0: the multi-temperature epilogue for n_t <= kMaxT occupation tables nb_stride apart,
+// accumulating into n_t linewidth arrays t_stride apart (wacc unused).
 template <int PREC>
 phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcBuffers& B, const double* freq,
                       const double* evec, const double* nB, const int32_t* irr_host, int n_irr, const GammaParams& gp,
-                      double* gacc, double* wacc, cudaStream_t s) {
+                      double* gacc, double* wacc, cudaStream_t s, int n_t = 0, int64_t nb_stride = 0,
+                      int64_t t_stride = 0) {
     const int n = P.n, nq = P.nq, kr = P.kr, kcp = P.kcp, kr_d = P.kr_d, kcp_d = P.kcp_d;
     const int np = P.np, mg = P.mg, Q = P.Q, qp_np = P.qp_np, n_nu = P.n_nu;
     const int64_t n2 = (int64_t)n * n;
@@ -842,6 +912,7 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
     aB.n = n; aB.freq = freq; aB.nB = nB;
     aB.m1 = f->mesh[0]; aB.m2 = f->mesh[1]; aB.m3 = f->mesh[2];
     aB.sigma = (float)gp.sigma; aB.window = (float)gp.window; aB.f_min = (float)gp.f_min; aB.shape = gp.shape;
+    aB.n_t = n_t; aB.nb_stride = nb_stride; aB.t_stride = t_stride;
 
     for (int si = 0; si < n_irr; ++si) {
         const int iq = irr_host[si];
@@ -892,7 +963,10 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
                 aB.b_idx = f->tc_ident + t0;
                 aB.t0 = t0;
                 pp = phx_prof_begin(ctx, s);
-                PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_G>(ctx, aB, P.stream_b, Qt, sms, s)));
+                if (n_t > 0)
+                    PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_GT>(ctx, aB, P.stream_b, Qt, sms, s)));
+                else
+                    PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_G>(ctx, aB, P.stream_b, Qt, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_GEMM_E1, fl_e, op_bytes * (double)Qt * ra * n);
                 ctx->launches += 3;
             }
@@ -904,13 +978,14 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
 template <int PREC>
 phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec, const double* nB,
                   const int32_t* irr_host, int n_irr, const GammaParams& gp, double* gacc, double* wacc,
-                  cudaStream_t s) {
+                  cudaStream_t s, int n_t = 0, int64_t nb_stride = 0, int64_t t_stride = 0) {
     TcPlan P;
     PHX_TRY(tc_plan(ctx, f, PREC, 0, &P));
     PHX_TRY(tc_prepare_fc3(ctx, const_cast<phx_fc3*>(f)));
     TcBuffers B;
     PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.bytes_e, P.bytes_p, P.nq, f->nnz, (int64_t)P.n * P.n, &B));
-    return tc_enqueue<PREC>(ctx, P, f, B, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s);
+    return tc_enqueue<PREC>(ctx, P, f, B, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s, n_t, nb_stride,
+                            t_stride);
 }
 
 }  // namespace
@@ -922,6 +997,18 @@ phx_status phx_gamma_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, cons
         return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path needs a Blackwell (sm_10x) device");
     if (prec == PHX_BF16X3) return run_tc<P_BF16X3>(ctx, f, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s);
     return run_tc<P_TF32>(ctx, f, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s);
+}
+
+phx_status phx_gamma_tc_multi_t(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec,
+                                const double* nB, int n_t, const int32_t* irr_host, int n_irr, const GammaParams& gp,
+                                int prec, double* gacc, cudaStream_t s) {
+    if (ctx->cc_major != 10)
+        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path needs a Blackwell (sm_10x) device");
+    if (n_t < 1 || n_t > kMaxT) return phx_set_error(ctx, PHX_ERR_INVALID, "multi-temperature pass of %d", n_t);
+    const int64_t nb_stride = (int64_t)f->nq * f->n, t_stride = (int64_t)n_irr * f->n;
+    if (prec == PHX_BF16X3)
+        return run_tc<P_BF16X3>(ctx, f, freq, evec, nB, irr_host, n_irr, gp, gacc, nullptr, s, n_t, nb_stride, t_stride);
+    return run_tc<P_TF32>(ctx, f, freq, evec, nB, irr_host, n_irr, gp, gacc, nullptr, s, n_t, nb_stride, t_stride);
 }
 
 // ---------------------------------------------------------------- batched jobs (one CUDA graph)

@@ -405,6 +405,27 @@ def run_phx(args):
                              "gamma_max_rel_err_vs_fp64": float((np.abs(a - b)[big] / b[big]).max())}
         line["speedup_vs_fp64_path"] = value / world / (trip64 / t64)
 
+    if args.multi_t > 0:
+        # several temperatures from one contraction against one call per temperature
+        w = wl.w
+        temps = [float(x) for x in np.linspace(20.0, 80.0, args.multi_t)]
+        gm = torch.zeros((len(temps), wl.irr_d.shape[0], wl.n), dtype=torch.float64, device=device)
+        g1 = torch.zeros((wl.irr_d.shape[0], wl.n), dtype=torch.float64, device=device)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        wl.ctx.gamma_multi_t(wl.h, wl.freq, wl.evec, wl.irr_d, temps, w.shape, w.sigma_thz, w.window, w.f_min_thz,
+                             precision=args.precision, gamma=gm)
+        e1.record(stream)
+        for T in temps:
+            wl.ctx.gamma(wl.h, wl.freq, wl.evec, wl.irr_d, T, w.shape, w.sigma_thz, w.window, w.f_min_thz,
+                         precision=args.precision, gamma=g1)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        ms_m, ms_s = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        line["multi_t"] = {"temperatures_K": temps, "ms_one_contraction": ms_m, "ms_one_call_per_T": ms_s,
+                           "speedup": ms_s / ms_m,
+                           "value": len(temps) * trip / (ms_m / 1e3), "unit": "temperature-triplets/s"}
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, ctrip, desc = oracle_sample(n_qp=args.cpu_qp)
         line["cpu_baseline"] = {"value": ctrip / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
@@ -599,7 +620,7 @@ def run_cell(args):
     peaks = load_peaks()
     per = {k: v for k, v in prof.items() if k != "launches" and v[1] > 0}
     ms_k = {k: v[0] / args.steps for k, v in per.items()}
-    top = max(("cell_sparse", "cell_gemm", "cell_transpose", "eigensolver"), key=lambda k: ms_k.get(k, 0.0))
+    top = max(("cell_sparse", "cell_gemm", "cell_transpose"), key=lambda k: ms_k.get(k, 0.0))
     ms_top, n_top, fl_top, by_top = per[top]
     if top == "cell_gemm":
         peak = peaks["bf16_tflops_sustained"] / 3.0 if args.precision == "bf16x3" else \
@@ -655,6 +676,8 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32", "fp64"])
     ap.add_argument("--fp64-q", type=int, default=4, help="irreducible q timed on the FP64 GPU path (0: skip)")
     ap.add_argument("--cpu-qp", type=int, default=None, help="q' of the oracle sample (default all)")
+    ap.add_argument("--multi-t", type=int, default=4,
+                    help="temperatures timed in one contraction vs one call each (0: skip)")
     ap.add_argument("--ref-qp", type=int, default=64, help="q' per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fcc32",

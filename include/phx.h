@@ -124,12 +124,12 @@ phx_status phx_irreducible(const int32_t mesh[3], int32_t n_rot, const int32_t* 
  *                       (|df| < 1e-5 max|f|) every mode gets
  *                       (1/|S|) sum_{m,m' in S} Re(V^a_{mm'} V^b_{m'm})/(4 w^2)         [mem, may be NULL]
  * n = 3 * cell->n_atoms, 3 <= n <= 192 for any q.
- * Larger cells (192 < n <= 16384; Eq. (eigenvalue), the real-space problem of a Gamma-only or
+ * Larger cells (192 < n <= 8192; Eq. (eigenvalue), the real-space problem of a Gamma-only or
  * disordered cell): every q must be a lattice vector (Gamma), vel and vv must be NULL, and D is
  * real symmetric; it is solved in FP64 by Householder reduction to tridiagonal form, Sturm
  * bisection, inverse iteration (eigenvalues closer than 1e-7 ||D|| orthogonalised as a
  * cluster) and back-transformation.  evec then holds real columns (imaginary parts 0), largest
- * component positive.  Device workspace ~49 n^2 bytes (441 MB at n = 3000).
+ * component positive.  Device workspace ~57 n^2 bytes (513 MB at n = 3000).
  * Errors: PHX_ERR_INVALID (block index out of range), PHX_ERR_UNSUPPORTED (q != Gamma or
  * velocities requested for n > 192), PHX_ERR_NUMERIC (no convergence / non-finite result). */
 phx_status phx_harmonic(phx_ctx* ctx, const phx_cell* cell, const phx_ifc2* fc2,
@@ -177,9 +177,24 @@ phx_status phx_gamma_multi_t(phx_ctx* ctx, const phx_fc3* fc3, const double* fre
                              const double* temperatures, int32_t n_t, phx_broadening br,
                              double f_min_thz, int32_t prec, double* gamma, int32_t mem, void* stream);
 
+/* Isotope / mass-variance scattering, Eq. (isotope) (Tamura):
+ *   gamma_iso(q s) = pi/(2 N_q) w^2 sum_{q' s'} delta(w - w') sum_i g_i |<e_i(q s)|e_i(q' s')>|^2
+ * with the per-atom overlap <e_i|e'_i> = sum_alpha conj(e[3i+alpha]) e'[3i+alpha] (the Cartesian
+ * sum inside the modulus, the frame-invariant placement), delta(w) = g(f)/(2 pi) with the
+ * broadening and window of phx_gamma, modes and partners below f_min_thz skipped.  The total
+ * rate of the paper is gamma = gamma_anh + gamma_iso (add the two outputs).
+ * Inputs: freq_thz[nq][n], evec[nq][n][n] over the full mesh (complex; nq = N_q) [mem];
+ * irr_q[n_irr] [mem]; g_atom[n/3] (host): g_i = sum_iso f (dM/M)^2 per atom of the cell.
+ * Output: gamma[n_irr][n] (1/ps) [mem].  FP64 on the CUDA cores; n <= 12800.
+ * Errors: PHX_ERR_INVALID (bad sizes, g < 0, sigma/window/f_min <= 0, index out of range). */
+phx_status phx_gamma_isotope(phx_ctx* ctx, int32_t nq, int32_t n, const double* freq_thz,
+                             const double* evec, const int32_t* irr_q, int32_t n_irr,
+                             const double* g_atom, phx_broadening br, double f_min_thz,
+                             double* gamma, int32_t mem, void* stream);
+
 /* ---------------------------------------------------------------- Gamma-only large cell
  * Eq. (phi3_proj) at q = q' = q'' = 0 and Eq. (gamma) with N_q = 1 for every mode of a
- * (disordered) cell of up to 16384/3 atoms: the real-space treatment of Gamma-only and
+ * (disordered) cell of up to 8192/3 atoms: the real-space treatment of Gamma-only and
  * amorphous systems.  fc3 must come from phx_fc3_create with mesh {1, 1, 1}; on creation its
  * COO is summed over images and symmetrised over the permutations of (i, j, k) (a third
  * derivative is symmetric; input that already is stays unchanged).
@@ -331,7 +346,11 @@ typedef enum {
     PHX_K_CELL_SPARSE = 7,  /* Gamma-only cell: W_a = F e_a and X_a = W_a E (CUDA cores)      */
     PHX_K_CELL_TRANSPOSE = 8, /* Gamma-only cell: operand layout transposes                   */
     PHX_K_CELL_GEMM = 9,    /* Gamma-only cell: E^T X_a tiles + fused role-weight epilogue   */
-    PHX_K_COUNT = 10
+    PHX_K_EIG_TRIDIAG = 10, /* large-cell eigensolver: dynamical matrix + Householder steps  */
+    PHX_K_EIG_VECTORS = 11, /* large-cell eigensolver: inverse iteration                    */
+    PHX_K_EIG_BACK = 12,    /* large-cell eigensolver: back-transformation + output          */
+    PHX_K_EIG_BISECT = 13,  /* large-cell eigensolver: Sturm multisection (eigenvalues)      */
+    PHX_K_COUNT = 14
 } phx_kernel_class;
 
 /* Turn profiling on (1) or off (0); turning it on clears the counters.  Off by default. */

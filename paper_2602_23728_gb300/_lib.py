@@ -81,6 +81,8 @@ lib.phx_gamma.argtypes = [_P, _P, _P, _P, _P, _I, C.c_double, Broadening, C.c_do
 lib.phx_gamma.restype = C.c_int
 lib.phx_gamma_multi_t.argtypes = [_P, _P, _P, _P, _P, _I, _P, _I, Broadening, C.c_double, _I, _P, _I, _P]
 lib.phx_gamma_multi_t.restype = C.c_int
+lib.phx_gamma_isotope.argtypes = [_P, _I, _I, _P, _P, _P, _I, _P, Broadening, C.c_double, _P, _I, _P]
+lib.phx_gamma_isotope.restype = C.c_int
 lib.phx_gamma_cell.argtypes = [_P, _P, _P, _P, C.c_double, Broadening, C.c_double, _I, _P, _I, _P]
 lib.phx_gamma_cell.restype = C.c_int
 lib.phx_unfold.argtypes = [_P, _I, _I, _I, _P, _P, _P, _P, _P, _I, _P]
@@ -119,10 +121,11 @@ lib.phx_mlp_predict.argtypes = [_P, _P, _I, _P, _P, _P]
 lib.phx_mlp_predict.restype = C.c_int
 
 KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4, "fp64_epilogue": 5,
-           "eigensolver": 6, "cell_sparse": 7, "cell_transpose": 8, "cell_gemm": 9}
+           "eigensolver": 6, "cell_sparse": 7, "cell_transpose": 8, "cell_gemm": 9, "eig_tridiag": 10,
+           "eig_vectors": 11, "eig_back": 12, "eig_bisect": 13}
 
 EXPORTED = ["phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
-            "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta",
+            "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_isotope", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta",
             "phx_kappa_rta_noalloc", "phx_gamma_batched", "phx_features", "phx_mlp_create", "phx_mlp_destroy",
             "phx_mlp_num_params", "phx_mlp_get_params", "phx_mlp_set_params", "phx_mlp_loss_grad", "phx_mlp_train",
             "phx_mlp_predict"]
@@ -327,6 +330,22 @@ class Context:
         self._check(lib.phx_gamma_multi_t(self.h, fc3.h, _ptr(freq), _ptr(evec), _ptr(irr_q), int(irr_q.shape[0]),
                                           temps.ctypes.data, int(temps.shape[0]), br, float(f_min),
                                           PRECISIONS[precision], _ptr(gamma), mem, stream))
+        return gamma
+
+    def gamma_isotope(self, freq, evec, irr_q, g_atom, shape="gauss", sigma=0.1, window=2.0, f_min=0.01,
+                      gamma=None):
+        """phx_gamma_isotope: Tamura mass-variance rates [n_irr][n] (freq [nq, n], evec [nq, n, n])."""
+        br = Broadening(SHAPES[shape], float(sigma), float(window))
+        g = _host(g_atom, np.float64).reshape(-1)
+        nq, n = int(freq.shape[0]), int(freq.shape[1])
+        if not _is_torch(freq):
+            freq = _host(freq, np.float64)
+            evec = _host(evec, np.complex128)
+            irr_q = _host(irr_q, np.int32)
+            gamma = np.zeros((irr_q.shape[0], n)) if gamma is None else gamma
+        mem, stream = _mem_and_stream([freq, evec, irr_q, gamma])
+        self._check(lib.phx_gamma_isotope(self.h, nq, n, _ptr(freq), _ptr(evec), _ptr(irr_q), int(irr_q.shape[0]),
+                                          g.ctypes.data, br, float(f_min), _ptr(gamma), mem, stream))
         return gamma
 
     def gamma_cell(self, fc3, freq, evec, temperature, shape="lorentz", sigma=0.1, window=2.0, f_min=0.01,

@@ -150,7 +150,7 @@ cudaError_t phx_launch_jacobi(double* A, double* V, int n, int nq, double* freq,
 cudaError_t phx_launch_velocity(const double* evec, const double* Y, const double* freq, int n,
                                 int nq, double* vel, double* vv, cudaStream_t s);
 // eigh_large.cu: Gamma point of a cell with more than 64 atoms (device pair CSR in, device out)
-constexpr int kPhxMaxLargeModes = 16384;
+constexpr int kPhxMaxLargeModes = 8192;
 phx_status phx_eigh_gamma_large(phx_ctx* ctx, int na, const double* blk_val, const int32_t* pair_start,
                                 const double* masses, double* freq, double* evec, cudaStream_t s);
 

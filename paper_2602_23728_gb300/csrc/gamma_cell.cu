@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -103,17 +104,21 @@ __global__ void w_kernel(const int64_t* __restrict__ seg_start, const int32_t* _
     }
 }
 
-// X[al][j][cc] = sum_{k in nbr(J)} W_a[j][k] E[k][c_base + cc], one thread per column c, LA modes
-// per CTA, atom rows J in [blockIdx.y * tj, ...).  W of the current J is staged in shared memory.
-template <typename T, int LA>
+// X[al][j][cc] = sum_{k in nbr(J)} W_a[j][k] E[k][c_base + cc].  A CTA covers NC x 256 columns
+// (thread t: columns t, t + 256, ...), LA modes and the atom rows J in [blockIdx.y * tj, ...);
+// W of the current J is staged in shared memory and read as LA-wide vectors, each value
+// feeding NC columns.
+template <typename T, int LA, int NC>
 __global__ void __launch_bounds__(256)
 xform_kernel(const T* __restrict__ E, int pe, const T* __restrict__ W, int64_t n_seg,
              const int32_t* __restrict__ nbr_start, const int32_t* __restrict__ nbr_atom, int na, int n, int c_base,
              int ncc, int tj, int L, T* __restrict__ X) {
+    static_assert(LA % 4 == 0, "LA must be a multiple of 4");
     extern __shared__ __align__(16) uint8_t xs_raw[];
     T* Ws = (T*)xs_raw;
-    const int cc = blockIdx.x * 256 + threadIdx.x;
-    const int c = c_base + cc;
+    int cc[NC];
+#pragma unroll
+    for (int u = 0; u < NC; ++u) cc[u] = blockIdx.x * (256 * NC) + u * 256 + threadIdx.x;
     const int asub = blockIdx.z;
     const T* Wsub = W + (int64_t)asub * n_seg * LA;
     const int J0 = blockIdx.y * tj, J1 = min(na, J0 + tj);
@@ -122,28 +127,64 @@ xform_kernel(const T* __restrict__ E, int pe, const T* __restrict__ W, int64_t n
         const T* src = Wsub + (int64_t)s0 * 9 * LA;
         for (int t = threadIdx.x; t < ns * 9 * LA; t += 256) Ws[t] = src[t];
         __syncthreads();
-        if (cc < ncc) {
-            T acc[LA][3];
+        T acc[NC][LA][3];
 #pragma unroll
-            for (int la = 0; la < LA; ++la) acc[la][0] = acc[la][1] = acc[la][2] = T(0);
-            for (int s = 0; s < ns; ++s) {
-                const int K = nbr_atom[s0 + s];
-                const T e0 = E[(int64_t)(3 * K) * pe + c];
-                const T e1 = E[(int64_t)(3 * K + 1) * pe + c];
-                const T e2 = E[(int64_t)(3 * K + 2) * pe + c];
-                const T* w = Ws + s * 9 * LA;
+        for (int u = 0; u < NC; ++u)
+#pragma unroll
+            for (int la = 0; la < LA; ++la) acc[u][la][0] = acc[u][la][1] = acc[u][la][2] = T(0);
+        // E rows of the next neighbour are loaded while the current one is consumed
+        T en[NC][3];
+        {
+            const int64_t k0 = (int64_t)(3 * nbr_atom[s0]) * pe + c_base;
+#pragma unroll
+            for (int u = 0; u < NC; ++u)
+#pragma unroll
+                for (int g = 0; g < 3; ++g) en[u][g] = (ns > 0 && cc[u] < ncc) ? E[k0 + g * pe + cc[u]] : T(0);
+        }
+        for (int s = 0; s < ns; ++s) {
+            T e[NC][3];
+#pragma unroll
+            for (int u = 0; u < NC; ++u)
+#pragma unroll
+                for (int g = 0; g < 3; ++g) e[u][g] = en[u][g];
+            if (s + 1 < ns) {
+                const int64_t k1 = (int64_t)(3 * nbr_atom[s0 + s + 1]) * pe + c_base;
+#pragma unroll
+                for (int u = 0; u < NC; ++u)
+#pragma unroll
+                    for (int g = 0; g < 3; ++g) en[u][g] = cc[u] < ncc ? E[k1 + g * pe + cc[u]] : T(0);
+            }
+            const T* w = Ws + s * 9 * LA;
+#pragma unroll
+            for (int g = 0; g < 3; ++g)
 #pragma unroll
                 for (int be = 0; be < 3; ++be)
 #pragma unroll
-                    for (int la = 0; la < LA; ++la)
-                        acc[la][be] += e0 * w[(0 + be) * LA + la] + e1 * w[(3 + be) * LA + la] + e2 * w[(6 + be) * LA + la];
-            }
+                    for (int l4 = 0; l4 < LA; l4 += 4) {
+                        T wv[4];
+                        if (sizeof(T) == 4) {
+                            const float4 q = *reinterpret_cast<const float4*>(w + (g * 3 + be) * LA + l4);
+                            wv[0] = (T)q.x; wv[1] = (T)q.y; wv[2] = (T)q.z; wv[3] = (T)q.w;
+                        } else {
+                            const double2 q0 = *reinterpret_cast<const double2*>(w + (g * 3 + be) * LA + l4);
+                            const double2 q1 = *reinterpret_cast<const double2*>(w + (g * 3 + be) * LA + l4 + 2);
+                            wv[0] = (T)q0.x; wv[1] = (T)q0.y; wv[2] = (T)q1.x; wv[3] = (T)q1.y;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int u = 0; u < NC; ++u) acc[u][l4 + i][be] += e[u][g] * wv[i];
+                    }
+        }
+#pragma unroll
+        for (int u = 0; u < NC; ++u) {
+            if (cc[u] >= ncc) continue;
 #pragma unroll
             for (int la = 0; la < LA; ++la) {
                 const int al = asub * LA + la;
                 if (al < L)
 #pragma unroll
-                    for (int be = 0; be < 3; ++be) X[((int64_t)al * n + 3 * J + be) * ncc + cc] = acc[la][be];
+                    for (int be = 0; be < 3; ++be) X[((int64_t)al * n + 3 * J + be) * ncc + cc[u]] = acc[u][la][be];
             }
         }
         __syncthreads();
@@ -156,21 +197,21 @@ template <typename Tin, int PREC>
 __global__ void transpose_kernel(const Tin* __restrict__ in, int64_t in_zstride, int in_pitch, int rows_in,
                                  int cols_in, void* __restrict__ out_hi, void* __restrict__ out_lo,
                                  int64_t out_zstride, int out_pitch, int rows_out) {
-    __shared__ double tile[32][33];
+    __shared__ Tin tile[32][33];
     const int z = blockIdx.z;
     const int j0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;         // 32 x 8
     for (int yy = ty; yy < 32; yy += 8) {
         const int j = j0 + yy, r = r0 + tx;
-        double v = 0.0;
-        if (j < rows_in && r < cols_in) v = (double)in[(int64_t)z * in_zstride + (int64_t)j * in_pitch + r];
+        Tin v = Tin(0);
+        if (j < rows_in && r < cols_in) v = in[(int64_t)z * in_zstride + (int64_t)j * in_pitch + r];
         tile[yy][tx] = v;
     }
     __syncthreads();
     for (int yy = ty; yy < 32; yy += 8) {
         const int r = r0 + yy, j = j0 + tx;
         if (r >= rows_out || j >= out_pitch) continue;
-        const double v = tile[tx][yy];
+        const double v = (double)tile[tx][yy];
         const int64_t idx = (int64_t)z * out_zstride + (int64_t)r * out_pitch + j;
         if (PREC == P_BF16X3) {
             __nv_bfloat16 h, l;
@@ -674,8 +715,18 @@ extern "C" phx_status phx_gamma_cell(phx_ctx* ctx, const phx_fc3* fc3, const dou
                 transpose_kernel<double, P_FP64><<<grid, block, 0, s>>>(e64, 0, pe, n, n, et_hi, nullptr, 0, kpad, pe);
             ctx->launches += 1;
         }
+        // FP32 product shape: LA modes per CTA x NC columns per thread (PHX_XFORM = "16x1", "16x2",
+        // "8x2" or "8x4" to tune; default 16x1)
+        static const int xcfg = [] {
+            const char* v = std::getenv("PHX_XFORM");
+            if (!v) return 161;
+            if (!std::strcmp(v, "16x2")) return 162;
+            if (!std::strcmp(v, "8x2")) return 82;
+            if (!std::strcmp(v, "8x4")) return 84;
+            return 161;
+        }();
         // chunks of consecutive work modes, sized to ~6 GB of X + XT
-        const int LA = P == P_FP64 ? 8 : 16;
+        const int LA = P == P_FP64 ? 8 : xcfg / 10;
         const size_t xbytes = P == P_FP64 ? 8 : 4;
         const size_t per_a = (size_t)n * pe * xbytes + (size_t)pe * kpad * (P == P_FP64 ? 8 : 4);
         int L = (int)std::min<size_t>(128, ((size_t)6 << 30) / per_a);
@@ -717,8 +768,11 @@ extern "C" phx_status phx_gamma_cell(phx_ctx* ctx, const phx_fc3* fc3, const dou
                                  fc3->g0_max_slots);
         static bool attr_done = false;
         if (!attr_done) {
-            cudaFuncSetAttribute(xform_kernel<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDyn);
-            cudaFuncSetAttribute(xform_kernel<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDyn);
+            cudaFuncSetAttribute(xform_kernel<float, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDyn);
+            cudaFuncSetAttribute(xform_kernel<float, 16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDyn);
+            cudaFuncSetAttribute(xform_kernel<float, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDyn);
+            cudaFuncSetAttribute(xform_kernel<float, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDyn);
+            cudaFuncSetAttribute(xform_kernel<double, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDyn);
             cudaFuncSetAttribute(sym_tc_kernel<P_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDyn);
             cudaFuncSetAttribute(sym_tc_kernel<P_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDyn);
             attr_done = true;
@@ -736,19 +790,38 @@ extern "C" phx_status phx_gamma_cell(phx_ctx* ctx, const phx_fc3* fc3, const dou
             const int64_t wtot = (int64_t)n_asub * n_seg * LA;
             const unsigned wblocks = (unsigned)std::min<int64_t>((wtot + 255) / 256, 64 * ctx->sm_count);
             const int tj = 4;
-            dim3 xgrid((ncc + 255) / 256, (na + tj - 1) / tj, n_asub);
+            const int xnc = xcfg % 10;
+            const int ncol = P == P_FP64 ? 256 : 256 * xnc;     // columns per CTA (NC x 256)
+            dim3 xgrid((ncc + ncol - 1) / ncol, (na + tj - 1) / tj, n_asub);
             if (P == P_FP64) {
                 w_kernel<double, 8><<<wblocks, 256, 0, s>>>(fc3->g0_seg_start, fc3->g0_ent_i, fc3->g0_ent_w, n_seg, e64,
                                                             pe, d_chunk_a + ch.a_begin, Lc, n_asub, (double*)Wb);
-                xform_kernel<double, 8><<<xgrid, 256, xs_smem, s>>>(e64, pe, (const double*)Wb, n_seg, fc3->g0_nbr_start,
+                xform_kernel<double, 8, 1><<<xgrid, 256, xs_smem, s>>>(e64, pe, (const double*)Wb, n_seg, fc3->g0_nbr_start,
                                                                     fc3->g0_nbr_atom, na, n, ch.c_base, ncc, tj, Lc,
                                                                     (double*)Xb);
             } else {
-                w_kernel<float, 16><<<wblocks, 256, 0, s>>>(fc3->g0_seg_start, fc3->g0_ent_i, fc3->g0_ent_w, n_seg, e64,
-                                                            pe, d_chunk_a + ch.a_begin, Lc, n_asub, (float*)Wb);
-                xform_kernel<float, 16><<<xgrid, 256, xs_smem, s>>>(e32, pe, (const float*)Wb, n_seg, fc3->g0_nbr_start,
-                                                                    fc3->g0_nbr_atom, na, n, ch.c_base, ncc, tj, Lc,
-                                                                    (float*)Xb);
+                const int* ns_ = fc3->g0_nbr_start;
+                const int* na_ = fc3->g0_nbr_atom;
+                if (LA == 16)
+                    w_kernel<float, 16><<<wblocks, 256, 0, s>>>(fc3->g0_seg_start, fc3->g0_ent_i, fc3->g0_ent_w, n_seg,
+                                                                e64, pe, d_chunk_a + ch.a_begin, Lc, n_asub, (float*)Wb);
+                else
+                    w_kernel<float, 8><<<wblocks, 256, 0, s>>>(fc3->g0_seg_start, fc3->g0_ent_i, fc3->g0_ent_w, n_seg,
+                                                               e64, pe, d_chunk_a + ch.a_begin, Lc, n_asub, (float*)Wb);
+                const float* Wf = (const float*)Wb;
+                float* Xf = (float*)Xb;
+                if (xcfg == 162)
+                    xform_kernel<float, 16, 2><<<xgrid, 256, xs_smem, s>>>(e32, pe, Wf, n_seg, ns_, na_, na, n, ch.c_base,
+                                                                          ncc, tj, Lc, Xf);
+                else if (xcfg == 82)
+                    xform_kernel<float, 8, 2><<<xgrid, 256, xs_smem, s>>>(e32, pe, Wf, n_seg, ns_, na_, na, n, ch.c_base,
+                                                                         ncc, tj, Lc, Xf);
+                else if (xcfg == 84)
+                    xform_kernel<float, 8, 4><<<xgrid, 256, xs_smem, s>>>(e32, pe, Wf, n_seg, ns_, na_, na, n, ch.c_base,
+                                                                         ncc, tj, Lc, Xf);
+                else
+                    xform_kernel<float, 16, 1><<<xgrid, 256, xs_smem, s>>>(e32, pe, Wf, n_seg, ns_, na_, na, n, ch.c_base,
+                                                                          ncc, tj, Lc, Xf);
             }
             PHX_CUDA_CHECK(ctx, cudaGetLastError());
             // algorithmic work of X = W E: 2 x (3 x slots) x n_cols per mode

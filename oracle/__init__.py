@@ -18,10 +18,11 @@ Modules
   supercell  -- Gamma-only brute force of Eq. (phi3_proj) on a supercell (folding pin)
   gammapoint -- Gamma-only linewidths of a large cell mode by mode, sparse Phi3 (1000-atom cell)
   isotope    -- Eq. (isotope): Tamura mass-variance scattering
+  qhgk       -- Eqs. (qhgk), (qhgk_crystal): quasi-harmonic Green-Kubo conductivity
   surrogate  -- FP64 reference of the linewidth surrogate network (checks the GPU training)
 
 Parity status: every function here is pinned by tests under tests/ (closed forms,
 invariants, brute force); none is "parity unpinned" except the absolute value of the
 LJ-argon conductivity, for which the paper prints no number.
 """
-from . import constants, grid, harmonic, occupation, anharmonic, transport, supercell, surrogate, gammapoint, isotope  # noqa: F401
+from . import constants, grid, harmonic, occupation, anharmonic, transport, supercell, surrogate, gammapoint, isotope, qhgk  # noqa: F401

@@ -557,7 +557,8 @@ def run_surrogate(args):
 
 def run_cell(args):
     """Gamma-only disordered cell: 1000 atoms (3000 modes), Lorentzian (half width 0.05 THz),
-    300 K.  One step = the 3000 x 3000 FP64 eigensolve and the linewidths of all modes.  A
+    300 K.  One step = the 3000 x 3000 FP64 eigensolve, the linewidths of all modes and the
+    QHGK conductivity (Eq. qhgk).  A
     triplet is one (lambda, nu', nu'') with lambda above f_min, so a step holds
     n_live x 3000^2 of them (each unordered triple is evaluated once; the count is that of the
     ordered sum).  The FP64 GPU path is timed once beside it and the oracle on two modes."""
@@ -581,10 +582,13 @@ def run_cell(args):
     kw = dict(shape=w.shape, sigma=w.sigma_thz, window=w.window, f_min=w.f_min_thz)
     t_setup = time.perf_counter() - t_setup
 
+    f2v = f2.val.reshape(-1, 9)
+
     def step(prec):
-        ctx.harmonic(c.lattice, c.masses, f2.idx, f2.val.reshape(-1, 9), q, freq=freq, evec=evec, want_vel=False,
-                     want_vv=False)
+        ctx.harmonic(c.lattice, c.masses, f2.idx, f2v, q, freq=freq, evec=evec, want_vel=False, want_vv=False)
         ctx.gamma_cell(h, freq[0], evec[0], w.temperature, precision=prec, gamma=gam, **kw)
+        return ctx.kappa_qhgk(c.lattice, c.masses, c.positions, f2.idx, f2v, freq[0], evec[0], gam, w.temperature,
+                              f_min=w.f_min_thz)
 
     for _ in range(args.warmup):
         step(args.precision)
@@ -604,6 +608,8 @@ def run_cell(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     prof = ctx.profile_read()
     ctx.profile_enable(False)
+    kappa_q = step(args.precision)
+    torch.cuda.synchronize()
     g_mixed = gam.cpu().numpy().copy()
     f_h = freq[0].cpu().numpy()
     e_h = evec[0].cpu().numpy()
@@ -639,9 +645,14 @@ def run_cell(args):
         ach = by_top / (ms_top / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": top}
+    # the conductivity with the FP64 linewidths, for the kappa error of the chosen precision
+    kappa_64 = ctx.kappa_qhgk(c.lattice, c.masses, c.positions, f2.idx, f2v, freq[0], evec[0], gam, w.temperature,
+                              f_min=w.f_min_thz)
+    kerr = float(np.linalg.norm(kappa_q - kappa_64) / np.linalg.norm(kappa_64))
     line = {"metric": METRIC, "value": trip / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "kappa_qhgk_wmk": np.diag(kappa_q).tolist(), "kappa_rel_err_vs_fp64_linewidths": kerr,
             "config": {"workload": "Gamma-only disordered cell: 10x10x10 primitive LJ fcc = 1000 atoms, 3000 modes, "
                                    "N(0, 0.05 A) noise seed 5 relaxed to max force 1e-8 eV/A, 50/50 masses "
                                    "39.95/83.8, sparse COO Phi3 (r_c 8.5 A), Lorentzian half width 0.05 THz, 300 K",

@@ -192,6 +192,23 @@ phx_status phx_gamma_isotope(phx_ctx* ctx, int32_t nq, int32_t n, const double* 
                              const double* g_atom, phx_broadening br, double f_min_thz,
                              double* gamma, int32_t mem, void* stream);
 
+/* Quasi-harmonic Green-Kubo conductivity of a Gamma-only cell, Eq. (qhgk):
+ *   kappa_ab = 1/V sum_{mu mu'} c_{mu mu'} Re(v^a_{mu mu'} v^b_{mu' mu}) tau_{mu mu'}
+ * c_{mu mu'} = (hbar w w'/T)(n - n')/(w' - w) (the average of c_mu and c_mu' of Eq. (heatcap)
+ * for |f - f'| < 1e-5 f_max); v^a_{mu mu'} = <e_mu|dD/dq_a|e_mu'>/(2 sqrt(w w')) with the
+ * atom-position-gauge derivative dD/dq_a = -i sum_R (x_j + R - x_i)_a Phi2(0i, Rj)/sqrt(m m);
+ * tau_{mu mu'} = g/(2((w - w')^2 + g^2)), g = (gamma_mu + gamma_mu')/4 (so tau_mu mu = 1/gamma_mu).
+ * Modes below f_min_thz or with gamma <= 0 are left out; V is the cell volume.
+ * Inputs: cell (lattice, positions, masses), fc2 (blocks with image vectors R), freq_thz[n],
+ * evec[n][n] complex with zero imaginary parts (as phx_harmonic returns at Gamma), gamma[n]
+ * (1/ps, e.g. from phx_gamma_cell) [mem]; output kappa_wmk[9] (host, W/(m K)).
+ * FP64: sparse G E, dense E^T (G E) on 128 x 128 upper-triangle tiles, pair sum.  Workspace
+ * 7 n^2 doubles.  The call synchronises the stream.  Errors: PHX_ERR_INVALID (complex
+ * eigenvectors, bad indices, T or f_min <= 0), PHX_ERR_UNSUPPORTED (n > 8192). */
+phx_status phx_kappa_qhgk(phx_ctx* ctx, const phx_cell* cell, const phx_ifc2* fc2, const double* freq_thz,
+                          const double* evec, const double* gamma, double temperature, double f_min_thz,
+                          double kappa_wmk[9], int32_t mem, void* stream);
+
 /* ---------------------------------------------------------------- Gamma-only large cell
  * Eq. (phi3_proj) at q = q' = q'' = 0 and Eq. (gamma) with N_q = 1 for every mode of a
  * (disordered) cell of up to 8192/3 atoms: the real-space treatment of Gamma-only and

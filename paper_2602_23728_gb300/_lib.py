@@ -83,6 +83,8 @@ lib.phx_gamma_multi_t.argtypes = [_P, _P, _P, _P, _P, _I, _P, _I, Broadening, C.
 lib.phx_gamma_multi_t.restype = C.c_int
 lib.phx_gamma_isotope.argtypes = [_P, _I, _I, _P, _P, _P, _I, _P, Broadening, C.c_double, _P, _I, _P]
 lib.phx_gamma_isotope.restype = C.c_int
+lib.phx_kappa_qhgk.argtypes = [_P, C.POINTER(Cell), C.POINTER(Ifc2), _P, _P, _P, C.c_double, C.c_double, _P, _I, _P]
+lib.phx_kappa_qhgk.restype = C.c_int
 lib.phx_gamma_cell.argtypes = [_P, _P, _P, _P, C.c_double, Broadening, C.c_double, _I, _P, _I, _P]
 lib.phx_gamma_cell.restype = C.c_int
 lib.phx_unfold.argtypes = [_P, _I, _I, _I, _P, _P, _P, _P, _P, _I, _P]
@@ -125,7 +127,7 @@ KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4
            "eig_vectors": 11, "eig_back": 12, "eig_bisect": 13}
 
 EXPORTED = ["phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
-            "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_isotope", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta",
+            "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_isotope", "phx_kappa_qhgk", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta",
             "phx_kappa_rta_noalloc", "phx_gamma_batched", "phx_features", "phx_mlp_create", "phx_mlp_destroy",
             "phx_mlp_num_params", "phx_mlp_get_params", "phx_mlp_set_params", "phx_mlp_loss_grad", "phx_mlp_train",
             "phx_mlp_predict"]
@@ -431,6 +433,26 @@ class Context:
                                    _ptr(freq_full), _ptr(irr_q), _ptr(gamma_irr), _ptr(full_to_irr), _ptr(out),
                                    mem, stream))
         return out
+
+    def kappa_qhgk(self, lattice, masses, positions, ifc2_idx, ifc2_val, freq, evec, gamma, temperature,
+                   f_min=0.01):
+        """phx_kappa_qhgk: Gamma-only QHGK conductivity (3 x 3, W/(m K)) of a cell; freq [n],
+        evec [n, n] complex with zero imaginary parts, gamma [n] (numpy or CUDA tensors)."""
+        cell, m = make_cell(lattice, masses)
+        pos = _host(positions, np.float64).reshape(-1, 3)
+        cell.positions = pos.ctypes.data
+        bi = _host(ifc2_idx, np.int32)
+        bv = _host(ifc2_val, np.float64)
+        f2 = Ifc2(bi.shape[0], bi.ctypes.data, bv.ctypes.data)
+        if not _is_torch(freq):
+            freq = _host(freq, np.float64).reshape(-1)
+            evec = _host(evec, np.complex128)
+            gamma = _host(gamma, np.float64).reshape(-1)
+        mem, stream = _mem_and_stream([freq, evec, gamma])
+        k = np.zeros(9)
+        self._check(lib.phx_kappa_qhgk(self.h, C.byref(cell), C.byref(f2), _ptr(freq), _ptr(evec), _ptr(gamma),
+                                       float(temperature), float(f_min), k.ctypes.data, mem, stream))
+        return k.reshape(3, 3)
 
     def kappa_rta(self, lattice, masses, freq, gamma_full, temperature, vel=None, vv=None, f_min=0.01,
                   is_classic=False):

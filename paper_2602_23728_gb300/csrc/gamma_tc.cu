@@ -15,11 +15,12 @@
 // so D = A B^T holds [Re | Im] of the complex product.  Precisions: BF16x3 (x = hi + lo in
 // bf16, product hi*hi + hi*lo + lo*hi, FP32 accumulate in tensor memory) or TF32 (one pass).
 //
-// GEMM kernel: one CTA = 6 warps.  Warp 0 issues TMA loads of 128-row x 128-byte A chunks
-// (128B swizzle) into a ring of stages; warp 1 owns tensor memory and issues tcgen05.mma
-// (M = 128, N = the whole padded output width) into one of two accumulators; warps 2-5 read
-// the accumulator back with tcgen05.ld and run the fused epilogue while the next tile
-// accumulates.  The B operand of a problem (<= 150 KB) stays resident in shared memory.
+// GEMM kernel: warp 0 issues TMA loads of 128-row x 128-byte A chunks (128B swizzle) into a
+// ring of stages; warp 1 owns tensor memory and issues tcgen05.mma (M = 128, N = the padded
+// output width of a column group) into one of two accumulators; the epilogue warps (24 / 16
+// for the operand-writing GEMMs, 8 for the weighting GEMM) read the accumulator back with
+// tcgen05.ld while the next tile accumulates.  The B operand of a problem stays resident in
+// shared memory when it fits, else it is streamed with A.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -34,8 +35,11 @@
 
 namespace {
 
-constexpr int kEpiThreads = 256;                // 8 epilogue warps, two per TMEM lane group
-constexpr int kThreads = 64 + kEpiThreads;
+// Epilogue warps (a multiple of 4: the TMEM lane group of a warp is its index mod 4), as
+// measured best per mode: the Fourier GEMM's operand stores 24, the e_q'' GEMM 16, the
+// register-heavy weighting epilogues EPI_G / EPI_GT 8.
+template <int EPI> constexpr int epi_warps() { return EPI == 0 ? 24 : EPI == 1 ? 16 : 8; }
+template <int EPI> constexpr int kernel_threads() { return 64 + 32 * epi_warps<EPI>(); }
 constexpr int kMaxStages = 8;
 constexpr int kBoxRows = 128;                  // rows of an A tile (= MMA M)
 constexpr int kChunkBytes = 128;               // bytes of K per chunk (one swizzle row)
@@ -98,10 +102,12 @@ __device__ __forceinline__ void store_operand(void* hi, void* lo, int64_t idx, f
     }
 }
 
-__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_barrier(int threads) { asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory"); }
 
 template <int PREC, int EPI, bool kStreamB>
-__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcArgs args) {
+__global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const __grid_constant__ TcArgs args) {
+    constexpr int kEpiThreads = 32 * epi_warps<EPI>();
+    constexpr int kEpiParts = epi_warps<EPI>() / 4;          // warps per TMEM lane group
     constexpr int kPlanes = (PREC == P_BF16X3) ? 2 : 1;
     constexpr uint32_t kFmt = (PREC == P_BF16X3) ? 1u : 2u;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -279,11 +285,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
     } else {
         // ------------------------------------------------------------ epilogue (warps 2..9)
-        // Two warps per tensor-memory lane group; warp half h handles the 16-column chunks
-        // with (chunk index % 2) == h.
+        // kEpiParts warps per tensor-memory lane group; warp part h handles the 16-column
+        // chunks with (chunk index % kEpiParts) == h.
         const int et = threadIdx.x - 64;                  // 0..255
         const int lgrp = warp & 3;                        // tensor-memory lane group of this warp
-        const int half = (warp - 2) >> 2;
+        const int half = (warp - 2) >> 2;                 // part index (0 .. kEpiParts - 1)
+        constexpr int kStride = 16 * kEpiParts;
         int q1 = 0, q2 = 0, cur_p = -1;
         int acc = 0;
         uint32_t acc_phase = 0;
@@ -295,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 abort_flag = 1;
                 atomicExch(args.status, (int)PHX_ERR_TIMEOUT);
             }
-            epi_barrier();                 // every epilogue thread takes the same decision
+            epi_barrier(kEpiThreads);      // every epilogue thread takes the same decision
             if (abort_flag) break;
             if ((EPI == EPI_G || EPI == EPI_GT) && p != cur_p) {
                 // partner tables of this problem's q' (the previous tile is done: barrier above)
@@ -312,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                             s_n1t[t * kMaxNp + j] =
                                 (v && t < args.n_t) ? (float)args.nB[t * args.nb_stride + (int64_t)q1 * args.n + j] : 0.0f;
                 }
-                epi_barrier();
+                epi_barrier(kEpiThreads);
                 cur_p = p;
             }
             tc::tc_fence_after();
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             if (EPI == EPI_M) {
                 // row (nu, b, c) of W -> M_slot[(nu, b)][c] (re) and [(nu, b)][Kcp + c] (im)
                 const int nb = row / args.n, c = row % args.n;
-                for (int j0 = half * 16; j0 < NA; j0 += 32) {
+                for (int j0 = half * 16; j0 < NA; j0 += kStride) {
                     tc::tmem_ld16(taddr + j0, v);
                     if (valid) {
 #pragma unroll
@@ -341,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 // row (nu, b) -> X[(nu, nu'')][b] (re) and [(nu, nu'')][Kcp + b] (im)
                 const int nu = row / args.n, b = row % args.n;
                 const int64_t base = (int64_t)p * args.out_rows_per_slot + (int64_t)nu * args.n;
-                for (int j0 = half * 16; j0 < NA; j0 += 32) {
+                for (int j0 = half * 16; j0 < NA; j0 += kStride) {
                     tc::tmem_ld16(taddr + j0, v);
                     if (valid) {
 #pragma unroll
@@ -378,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 #pragma unroll
                 for (int t = 0; t < kMaxT; ++t) gs[t] = 0.f;
                 float vi[16];
-                for (int j0 = half * 16; j0 < mg; j0 += 32) {
+                for (int j0 = half * 16; j0 < mg; j0 += kStride) {
                     tc::tmem_ld16(taddr + j0, v);
                     tc::tmem_ld16(taddr + mg + j0, vi);
 #pragma unroll
@@ -429,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 float vi[16];
                 if (args.shape == PHX_GAUSS) {
                     const float a = -1.f / (args.sigma * args.sigma), norm = 0.56418958354775628f / args.sigma;
-                    for (int j0 = half * 16; j0 < mg; j0 += 32) {
+                    for (int j0 = half * 16; j0 < mg; j0 += kStride) {
                         tc::tmem_ld16(taddr + j0, v);
                         tc::tmem_ld16(taddr + mg + j0, vi);
 #pragma unroll
@@ -448,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                     ws *= norm;
                 } else {
                     const float h = 0.5f * args.sigma, h2 = h * h, norm = h / 3.14159265358979f;
-                    for (int j0 = half * 16; j0 < mg; j0 += 32) {
+                    for (int j0 = half * 16; j0 < mg; j0 += kStride) {
                         tc::tmem_ld16(taddr + j0, v);
                         tc::tmem_ld16(taddr + mg + j0, vi);
 #pragma unroll
@@ -681,7 +688,7 @@ cudaError_t launch_gemm(phx_ctx* ctx, TcArgs& a, int n_problems, int ctas, cudaS
     a.n_problems = n_problems;
     const int64_t items = (int64_t)n_problems * a.tiles * a.n_groups;
     dim3 grid((unsigned)std::min<int64_t>(items, ctas), 1);
-    tc_gemm_kernel<PREC, EPI, STREAM><<<grid, kThreads, smem, s>>>(a);
+    tc_gemm_kernel<PREC, EPI, STREAM><<<grid, kernel_threads<EPI>(), smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,8 @@
 //                   round-robin ordering (n/2 disjoint rotations per step applied as one
 //                   left and one right multiplication); matrix in shared memory when it fits
 //  velocity_kernel  v_a = Re<e|dD/dq_a|e>/(2w) and the basis-invariant v(x)v per degenerate set
+#include <cstdlib>
+
 #include "common.h"
 
 namespace {
@@ -234,6 +236,259 @@ jacobi_kernel(double2* __restrict__ Ag, double2* __restrict__ Vg, int n, double*
     }
 }
 
+// Batched complex-Hermitian eigensolver for n <= kHhqlMaxModes, one CTA per matrix, the
+// matrix in shared memory:
+//  1. Householder reduction to tridiagonal form, H_k = I - beta v v^H with v = x + e^{i phi}|x| e1
+//     (x = column k below the diagonal, phi = arg x_0), rank-2 update A22 -= v w^H + w v^H with
+//     w = p - (beta v^H p / 2) v, p = beta A22 v; v stays in column k
+//  2. the complex subdiagonal made real by the diagonal phases delta_{k+1} = delta_k e_k/|e_k|
+//  3. implicit QL with Wilkinson shifts on the real tridiagonal (thread 0 forms the rotations of
+//     a sweep, every thread applies them to its row of Z)
+//  4. back-transformation E = H_0 ... H_{n-3} diag(delta) Z, then the Jacobi solver's output
+//     conventions: ascending order, largest-modulus component real and positive.
+// About 15 n^3 real flops per matrix against ~200 n^3 for the cyclic Jacobi sweeps.
+constexpr int kHhqlMaxModes = 96;
+constexpr int kQlMaxIter = 60;
+
+__global__ void __launch_bounds__(256)
+hhql_kernel(const double2* __restrict__ Dg, double* __restrict__ Zg, double2* __restrict__ Eg, int n,
+            double* __restrict__ freq, double2* __restrict__ evec, int32_t* __restrict__ status) {
+    extern __shared__ double2 A[];                           // n x n, row-major
+    __shared__ double d[kHhqlMaxModes], e[kHhqlMaxModes], bet[kHhqlMaxModes], rc[kHhqlMaxModes],
+        rs[kHhqlMaxModes], red[32];
+    __shared__ double2 ph[kHhqlMaxModes];
+    __shared__ int rank_of[kHhqlMaxModes];
+    __shared__ int sweep_lo, sweep_hi, sweep_fail;
+    const int qi = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int64_t nn = (int64_t)n * n;
+    const double2* Dq = Dg + (int64_t)qi * nn;
+    double* Z = Zg + (int64_t)qi * nn * 2;                  // real n x n, column-major Z[col * n + row]
+    double2* E = Eg + (int64_t)qi * nn;                      // complex n x n, row-major
+    // Hermitian part (D + D^H)/2 (the two triangles differ at the rounding level)
+    for (int64_t t = tid; t < nn; t += nt) {
+        const int i = (int)(t / n), j = (int)(t % n);
+        const double2 a = Dq[(int64_t)i * n + j], b = Dq[(int64_t)j * n + i];
+        A[t] = make_double2(0.5 * (a.x + b.x), i == j ? 0.0 : 0.5 * (a.y - b.y));
+    }
+    __syncthreads();
+    // ---- 1. Householder
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        double s2 = 0.0;
+        for (int i = 1 + tid; i < m; i += nt) { const double2 x = A[(k + 1 + i) * n + k]; s2 += x.x * x.x + x.y * x.y; }
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0) red[warp] = s2;
+        __syncthreads();
+        double tail = 0.0;
+        for (int w = 0; w < nw; ++w) tail += red[w];
+        const double2 x0 = A[(k + 1) * n + k];
+        const double a0 = hypot(x0.x, x0.y);
+        double beta = 0.0;
+        double2 alpha = x0, v0 = make_double2(0.0, 0.0);
+        if (tail > 0.0) {
+            const double nrm = sqrt(a0 * a0 + tail);
+            const double2 u = a0 > 0.0 ? make_double2(x0.x / a0, x0.y / a0) : make_double2(1.0, 0.0);
+            alpha = make_double2(-u.x * nrm, -u.y * nrm);
+            v0 = make_double2(x0.x + u.x * nrm, x0.y + u.y * nrm);
+            beta = 2.0 / (v0.x * v0.x + v0.y * v0.y + tail);
+        }
+        __syncthreads();                                     // all read x0 before it is replaced
+        if (tid == 0) {
+            e[k] = 0.0;
+            ph[k] = alpha;                                   // complex subdiagonal, made real below
+            bet[k] = beta;
+            A[(k + 1) * n + k] = v0;                         // v_0; v_i (i >= 1) = x_i in place
+        }
+        __syncthreads();
+        if (beta != 0.0) {
+            // p = beta A22 v (one warp per row), stored in row k (columns k+1..) as scratch
+            for (int r = warp; r < m; r += nw) {
+                double2 acc = make_double2(0.0, 0.0);
+                for (int c = lane; c < m; c += 32) {
+                    const double2 a = A[(k + 1 + r) * n + k + 1 + c], v = A[(k + 1 + c) * n + k];
+                    acc.x += a.x * v.x - a.y * v.y;
+                    acc.y += a.x * v.y + a.y * v.x;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+                }
+                if (lane == 0) A[k * n + k + 1 + r] = make_double2(beta * acc.x, beta * acc.y);
+            }
+            __syncthreads();
+            // K = beta/2 v^H p (real for Hermitian A22)
+            double kr = 0.0;
+            for (int c = tid; c < m; c += nt) {
+                const double2 v = A[(k + 1 + c) * n + k], p = A[k * n + k + 1 + c];
+                kr += v.x * p.x + v.y * p.y;
+            }
+            for (int o = 16; o > 0; o >>= 1) kr += __shfl_xor_sync(0xffffffffu, kr, o);
+            if (lane == 0) red[warp] = kr;
+            __syncthreads();
+            double K = 0.0;
+            for (int w = 0; w < nw; ++w) K += red[w];
+            K *= 0.5 * beta;
+            // w = p - K v (in row k), then A22 -= v w^H + w v^H
+            __syncthreads();
+            for (int c = tid; c < m; c += nt) {
+                const double2 v = A[(k + 1 + c) * n + k], p = A[k * n + k + 1 + c];
+                A[k * n + k + 1 + c] = make_double2(p.x - K * v.x, p.y - K * v.y);
+            }
+            __syncthreads();
+            for (int t = tid; t < m * m; t += nt) {
+                const int r = t / m, c = t % m;
+                const double2 vr = A[(k + 1 + r) * n + k], vc = A[(k + 1 + c) * n + k];
+                const double2 wr = A[k * n + k + 1 + r], wc = A[k * n + k + 1 + c];
+                // v_r conj(w_c) + w_r conj(v_c)
+                const double re = vr.x * wc.x + vr.y * wc.y + wr.x * vc.x + wr.y * vc.y;
+                const double im = vr.y * wc.x - vr.x * wc.y + wr.y * vc.x - wr.x * vc.y;
+                double2& a = A[(k + 1 + r) * n + k + 1 + c];
+                a.x -= re;
+                a.y -= im;
+            }
+            __syncthreads();
+        }
+    }
+    // ---- 2. real tridiagonal: d, |e|, phases delta
+    if (tid == 0) {
+        for (int k = 0; k < n; ++k) d[k] = A[k * n + k].x;
+        if (n >= 2) ph[n - 2] = A[(n - 1) * n + n - 2];      // last subdiagonal (no reflector)
+        double2 dl = make_double2(1.0, 0.0);
+        for (int k = 0; k + 1 < n; ++k) {
+            const double2 a = ph[k];
+            const double m = hypot(a.x, a.y);
+            e[k] = m;
+            const double2 u = m > 0.0 ? make_double2(a.x / m, a.y / m) : make_double2(1.0, 0.0);
+            ph[k] = dl;                                      // delta_k
+            dl = make_double2(dl.x * u.x - dl.y * u.y, dl.x * u.y + dl.y * u.x);
+        }
+        ph[n - 1] = dl;
+        if (n >= 1) e[n - 1] = 0.0;
+        sweep_fail = 0;
+    }
+    for (int64_t t = tid; t < nn; t += nt) Z[t] = (t / n == t % n) ? 1.0 : 0.0;
+    __syncthreads();
+    // ---- 3. implicit QL (tql2): thread 0 forms the rotations, all threads apply them
+    for (int l = 0; l < n; ++l) {
+        for (int iter = 0; iter <= kQlMaxIter; ++iter) {
+            if (tid == 0) {
+                int m = l;
+                for (; m < n - 1; ++m) {
+                    const double dd = fabs(d[m]) + fabs(d[m + 1]);
+                    if (fabs(e[m]) <= 2.2204460492503131e-16 * dd) break;
+                }
+                sweep_lo = l;
+                sweep_hi = m;
+                if (m != l) {
+                    if (iter == kQlMaxIter) { sweep_fail = 1; sweep_hi = l; }
+                    else {
+                        double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+                        double r = hypot(g, 1.0);
+                        g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+                        double sn = 1.0, cs = 1.0, p = 0.0;
+                        int i = m - 1;
+                        bool underflow = false;
+                        for (; i >= l; --i) {
+                            double f = sn * e[i], b = cs * e[i];
+                            r = hypot(f, g);
+                            e[i + 1] = r;
+                            if (r == 0.0) { d[i + 1] -= p; e[m] = 0.0; underflow = true; break; }
+                            sn = f / r;
+                            cs = g / r;
+                            g = d[i + 1] - p;
+                            r = (d[i] - g) * sn + 2.0 * cs * b;
+                            p = sn * r;
+                            d[i + 1] = g + p;
+                            g = cs * r - b;
+                            rc[i] = cs;
+                            rs[i] = sn;
+                        }
+                        if (underflow) {
+                            sweep_lo = i + 1;                  // rotations i+1 .. m-1 were formed
+                        } else {
+                            d[l] -= p;
+                            e[l] = g;
+                            e[m] = 0.0;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            const int lo = sweep_lo, hi = sweep_hi;
+            if (hi == l && lo == l) break;                       // converged (or gave up)
+            // apply rotations i = hi-1 down to lo to every row of Z (columns i, i+1)
+            for (int row = tid; row < n; row += nt) {
+                for (int i = hi - 1; i >= lo; --i) {
+                    const double c = rc[i], sg = rs[i];
+                    const double f = Z[(int64_t)(i + 1) * n + row], zi = Z[(int64_t)i * n + row];
+                    Z[(int64_t)(i + 1) * n + row] = sg * zi + c * f;
+                    Z[(int64_t)i * n + row] = c * zi - sg * f;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0 && sweep_fail) atomicExch(status, (int)PHX_ERR_NUMERIC);
+    // ---- 4. E = H_0 ... H_{n-3} diag(delta) Z  (thread per column j)
+    for (int j = tid; j < n; j += nt) {
+        for (int i = 0; i < n; ++i) {
+            const double z = Z[(int64_t)j * n + i];
+            E[(int64_t)i * n + j] = make_double2(ph[i].x * z, ph[i].y * z);
+        }
+        for (int k = n - 3; k >= 0; --k) {
+            const double beta = bet[k];
+            if (beta == 0.0) continue;
+            const int m = n - k - 1;
+            double2 s = make_double2(0.0, 0.0);
+            for (int i = 0; i < m; ++i) {
+                const double2 v = A[(k + 1 + i) * n + k], x = E[(int64_t)(k + 1 + i) * n + j];
+                s.x += v.x * x.x + v.y * x.y;                    // conj(v) x
+                s.y += v.x * x.y - v.y * x.x;
+            }
+            s.x *= beta;
+            s.y *= beta;
+            for (int i = 0; i < m; ++i) {
+                const double2 v = A[(k + 1 + i) * n + k];
+                double2& x = E[(int64_t)(k + 1 + i) * n + j];
+                x.x -= v.x * s.x - v.y * s.y;
+                x.y -= v.x * s.y + v.y * s.x;
+            }
+        }
+    }
+    __syncthreads();
+    // ---- ranks, frequencies, gauge
+    for (int i = tid; i < n; i += nt) {
+        int r = 0;
+        const double li = d[i];
+        for (int j = 0; j < n; ++j) r += (d[j] < li) || (d[j] == li && j < i);
+        rank_of[i] = r;
+        const double w2 = li * phx::kEvA2AmuToPs2;
+        freq[(int64_t)qi * n + r] = (w2 >= 0.0 ? sqrt(w2) : -sqrt(-w2)) / phx::kTwoPi;
+    }
+    __syncthreads();
+    for (int col = warp; col < n; col += nw) {
+        double best = -1.0;
+        int bi = 0;
+        for (int i = lane; i < n; i += 32) {
+            const double2 v = E[(int64_t)i * n + col];
+            const double a = v.x * v.x + v.y * v.y;
+            if (a > best) { best = a; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        const double2 vm = E[(int64_t)bi * n + col];
+        const double h = hypot(vm.x, vm.y);
+        const double2 g = h > 0.0 ? make_double2(vm.x / h, -vm.y / h) : make_double2(1.0, 0.0);
+        const int dst = rank_of[col];
+        for (int i = lane; i < n; i += 32)
+            evec[(int64_t)qi * nn + (int64_t)i * n + dst] = cmul(E[(int64_t)i * n + col], g);
+    }
+}
+
 // One CTA per q.  Y[q][a] = dD_a(q) E(q) (complex), E sorted by frequency.
 __global__ void velocity_kernel(const double2* __restrict__ E, const double2* __restrict__ Y,
                                 const double* __restrict__ freq, int n, double* __restrict__ vel,
@@ -320,6 +575,13 @@ cudaError_t phx_launch_jacobi(double* A, double* V, int n, int nq, double* freq,
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (n <= kHhqlMaxModes && !std::getenv("PHX_EIG_JACOBI")) {
+        // Householder + QL; Z (real) lives in A's buffer, the back-transformed vectors in V's
+        cudaError_t e = cudaFuncSetAttribute(hhql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        hhql_kernel<<<nq, 256, smem, s>>>((const double2*)A, A, (double2*)V, n, freq, (double2*)evec, status);
+        return cudaGetLastError();
+    }
     const size_t static_bytes = 8 * 1024;     // rotation tables etc. (upper bound)
     if (smem + static_bytes <= (size_t)optin) {
         cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

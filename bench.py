@@ -29,6 +29,11 @@ sys.path.insert(0, ROOT)
 METRIC = "phonon triplets/s (V3+gamma) on 1 GB300, mixed/batched vs FP64 path, at stated kappa error"
 UNIT = "triplets/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu capture summarised in
+# profiles/tc_gemm_fcc32_mesh8.md (same per-launch shape as the bench); valid for the kernel
+# source it was taken on
+DRAM_TRAFFIC_PER_LAUNCH = {("dft", "bf16x3"): 226.68e6 + 426.45e6, ("gemm_e2", "bf16x3"): 500.43e6 + 433.85e6,
+                           ("gemm_e1_gamma", "bf16x3"): 499.97e6 + 3.29e6}
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
 
 
@@ -341,7 +346,8 @@ def run_phx(args):
     e2e_ms, _ = reduce_over_ranks(e2e_ms, trip, world, dist, device)
     h2d, d2h = wl.host_bytes(bufs)
 
-    # roofline of the dominant kernel class, from events recorded around its launches
+    # roofline of the dominant kernel class, from events recorded around its launches; the
+    # bound follows from its algorithmic intensity against the measured ridge point
     peaks, src = load_peaks()
     gemms = {k: prof[k] for k in ("dft", "gemm_e2", "gemm_e1_gamma", "fp64_gemm") if prof[k][1] > 0}
     roof = None
@@ -355,12 +361,24 @@ def run_phx(args):
             peak, note = bf16_sus * NOMINAL_TF32_OVER_BF16, "bf16 sustained x nominal tf32/bf16 (1.1/2.25)"
         else:
             peak, note = None, "FP64 CUDA-core path"
-        achieved = fl / (tot_ms / 1e3) / 1e12
-        roof = {"bound": "tensor", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if peak else None, "traffic": None,
-                "launches_per_step": nl / args.steps, "avg_launch_ms": tot_ms / nl,
-                "peak_source": f"{src}: {note}",
-                "share_of_step": tot_ms / args.steps / ms}
+        ridge = peak * 1e12 / (peaks["hbm_gbs"] * 1e9) if peak else None      # flop per byte
+        intensity = fl / by if by > 0 else None
+        t = tot_ms / 1e3
+        traffic = DRAM_TRAFFIC_PER_LAUNCH.get((name, args.precision))
+        if ridge is not None and intensity is not None and intensity < ridge:
+            achieved = by / t / 1e9
+            roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                    "peak_source": f"{src}: copy bandwidth", "tensor_frac": fl / t / 1e12 / peak}
+        else:
+            achieved = fl / t / 1e12
+            roof = {"bound": "tensor", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": (achieved / peak) if peak else None, "traffic": traffic,
+                    "peak_source": f"{src}: {note}"}
+        roof.update({"algorithmic_bytes_per_launch": by / nl, "algorithmic_flops_per_launch": fl / nl,
+                     "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
+                     "launches_per_step": nl / args.steps, "avg_launch_ms": tot_ms / nl,
+                     "share_of_step": tot_ms / args.steps / ms})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",

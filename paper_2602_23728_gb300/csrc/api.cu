@@ -386,17 +386,18 @@ phx_status phx_harmonic(phx_ctx* ctx, const phx_cell* cell, const phx_ifc2* fc2,
     const int64_t per_q = n2 * 16 * (want_v ? 8 : 2);
     const int chunk = large ? 0 : (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)nq, ((int64_t)1 << 30) / per_q, (int64_t)16384}));
     double* D = large ? nullptr : (double*)phx_ws(ctx, "h.D", (size_t)chunk * n2 * 16);
+    double* hsc = large ? nullptr : (double*)phx_ws(ctx, "h.hsc", (size_t)chunk * n * 4 * 8);
     double* Vw = large ? nullptr : (double*)phx_ws(ctx, "h.V", (size_t)chunk * n2 * 16);
     double* dD = want_v ? (double*)phx_ws(ctx, "h.dD", (size_t)chunk * 3 * n2 * 16) : nullptr;
     double* Y = want_v ? (double*)phx_ws(ctx, "h.Y", (size_t)chunk * 3 * n2 * 16) : nullptr;
-    if (!large && (!D || !Vw || (want_v && (!dD || !Y)))) return PHX_ERR_NOMEM;
+    if (!large && (!D || !Vw || !hsc || (want_v && (!dD || !Y)))) return PHX_ERR_NOMEM;
     if (!large) PHX_CUDA_CHECK(ctx, cudaMemsetAsync(ctx->status_word, 0, 4, s));
     for (int q0 = 0; !large && q0 < nq; q0 += chunk) {
         const int c = std::min(chunk, nq - q0);
         PHX_CUDA_CHECK(ctx, phx_launch_dynmat(dq + 3 * q0, c, na, d_idx, d_val, d_ps, d_m, d_lat, D, dD, s));
         const int ps = phx_prof_begin(ctx, s);
         PHX_CUDA_CHECK(ctx, phx_launch_jacobi(D, Vw, n, c, o_f + (int64_t)q0 * n, o_e + (int64_t)q0 * n2 * 2,
-                                              (int32_t*)ctx->status_word, s));
+                                              (int32_t*)ctx->status_word, s, hsc));
         phx_prof_end(ctx, ps, s, PHX_K_EIGEN, 0.0, 0.0);
         ctx->launches += 2;
         if (want_v) {

@@ -145,8 +145,9 @@ static inline phx_status phx_stage_out_buf(phx_ctx* ctx, const char* name, T* p,
 cudaError_t phx_launch_dynmat(const double* q_frac, int nq, int n_atoms, const int32_t* blk_idx,
                               const double* blk_val, const int32_t* pair_start, const double* masses,
                               const double* lattice, double* D, double* dD, cudaStream_t s);
+// scratch: 4 n doubles per matrix (Householder path for n <= 96; nullptr selects Jacobi)
 cudaError_t phx_launch_jacobi(double* A, double* V, int n, int nq, double* freq, double* evec,
-                              int32_t* status, cudaStream_t s);
+                              int32_t* status, cudaStream_t s, double* scratch = nullptr);
 cudaError_t phx_launch_velocity(const double* evec, const double* Y, const double* freq, int n,
                                 int nq, double* vel, double* vv, cudaStream_t s);
 // eigh_large.cu: Gamma point of a cell with more than 64 atoms (device pair CSR in, device out)

@@ -236,43 +236,41 @@ jacobi_kernel(double2* __restrict__ Ag, double2* __restrict__ Vg, int n, double*
     }
 }
 
-// Batched complex-Hermitian eigensolver for n <= kHhqlMaxModes, one CTA per matrix, the
-// matrix in shared memory:
-//  1. Householder reduction to tridiagonal form, H_k = I - beta v v^H with v = x + e^{i phi}|x| e1
-//     (x = column k below the diagonal, phi = arg x_0), rank-2 update A22 -= v w^H + w v^H with
-//     w = p - (beta v^H p / 2) v, p = beta A22 v; v stays in column k
-//  2. the complex subdiagonal made real by the diagonal phases delta_{k+1} = delta_k e_k/|e_k|
-//  3. implicit QL with Wilkinson shifts on the real tridiagonal (thread 0 forms the rotations of
-//     a sweep, every thread applies them to its row of Z)
-//  4. back-transformation E = H_0 ... H_{n-3} diag(delta) Z, then the Jacobi solver's output
-//     conventions: ascending order, largest-modulus component real and positive.
+// Batched complex-Hermitian eigensolver for n <= kHhqlMaxModes in two kernels:
+//  hh_reduce_kernel  (one CTA per matrix, the matrix in shared memory) Householder reduction
+//     to tridiagonal form, H_k = I - beta v v^H with v = x + e^{i phi}|x| e1 (x = column k below
+//     the diagonal, phi = arg x_0), rank-2 update A22 -= v w^H + w v^H with
+//     w = p - (beta v^H p / 2) v, p = beta A22 v.  Writes the reflectors (row k of R holds v_k),
+//     beta, the diagonal and the complex subdiagonal.
+//  ql_back_kernel    (one small CTA per matrix, many per SM so their serial parts overlap) the
+//     subdiagonal made real by the phases delta_{k+1} = delta_k e_k/|e_k|, implicit QL with
+//     Wilkinson shifts (thread 0 forms a sweep's rotations, every thread applies them to its
+//     row of Z), eigenvalue ranks, back-transformation E = H_0 ... H_{n-3} diag(delta) Z written
+//     straight into the sorted output column, then the gauge (largest-modulus component real
+//     and positive, as the Jacobi solver).
 // About 15 n^3 real flops per matrix against ~200 n^3 for the cyclic Jacobi sweeps.
 constexpr int kHhqlMaxModes = 96;
 constexpr int kQlMaxIter = 60;
+constexpr int kQlThreads = 128;
 
+// per-matrix scratch (doubles): d[n], e re/im [2n], beta[n]
 __global__ void __launch_bounds__(256)
-hhql_kernel(const double2* __restrict__ Dg, double* __restrict__ Zg, double2* __restrict__ Eg, int n,
-            double* __restrict__ freq, double2* __restrict__ evec, int32_t* __restrict__ status) {
+hh_reduce_kernel(const double2* __restrict__ Dg, double2* __restrict__ Rg, double* __restrict__ scratch, int n) {
     extern __shared__ double2 A[];                           // n x n, row-major
-    __shared__ double d[kHhqlMaxModes], e[kHhqlMaxModes], bet[kHhqlMaxModes], rc[kHhqlMaxModes],
-        rs[kHhqlMaxModes], red[32];
-    __shared__ double2 ph[kHhqlMaxModes];
-    __shared__ int rank_of[kHhqlMaxModes];
-    __shared__ int sweep_lo, sweep_hi, sweep_fail;
+    __shared__ double red[32];
     const int qi = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int64_t nn = (int64_t)n * n;
     const double2* Dq = Dg + (int64_t)qi * nn;
-    double* Z = Zg + (int64_t)qi * nn * 2;                  // real n x n, column-major Z[col * n + row]
-    double2* E = Eg + (int64_t)qi * nn;                      // complex n x n, row-major
-    // Hermitian part (D + D^H)/2 (the two triangles differ at the rounding level)
+    double2* R = Rg + (int64_t)qi * nn;
+    double* sc = scratch + (int64_t)qi * 4 * n;
+    double *sd = sc, *se = sc + n, *sb = sc + 3 * n;
     for (int64_t t = tid; t < nn; t += nt) {
         const int i = (int)(t / n), j = (int)(t % n);
         const double2 a = Dq[(int64_t)i * n + j], b = Dq[(int64_t)j * n + i];
         A[t] = make_double2(0.5 * (a.x + b.x), i == j ? 0.0 : 0.5 * (a.y - b.y));
     }
     __syncthreads();
-    // ---- 1. Householder
     for (int k = 0; k + 2 < n; ++k) {
         const int m = n - k - 1;
         double s2 = 0.0;
@@ -295,14 +293,15 @@ hhql_kernel(const double2* __restrict__ Dg, double* __restrict__ Zg, double2* __
         }
         __syncthreads();                                     // all read x0 before it is replaced
         if (tid == 0) {
-            e[k] = 0.0;
-            ph[k] = alpha;                                   // complex subdiagonal, made real below
-            bet[k] = beta;
+            se[2 * k] = alpha.x;
+            se[2 * k + 1] = alpha.y;
+            sb[k] = beta;
             A[(k + 1) * n + k] = v0;                         // v_0; v_i (i >= 1) = x_i in place
         }
         __syncthreads();
+        for (int i = tid; i < m; i += nt) R[(int64_t)k * n + i] = A[(k + 1 + i) * n + k];
         if (beta != 0.0) {
-            // p = beta A22 v (one warp per row), stored in row k (columns k+1..) as scratch
+            // p = beta A22 v (one warp per row), kept in row k (columns k+1..) as scratch
             for (int r = warp; r < m; r += nw) {
                 double2 acc = make_double2(0.0, 0.0);
                 for (int c = lane; c < m; c += 32) {
@@ -317,8 +316,7 @@ hhql_kernel(const double2* __restrict__ Dg, double* __restrict__ Zg, double2* __
                 if (lane == 0) A[k * n + k + 1 + r] = make_double2(beta * acc.x, beta * acc.y);
             }
             __syncthreads();
-            // K = beta/2 v^H p (real for Hermitian A22)
-            double kr = 0.0;
+            double kr = 0.0;                                 // K = beta/2 v^H p (real)
             for (int c = tid; c < m; c += nt) {
                 const double2 v = A[(k + 1 + c) * n + k], p = A[k * n + k + 1 + c];
                 kr += v.x * p.x + v.y * p.y;
@@ -329,18 +327,16 @@ hhql_kernel(const double2* __restrict__ Dg, double* __restrict__ Zg, double2* __
             double K = 0.0;
             for (int w = 0; w < nw; ++w) K += red[w];
             K *= 0.5 * beta;
-            // w = p - K v (in row k), then A22 -= v w^H + w v^H
             __syncthreads();
-            for (int c = tid; c < m; c += nt) {
+            for (int c = tid; c < m; c += nt) {              // w = p - K v
                 const double2 v = A[(k + 1 + c) * n + k], p = A[k * n + k + 1 + c];
                 A[k * n + k + 1 + c] = make_double2(p.x - K * v.x, p.y - K * v.y);
             }
             __syncthreads();
-            for (int t = tid; t < m * m; t += nt) {
+            for (int t = tid; t < m * m; t += nt) {          // A22 -= v w^H + w v^H
                 const int r = t / m, c = t % m;
                 const double2 vr = A[(k + 1 + r) * n + k], vc = A[(k + 1 + c) * n + k];
                 const double2 wr = A[k * n + k + 1 + r], wc = A[k * n + k + 1 + c];
-                // v_r conj(w_c) + w_r conj(v_c)
                 const double re = vr.x * wc.x + vr.y * wc.y + wr.x * vc.x + wr.y * vc.y;
                 const double im = vr.y * wc.x - vr.x * wc.y + wr.y * vc.x - wr.x * vc.y;
                 double2& a = A[(k + 1 + r) * n + k + 1 + c];
@@ -350,13 +346,34 @@ hhql_kernel(const double2* __restrict__ Dg, double* __restrict__ Zg, double2* __
             __syncthreads();
         }
     }
-    // ---- 2. real tridiagonal: d, |e|, phases delta
+    for (int k = tid; k < n; k += nt) sd[k] = A[k * n + k].x;
+    if (tid == 0 && n >= 2) {                                // last subdiagonal (no reflector)
+        const double2 a = A[(n - 1) * n + n - 2];
+        se[2 * (n - 2)] = a.x;
+        se[2 * (n - 2) + 1] = a.y;
+        sb[n - 2] = 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(kQlThreads)
+ql_back_kernel(const double2* __restrict__ Rg, const double* __restrict__ scratch, double* __restrict__ Zg, int n,
+               double* __restrict__ freq, double2* __restrict__ evec, int32_t* __restrict__ status) {
+    __shared__ double d[kHhqlMaxModes], e[kHhqlMaxModes], rc[kHhqlMaxModes], rs[kHhqlMaxModes];
+    __shared__ double2 ph[kHhqlMaxModes];
+    __shared__ int rank_of[kHhqlMaxModes];
+    __shared__ int sweep_lo, sweep_hi, sweep_fail;
+    const int qi = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int64_t nn = (int64_t)n * n;
+    const double2* R = Rg + (int64_t)qi * nn;
+    const double* sc = scratch + (int64_t)qi * 4 * n;
+    double* Z = Zg + (int64_t)qi * nn * 2;                  // real n x n, column-major
+    double2* Eo = evec + (int64_t)qi * nn;
     if (tid == 0) {
-        for (int k = 0; k < n; ++k) d[k] = A[k * n + k].x;
-        if (n >= 2) ph[n - 2] = A[(n - 1) * n + n - 2];      // last subdiagonal (no reflector)
         double2 dl = make_double2(1.0, 0.0);
+        for (int k = 0; k < n; ++k) d[k] = sc[k];
         for (int k = 0; k + 1 < n; ++k) {
-            const double2 a = ph[k];
+            const double2 a = make_double2(sc[n + 2 * k], sc[n + 2 * k + 1]);
             const double m = hypot(a.x, a.y);
             e[k] = m;
             const double2 u = m > 0.0 ? make_double2(a.x / m, a.y / m) : make_double2(1.0, 0.0);
@@ -364,12 +381,11 @@ hhql_kernel(const double2* __restrict__ Dg, double* __restrict__ Zg, double2* __
             dl = make_double2(dl.x * u.x - dl.y * u.y, dl.x * u.y + dl.y * u.x);
         }
         ph[n - 1] = dl;
-        if (n >= 1) e[n - 1] = 0.0;
+        e[n - 1] = 0.0;
         sweep_fail = 0;
     }
     for (int64_t t = tid; t < nn; t += nt) Z[t] = (t / n == t % n) ? 1.0 : 0.0;
     __syncthreads();
-    // ---- 3. implicit QL (tql2): thread 0 forms the rotations, all threads apply them
     for (int l = 0; l < n; ++l) {
         for (int iter = 0; iter <= kQlMaxIter; ++iter) {
             if (tid == 0) {
@@ -390,7 +406,7 @@ hhql_kernel(const double2* __restrict__ Dg, double* __restrict__ Zg, double2* __
                         int i = m - 1;
                         bool underflow = false;
                         for (; i >= l; --i) {
-                            double f = sn * e[i], b = cs * e[i];
+                            const double f = sn * e[i], b = cs * e[i];
                             r = hypot(f, g);
                             e[i + 1] = r;
                             if (r == 0.0) { d[i + 1] -= p; e[m] = 0.0; underflow = true; break; }
@@ -404,60 +420,31 @@ hhql_kernel(const double2* __restrict__ Dg, double* __restrict__ Zg, double2* __
                             rc[i] = cs;
                             rs[i] = sn;
                         }
-                        if (underflow) {
-                            sweep_lo = i + 1;                  // rotations i+1 .. m-1 were formed
-                        } else {
-                            d[l] -= p;
-                            e[l] = g;
-                            e[m] = 0.0;
-                        }
+                        if (underflow) sweep_lo = i + 1;     // rotations i+1 .. m-1 were formed
+                        else { d[l] -= p; e[l] = g; e[m] = 0.0; }
                     }
                 }
             }
             __syncthreads();
             const int lo = sweep_lo, hi = sweep_hi;
-            if (hi == l && lo == l) break;                       // converged (or gave up)
-            // apply rotations i = hi-1 down to lo to every row of Z (columns i, i+1)
+            if (hi == l && lo == l) break;
+            // rotations hi-1 .. lo on columns (i, i+1) of every row; column i+1's new value is
+            // stored, column i's is carried to the next rotation in a register
             for (int row = tid; row < n; row += nt) {
+                if (hi <= lo) break;
+                double carry = Z[(int64_t)hi * n + row];
                 for (int i = hi - 1; i >= lo; --i) {
                     const double c = rc[i], sg = rs[i];
-                    const double f = Z[(int64_t)(i + 1) * n + row], zi = Z[(int64_t)i * n + row];
-                    Z[(int64_t)(i + 1) * n + row] = sg * zi + c * f;
-                    Z[(int64_t)i * n + row] = c * zi - sg * f;
+                    const double zi = Z[(int64_t)i * n + row];
+                    Z[(int64_t)(i + 1) * n + row] = sg * zi + c * carry;
+                    carry = c * zi - sg * carry;
                 }
+                Z[(int64_t)lo * n + row] = carry;
             }
             __syncthreads();
         }
     }
     if (tid == 0 && sweep_fail) atomicExch(status, (int)PHX_ERR_NUMERIC);
-    // ---- 4. E = H_0 ... H_{n-3} diag(delta) Z  (thread per column j)
-    for (int j = tid; j < n; j += nt) {
-        for (int i = 0; i < n; ++i) {
-            const double z = Z[(int64_t)j * n + i];
-            E[(int64_t)i * n + j] = make_double2(ph[i].x * z, ph[i].y * z);
-        }
-        for (int k = n - 3; k >= 0; --k) {
-            const double beta = bet[k];
-            if (beta == 0.0) continue;
-            const int m = n - k - 1;
-            double2 s = make_double2(0.0, 0.0);
-            for (int i = 0; i < m; ++i) {
-                const double2 v = A[(k + 1 + i) * n + k], x = E[(int64_t)(k + 1 + i) * n + j];
-                s.x += v.x * x.x + v.y * x.y;                    // conj(v) x
-                s.y += v.x * x.y - v.y * x.x;
-            }
-            s.x *= beta;
-            s.y *= beta;
-            for (int i = 0; i < m; ++i) {
-                const double2 v = A[(k + 1 + i) * n + k];
-                double2& x = E[(int64_t)(k + 1 + i) * n + j];
-                x.x -= v.x * s.x - v.y * s.y;
-                x.y -= v.x * s.y + v.y * s.x;
-            }
-        }
-    }
-    __syncthreads();
-    // ---- ranks, frequencies, gauge
     for (int i = tid; i < n; i += nt) {
         int r = 0;
         const double li = d[i];
@@ -467,11 +454,41 @@ hhql_kernel(const double2* __restrict__ Dg, double* __restrict__ Zg, double2* __
         freq[(int64_t)qi * n + r] = (w2 >= 0.0 ? sqrt(w2) : -sqrt(-w2)) / phx::kTwoPi;
     }
     __syncthreads();
+    // E = H_0 ... H_{n-3} diag(delta) Z, column j written into the sorted output column
+    for (int j = tid; j < n; j += nt) {
+        const int dst = rank_of[j];
+        for (int i = 0; i < n; ++i) {
+            const double z = Z[(int64_t)j * n + i];
+            Eo[(int64_t)i * n + dst] = make_double2(ph[i].x * z, ph[i].y * z);
+        }
+        for (int k = n - 3; k >= 0; --k) {
+            const double beta = sc[3 * n + k];
+            if (beta == 0.0) continue;
+            const int m = n - k - 1;
+            const double2* v = R + (int64_t)k * n;
+            double2 s = make_double2(0.0, 0.0);
+            for (int i = 0; i < m; ++i) {
+                const double2 vi = v[i], x = Eo[(int64_t)(k + 1 + i) * n + dst];
+                s.x += vi.x * x.x + vi.y * x.y;                  // conj(v) x
+                s.y += vi.x * x.y - vi.y * x.x;
+            }
+            s.x *= beta;
+            s.y *= beta;
+            for (int i = 0; i < m; ++i) {
+                const double2 vi = v[i];
+                double2& x = Eo[(int64_t)(k + 1 + i) * n + dst];
+                x.x -= vi.x * s.x - vi.y * s.y;
+                x.y -= vi.x * s.y + vi.y * s.x;
+            }
+        }
+    }
+    __syncthreads();
+    // gauge: largest-modulus component real positive (first index on ties); one warp per column
     for (int col = warp; col < n; col += nw) {
         double best = -1.0;
         int bi = 0;
         for (int i = lane; i < n; i += 32) {
-            const double2 v = E[(int64_t)i * n + col];
+            const double2 v = Eo[(int64_t)i * n + col];
             const double a = v.x * v.x + v.y * v.y;
             if (a > best) { best = a; bi = i; }
         }
@@ -480,12 +497,11 @@ hhql_kernel(const double2* __restrict__ Dg, double* __restrict__ Zg, double2* __
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        const double2 vm = E[(int64_t)bi * n + col];
+        const double2 vm = Eo[(int64_t)bi * n + col];
         const double h = hypot(vm.x, vm.y);
         const double2 g = h > 0.0 ? make_double2(vm.x / h, -vm.y / h) : make_double2(1.0, 0.0);
-        const int dst = rank_of[col];
-        for (int i = lane; i < n; i += 32)
-            evec[(int64_t)qi * nn + (int64_t)i * n + dst] = cmul(E[(int64_t)i * n + col], g);
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) Eo[(int64_t)i * n + col] = cmul(Eo[(int64_t)i * n + col], g);
     }
 }
 
@@ -568,18 +584,20 @@ cudaError_t phx_launch_dynmat(const double* q_frac, int nq, int n_atoms, const i
 }
 
 cudaError_t phx_launch_jacobi(double* A, double* V, int n, int nq, double* freq, double* evec,
-                              int32_t* status, cudaStream_t s) {
+                              int32_t* status, cudaStream_t s, double* scratch) {
     if (nq <= 0) return cudaSuccess;
     if (n > kMaxModes) return cudaErrorInvalidValue;
     const size_t smem = (size_t)n * n * sizeof(double2);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (n <= kHhqlMaxModes && !std::getenv("PHX_EIG_JACOBI")) {
-        // Householder + QL; Z (real) lives in A's buffer, the back-transformed vectors in V's
-        cudaError_t e = cudaFuncSetAttribute(hhql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (n <= kHhqlMaxModes && scratch && !std::getenv("PHX_EIG_JACOBI")) {
+        // Householder reduction (reflectors into V's buffer), then QL + back-transformation
+        // with Z (real) in A's buffer
+        cudaError_t e = cudaFuncSetAttribute(hh_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        hhql_kernel<<<nq, 256, smem, s>>>((const double2*)A, A, (double2*)V, n, freq, (double2*)evec, status);
+        hh_reduce_kernel<<<nq, 256, smem, s>>>((const double2*)A, (double2*)V, scratch, n);
+        ql_back_kernel<<<nq, kQlThreads, 0, s>>>((const double2*)V, scratch, A, n, freq, (double2*)evec, status);
         return cudaGetLastError();
     }
     const size_t static_bytes = 8 * 1024;     // rotation tables etc. (upper bound)

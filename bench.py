@@ -32,8 +32,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu capture summarised in
 # profiles/tc_gemm_fcc32_mesh8.md (same per-launch shape as the bench); valid for the kernel
 # source it was taken on
-DRAM_TRAFFIC_PER_LAUNCH = {("dft", "bf16x3"): 226.68e6 + 426.45e6, ("gemm_e2", "bf16x3"): 500.43e6 + 433.85e6,
-                           ("gemm_e1_gamma", "bf16x3"): 499.97e6 + 3.29e6}
+DRAM_TRAFFIC_PER_LAUNCH = {}
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
 
 

@@ -102,6 +102,23 @@ __device__ __forceinline__ void store_operand(void* hi, void* lo, int64_t idx, f
     }
 }
 
+// Two adjacent elements (idx even): one 4-byte (bf16 planes) or 8-byte (tf32) store per plane.
+template <int PREC>
+__device__ __forceinline__ void store_operand2(void* hi, void* lo, int64_t idx, float a0, float a1) {
+    if (PREC == P_BF16X3) {
+        __nv_bfloat16 h0, l0, h1, l1;
+        tc::split_bf16(a0, &h0, &l0);
+        tc::split_bf16(a1, &h1, &l1);
+        __nv_bfloat162 H, L;
+        H.x = h0; H.y = h1;
+        L.x = l0; L.y = l1;
+        *reinterpret_cast<__nv_bfloat162*>((__nv_bfloat16*)hi + idx) = H;
+        *reinterpret_cast<__nv_bfloat162*>((__nv_bfloat16*)lo + idx) = L;
+    } else {
+        *reinterpret_cast<float2*>((float*)hi + idx) = make_float2(tc::round_tf32(a0), tc::round_tf32(a1));
+    }
+}
+
 __device__ __forceinline__ void epi_barrier(int threads) { asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory"); }
 
 template <int PREC, int EPI, bool kStreamB>
@@ -327,7 +344,27 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
             const bool valid = row < args.rows;
             const uint32_t taddr = tmem_base + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)(acc * NA);
             float v[16];
-            if (EPI == EPI_M) {
+            if (EPI == EPI_M && (args.n & 1) == 0) {
+                // row (nu, b, c) of W -> M_slot[(nu, b)][c] (re) and [(nu, b)][Kcp + c] (im).  With n
+                // even, lanes (2l, 2l+1) hold rows c, c+1 of the same (nu, b): the pair exchanges one
+                // value per two columns and stores two adjacent elements at once.
+                const int nb = row / args.n, ce = (row % args.n) & ~1;
+                const bool odd = lane & 1;
+                for (int j0 = half * 16; j0 < NA; j0 += kStride) {
+                    tc::tmem_ld16(taddr + j0, v);
+#pragma unroll
+                    for (int i = 0; i < 16; i += 2) {
+                        const float recv = __shfl_xor_sync(0xffffffffu, odd ? v[i] : v[i + 1], 1);
+                        const int j = j0 + i + (odd ? 1 : 0);
+                        const float a0 = odd ? recv : v[i], a1 = odd ? v[i + 1] : recv;
+                        const int slot = m0 + (j < mg ? j : j - mg);
+                        if (!valid || slot >= args.nq_slots) continue;
+                        const int64_t idx = ((int64_t)slot * args.out_rows_per_slot + nb) * args.out_kr +
+                                            (j < mg ? 0 : args.out_kcp) + ce;
+                        store_operand2<PREC>(args.out_hi, args.out_lo, idx, a0, a1);
+                    }
+                }
+            } else if (EPI == EPI_M) {
                 // row (nu, b, c) of W -> M_slot[(nu, b)][c] (re) and [(nu, b)][Kcp + c] (im)
                 const int nb = row / args.n, c = row % args.n;
                 for (int j0 = half * 16; j0 < NA; j0 += kStride) {
@@ -342,6 +379,25 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                                                 (j < mg ? 0 : args.out_kcp) + c;
                             store_operand<PREC>(args.out_hi, args.out_lo, idx, v[i]);
                         }
+                    }
+                }
+            } else if (EPI == EPI_X && (args.n & 1) == 0) {
+                // row (nu, b) -> X[(nu, nu'')][b] (re) and [(nu, nu'')][Kcp + b] (im); paired stores
+                // of rows b, b+1 as in EPI_M
+                const int nu = row / args.n, be = (row % args.n) & ~1;
+                const bool odd = lane & 1;
+                const int64_t base = (int64_t)p * args.out_rows_per_slot + (int64_t)nu * args.n;
+                for (int j0 = half * 16; j0 < NA; j0 += kStride) {
+                    tc::tmem_ld16(taddr + j0, v);
+#pragma unroll
+                    for (int i = 0; i < 16; i += 2) {
+                        const float recv = __shfl_xor_sync(0xffffffffu, odd ? v[i] : v[i + 1], 1);
+                        const int j = j0 + i + (odd ? 1 : 0);
+                        const float a0 = odd ? recv : v[i], a1 = odd ? v[i + 1] : recv;
+                        const int mode = m0 + (j < mg ? j : j - mg);
+                        if (!valid || mode >= args.n) continue;
+                        const int64_t idx = (base + mode) * args.out_kr + (j < mg ? 0 : args.out_kcp) + be;
+                        store_operand2<PREC>(args.out_hi, args.out_lo, idx, a0, a1);
                     }
                 }
             } else if (EPI == EPI_X) {

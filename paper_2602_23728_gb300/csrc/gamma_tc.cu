@@ -632,38 +632,43 @@ __global__ void fold_phase_kernel(const int32_t* __restrict__ ent_r2, const doub
     }
 }
 
-// S3, part 2: the DFT's A operand, row (nu, b, c), K = [Re W(d) | Im W(d)].  One warp per
-// row, lane = d (looping when n_d > 32), so every store instruction writes one contiguous
-// run of the row.  seg_of[(b*n + c)*n_d + d] is the COO segment of (d, b, c) or -1; rows
-// without any segment are written as zeros, so no clearing is needed.
+// S3, part 2: the DFT's A operand, row (nu, b, c), K = [Re W(d) | Im W(d)].  Half a warp per
+// row, each lane two adjacent d (looping when n_d > 32), stored as pairs, so every store
+// instruction writes one contiguous run of the row.  seg_of[(b*n + c)*n_d + d] is the COO
+// segment of (d, b, c) or -1; rows without any segment are written as zeros, so no clearing
+// is needed.
 template <int PREC>
 __global__ void fold_tc_kernel(const int32_t* __restrict__ seg_of, const int64_t* __restrict__ seg_start,
                                const int32_t* __restrict__ ent_a, const float2* __restrict__ wph, int n_d,
                                const float2* __restrict__ eqf, int n, int nu0, int rows, int kcp, void* hi,
                                void* lo) {
+    // half a warp per row: lane h of the half computes d = 2h + 32 t and 2h + 1 + 32 t (two
+    // independent segment walks) and stores both as one pair per plane
     const int nn = n * n;
     const int kr = 2 * kcp;
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
+    const int h = threadIdx.x & 15;
+    const int halves = gridDim.x * (blockDim.x >> 4);
+    for (int row = blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4); row < rows; row += halves) {
         const int nu = nu0 + row / nn;
         const int bc = row % nn;
-        for (int d = lane; d < kcp; d += 32) {
-            float ar = 0.f, ai = 0.f;
-            if (d < n_d) {
+        for (int d0 = 2 * h; d0 < kcp; d0 += 32) {
+            float ar[2] = {0.f, 0.f}, ai[2] = {0.f, 0.f};
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int d = d0 + u;
+                if (d >= n_d) continue;
                 const int s = seg_of[bc * n_d + d];
-                if (s >= 0) {
-                    const int64_t k1 = seg_start[s + 1];
-                    for (int64_t k = seg_start[s]; k < k1; ++k) {
-                        const float2 w = wph[k];
-                        const float2 e = eqf[ent_a[k] * n + nu];
-                        ar += w.x * e.x - w.y * e.y;
-                        ai += w.x * e.y + w.y * e.x;
-                    }
+                if (s < 0) continue;
+                const int64_t k1 = seg_start[s + 1];
+                for (int64_t k = seg_start[s]; k < k1; ++k) {
+                    const float2 w = wph[k];
+                    const float2 e = eqf[ent_a[k] * n + nu];
+                    ar[u] += w.x * e.x - w.y * e.y;
+                    ai[u] += w.x * e.y + w.y * e.x;
                 }
             }
-            store_operand<PREC>(hi, lo, (int64_t)row * kr + d, ar);
-            store_operand<PREC>(hi, lo, (int64_t)row * kr + kcp + d, ai);
+            store_operand2<PREC>(hi, lo, (int64_t)row * kr + d0, ar[0], ar[1]);
+            store_operand2<PREC>(hi, lo, (int64_t)row * kr + kcp + d0, ai[0], ai[1]);
         }
     }
 }
@@ -995,7 +1000,7 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
             const int64_t rw = (int64_t)nnu * n2, ra = (int64_t)nnu * n;
             {
                 const int pf = phx_prof_begin(ctx, s);
-                const int blocks = (int)std::min<int64_t>((rw + 7) / 8, (int64_t)sms * 32);
+                const int blocks = (int)std::min<int64_t>((rw + 15) / 16, (int64_t)sms * 32);
                 fold_tc_kernel<PREC><<<blocks, 256, 0, s>>>(f->tc_seg_of, f->seg_start, f->ent_a, B.wph, f->n_d, B.eqf,
                                                             n, nu0, (int)rw, kcp_d, B.W.hi, B.W.lo);
                 PHX_CUDA_CHECK(ctx, cudaGetLastError());

@@ -422,6 +422,26 @@ def run_phx(args):
                              "gamma_max_rel_err_vs_fp64": float((np.abs(a - b)[big] / b[big]).max())}
         line["speedup_vs_fp64_path"] = value / world / (trip64 / t64)
 
+    if args.kappa_fp64:
+        # kappa of each precision against the FP64 GPU path over all irreducible q (the FP64
+        # path is parity-tested against the oracle); each run recomputes the whole step
+        out = {}
+        for prec in ("fp64", "bf16x3", "tf32"):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            k = wl.step(prec).copy()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[prec] = (k, e0.elapsed_time(e1), wl.g_irr.cpu().numpy().copy())
+        k64, _, g64 = out["fp64"]
+        big = g64 > 1e-3 * g64.max()
+        line["kappa_vs_fp64_path"] = {
+            p: {"kappa_rel_err": float(np.linalg.norm(out[p][0] - k64) / np.linalg.norm(k64)),
+                "gamma_max_rel_err": float((np.abs(out[p][2] - g64)[big] / g64[big]).max()),
+                "step_ms": out[p][1]} for p in ("bf16x3", "tf32")}
+        line["kappa_vs_fp64_path"]["fp64_step_ms"] = out["fp64"][1]
+        line["kappa_vs_fp64_path"]["kappa_fp64_wmk"] = np.diag(k64).tolist()
+
     if args.multi_t > 0:
         # several temperatures from one contraction against one call per temperature
         w = wl.w
@@ -470,7 +490,7 @@ def run_batched(args):
     t_setup = time.perf_counter()
     for w in sweep:
         c = w.crystal
-        f2, f3 = w.ifc2(), w.ifc3()
+        f2, f3 = P.ifc_lj_vectorised(c, w.pot)      # same entries as w.ifc2(), w.ifc3(), faster
         n = c.n_modes
         nq = int(np.prod(w.mesh))
         m = w.mesh
@@ -704,6 +724,8 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32", "fp64"])
     ap.add_argument("--fp64-q", type=int, default=4, help="irreducible q timed on the FP64 GPU path (0: skip)")
     ap.add_argument("--cpu-qp", type=int, default=None, help="q' of the oracle sample (default all)")
+    ap.add_argument("--kappa-fp64", action="store_true",
+                    help="also run the whole step in FP64 and TF32 and report the kappa error of each precision")
     ap.add_argument("--multi-t", type=int, default=4,
                     help="temperatures timed in one contraction vs one call each (0: skip)")
     ap.add_argument("--ref-qp", type=int, default=64, help="q' per reference step")

@@ -15,6 +15,7 @@ Modules
   occupation -- Eqs. (bose), (heatcap)
   anharmonic -- Eqs. (phi3_proj), (gamma), (broadening), (lifetime)
   transport  -- Eq. (rta)
+  bte        -- Eqs. (gamma1), (sc_iter), (inverse): iterative and direct linearised BTE
   supercell  -- Gamma-only brute force of Eq. (phi3_proj) on a supercell (folding pin)
   gammapoint -- Gamma-only linewidths of a large cell mode by mode, sparse Phi3 (1000-atom cell)
   isotope    -- Eq. (isotope): Tamura mass-variance scattering
@@ -25,4 +26,4 @@ Parity status: every function here is pinned by tests under tests/ (closed forms
 invariants, brute force); none is "parity unpinned" except the absolute value of the
 LJ-argon conductivity, for which the paper prints no number.
 """
-from . import constants, grid, harmonic, occupation, anharmonic, transport, supercell, surrogate, gammapoint, isotope, qhgk  # noqa: F401
+from . import constants, grid, harmonic, occupation, anharmonic, transport, supercell, surrogate, gammapoint, isotope, qhgk, bte  # noqa: F401

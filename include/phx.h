@@ -325,6 +325,42 @@ phx_status phx_kappa_rta(phx_ctx* ctx, const phx_cell* cell, int32_t nq, int32_t
                          const double* gamma_full, double temperature, double f_min_thz,
                          int32_t is_classic, double* kappa_wmk, int32_t mem, void* stream);
 
+/* ---------------------------------------------------------------- iterative BTE
+ * Sec. "Boltzmann Transport Equation", Eqs. (gamma1), (invBTE), (kappa_general), (sc_iter):
+ * the linearised BTE for the mean free paths lambda (A, a 3-vector per mode),
+ *     v_mu = Gamma0_mu lambda_mu + sum_mu' Gamma1[mu][mu'] lambda_mu',
+ * solved by iteration from the RTA start lambda^(0) = v / Gamma0 (Eq. rta), with
+ * kappa^(k) = 1/(N_q V) sum_mu c_mu v_mu (x) lambda^(k)_mu (quantum c, Eq. heatcap).
+ *  - Unknowns: every band of the time-reversal representatives of the fc3 handle's mesh
+ *    (each orbit {q, -q} keeps its smallest index; ascending, i.e. the irr list of
+ *    phx_irreducible with no rotation besides the identity).  Row r = s * n + nu of
+ *    representative s; R = n_tr * n rows.  lambda(-q) = -lambda(q), so points with
+ *    q = -q mod G carry lambda = 0, and modes with f < f_min or Gamma0 = 0 do too.
+ *  - One contraction pass in precision prec (as phx_gamma) gives Gamma0 (the linewidth
+ *    gamma, 1/ps) and the off-diagonal Gamma1 (1/ps), read from Eq. (gamma1) as the
+ *    linearised three-phonon collision operator: every element (q', nu', nu'') of mu's
+ *    linewidth sum, with weight w (decay + absorption term), adds w f'/f at column (q', nu')
+ *    and w f''/f at column (q'' = -q-q', nu''); a column of a point listed through -q is
+ *    added with sign -1.  Gamma1 stays on the device, R x R in FP64 (prec = PHX_FP64) or
+ *    FP32 (tensor-core precisions); inputs whose Gamma1 exceeds 96 GB return
+ *    PHX_ERR_UNSUPPORTED.
+ *  - Iteration (Eq. sc_iter) lambda^(k+1) = (v - Gamma1 lambda^(k)) / Gamma0 stops at the
+ *    first k >= 1 with |Tr kappa^(k) - Tr kappa^(k-1)| < tol |Tr kappa^(k-1)| (*converged =
+ *    1), or after max_iter iterations (*converged = 0).
+ * Arguments: freq_thz[nq][n], evec[nq][n][n] complex, vel[nq][n][3] (A/ps) cover the mesh
+ * [mem]; temperature, br, f_min_thz, prec as phx_gamma; max_iter >= 0; tol >= 0.
+ * Outputs (host): kappa_hist[(max_iter + 1) * 9] (W/(m K)), iterate k in entries 9k..9k+8
+ * (row-major 3x3), k = 0 .. *n_iter; *n_iter; *converged (may be NULL).  Optional [mem]
+ * outputs (NULL skips): gamma0[R], mfp[R][3] (the last iterate), gamma1[R][R] (doubles).
+ * The call synchronises `stream`.  Errors: PHX_ERR_INVALID (bad argument), PHX_ERR_UNSUPPORTED
+ * (a 1x1x1 mesh; too large), PHX_ERR_NOMEM, PHX_ERR_NUMERIC (a non-finite iterate: the
+ * iteration diverged), PHX_ERR_TIMEOUT (a bounded device wait gave up). */
+phx_status phx_kappa_sc(phx_ctx* ctx, const phx_cell* cell, const phx_fc3* fc3, const double* freq_thz,
+                        const double* evec, const double* vel, double temperature, phx_broadening br,
+                        double f_min_thz, int32_t prec, int32_t max_iter, double tol, double* kappa_hist,
+                        int32_t* n_iter, int32_t* converged, double* gamma0, double* mfp, double* gamma1,
+                        int32_t mem, void* stream);
+
 /* ---------------------------------------------------------------- allocation-free conductivity
  * The paper has no counterpart to this call: it exists for callers that cannot allocate
  * device memory at the time they call (a host framework whose allocator owns nearly all of
@@ -367,7 +403,8 @@ typedef enum {
     PHX_K_EIG_VECTORS = 11, /* large-cell eigensolver: inverse iteration                    */
     PHX_K_EIG_BACK = 12,    /* large-cell eigensolver: back-transformation + output          */
     PHX_K_EIG_BISECT = 13,  /* large-cell eigensolver: Sturm multisection (eigenvalues)      */
-    PHX_K_COUNT = 14
+    PHX_K_SC_STEP = 14,     /* iterative BTE: one Gamma1 x mean-free-path pass (HBM-bound)   */
+    PHX_K_COUNT = 15
 } phx_kernel_class;
 
 /* Turn profiling on (1) or off (0); turning it on clears the counters.  Off by default. */

@@ -91,6 +91,9 @@ lib.phx_unfold.argtypes = [_P, _I, _I, _I, _P, _P, _P, _P, _P, _I, _P]
 lib.phx_unfold.restype = C.c_int
 lib.phx_kappa_rta.argtypes = [_P, C.POINTER(Cell), _I, _I, _P, _P, _P, _P, C.c_double, C.c_double, _I, _P, _I, _P]
 lib.phx_kappa_rta.restype = C.c_int
+lib.phx_kappa_sc.argtypes = [_P, C.POINTER(Cell), _P, _P, _P, _P, C.c_double, Broadening, C.c_double, _I, _I,
+                             C.c_double, _P, _P, _P, _P, _P, _P, _I, _P]
+lib.phx_kappa_sc.restype = C.c_int
 
 lib.phx_profile_enable.argtypes = [_P, _I]
 lib.phx_profile_enable.restype = C.c_int
@@ -124,10 +127,10 @@ lib.phx_mlp_predict.restype = C.c_int
 
 KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4, "fp64_epilogue": 5,
            "eigensolver": 6, "cell_sparse": 7, "cell_transpose": 8, "cell_gemm": 9, "eig_tridiag": 10,
-           "eig_vectors": 11, "eig_back": 12, "eig_bisect": 13}
+           "eig_vectors": 11, "eig_back": 12, "eig_bisect": 13, "sc_step": 14}
 
 EXPORTED = ["phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
-            "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_isotope", "phx_kappa_qhgk", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta",
+            "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_isotope", "phx_kappa_qhgk", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta", "phx_kappa_sc",
             "phx_kappa_rta_noalloc", "phx_gamma_batched", "phx_features", "phx_mlp_create", "phx_mlp_destroy",
             "phx_mlp_num_params", "phx_mlp_get_params", "phx_mlp_set_params", "phx_mlp_loss_grad", "phx_mlp_train",
             "phx_mlp_predict"]
@@ -468,6 +471,39 @@ class Context:
                                       _ptr(vv), _ptr(gamma_full), float(temperature), float(f_min), int(is_classic),
                                       k.ctypes.data, mem, stream))
         return k.reshape(3, 3)
+
+
+    def kappa_sc(self, lattice, masses, fc3, freq, evec, vel, temperature, shape="gauss", sigma=0.1, window=2.0,
+                 f_min=0.01, precision="bf16x3", max_iter=100, tol=1e-6, want_gamma1=False, gamma0=None, mfp=None,
+                 gamma1=None):
+        """phx_kappa_sc: the iterative BTE on the time-reversal representatives of fc3's mesh.
+        Returns dict(kappa [k+1, 3, 3] (iterate 0 = RTA), n_iter, converged, gamma0 [n_tr, n],
+        mfp [n_tr, n, 3], gamma1 [R, R] or None)."""
+        br = Broadening(SHAPES[shape], float(sigma), float(window))
+        cell, m = make_cell(lattice, masses)
+        mesh = fc3.mesh
+        n_self = int(np.prod([2 if k % 2 == 0 else 1 for k in mesh]))
+        n_tr = (int(np.prod(mesh)) + n_self) // 2
+        R = n_tr * fc3.n
+        if not _is_torch(freq):
+            freq = _host(freq, np.float64)
+            evec = _host(evec, np.complex128)
+            vel = _host(vel, np.float64)
+            gamma0 = np.zeros((n_tr, fc3.n)) if gamma0 is None else gamma0
+            mfp = np.zeros((n_tr, fc3.n, 3)) if mfp is None else mfp
+            if want_gamma1 and gamma1 is None:
+                gamma1 = np.zeros((R, R))
+        mem, stream = _mem_and_stream([freq, evec, vel, gamma0, mfp, gamma1])
+        hist = np.zeros((int(max_iter) + 1) * 9)
+        n_it = C.c_int32(0)
+        conv = C.c_int32(0)
+        self._check(lib.phx_kappa_sc(self.h, C.byref(cell), fc3.h, _ptr(freq), _ptr(evec), _ptr(vel),
+                                     float(temperature), br, float(f_min), PRECISIONS[precision], int(max_iter),
+                                     float(tol), hist.ctypes.data, C.addressof(n_it), C.addressof(conv),
+                                     _ptr(gamma0), _ptr(mfp), _ptr(gamma1), mem, stream))
+        k = n_it.value
+        return dict(kappa=hist[:9 * (k + 1)].reshape(k + 1, 3, 3), n_iter=k, converged=bool(conv.value),
+                    gamma0=gamma0, mfp=mfp, gamma1=gamma1)
 
 
 class MLP:

@@ -11,12 +11,6 @@
 
 #include "common.h"
 
-phx_status phx_gamma_fp64(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec,
-                          const double* nB, const int32_t* irr_host, int n_irr, const GammaParams& gp,
-                          double* gacc, double* wacc, cudaStream_t s);
-phx_status phx_gamma_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec,
-                        const double* nB, const int32_t* irr_host, int n_irr, const GammaParams& gp,
-                        int prec, double* gacc, double* wacc, cudaStream_t s);
 phx_status phx_gamma_tc_multi_t(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec,
                                 const double* nB, int n_t, const int32_t* irr_host, int n_irr, const GammaParams& gp,
                                 int prec, double* gacc, cudaStream_t s);

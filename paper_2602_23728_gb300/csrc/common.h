@@ -187,6 +187,17 @@ cudaError_t phx_launch_finalize(int count, int n, const int32_t* irr, const doub
                                 double* wp2, cudaStream_t s);
 cudaError_t phx_launch_scale9(const double* acc, double scale, double* out, cudaStream_t s);
 
+// Off-diagonal scattering rows (Eq. gamma1) accumulated by a linewidth contraction, folded
+// onto time-reversal representatives: row (position s of the representative, band nu) is
+// s * n + nu; mesh point p with band nu' is column (|tr_code[p]| - 1) * n + nu', added with
+// the sign of tr_code[p]; tr_code[p] = 0 (p = -p mod G) drops the column.
+struct G1Target {
+    void* mat;                  // float [rows][ld] (tensor-core paths) or double (FP64 path)
+    int64_t ld;                 // row stride (elements)
+    const int32_t* tr_code;     // device, [nq]
+    double scale;               // the linewidth prefactor pi hbar conv^3 / (8 N_q)
+};
+
 // gamma path shared parameters
 struct GammaParams {
     int n;                 // modes
@@ -198,3 +209,12 @@ struct GammaParams {
     double window;
     double f_min;
 };
+
+// Linewidth contractions (gacc/wacc: [n_irr][n] device accumulators, zeroed by the caller);
+// g1 (optional): also accumulate the off-diagonal scattering rows of the irreducible points.
+phx_status phx_gamma_fp64(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec,
+                          const double* nB, const int32_t* irr_host, int n_irr, const GammaParams& gp,
+                          double* gacc, double* wacc, cudaStream_t s, const G1Target* g1 = nullptr);
+phx_status phx_gamma_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec,
+                        const double* nB, const int32_t* irr_host, int n_irr, const GammaParams& gp,
+                        int prec, double* gacc, double* wacc, cudaStream_t s, const G1Target* g1 = nullptr);

@@ -107,6 +107,54 @@ epilogue_fp64_kernel(const double2* __restrict__ V, int t0, int iq, int n, int n
     }
 }
 
+// Off-diagonal scattering rows (Eq. gamma1) of the same tile: CTA (q' in tile, nu) adds, for
+// every element (nu', nu'') with weight w = |V|^2 x pair weight, w f'/f to column (q', nu') and
+// w f''/f to column (q'', nu'') of row (q, nu), folded onto the time-reversal representatives.
+__global__ void __launch_bounds__(256)
+g1_fp64_kernel(const double2* __restrict__ V, int t0, int iq, int n, int nu0, int n_nu,
+               const double* __restrict__ freq, const double* __restrict__ nB, const int32_t* __restrict__ qpp,
+               GammaParams gp, double* __restrict__ g1, int64_t ld, int64_t row0,
+               const int32_t* __restrict__ tr_code, double scale) {
+    const int b = blockIdx.x / n_nu, nl = blockIdx.x % n_nu;
+    const int qp = t0 + b;
+    const int q2 = qpp[qp];
+    const double f0 = freq[(int64_t)iq * n + nu0 + nl];
+    if (!(f0 >= gp.f_min)) return;
+    const double2* v = V + ((int64_t)b * n_nu + nl) * n * n;
+    double* row = g1 + (row0 + nl) * ld;
+    const int c1 = tr_code[qp], c2 = tr_code[q2];
+    // column (q', nu'): sum over nu''
+    if (c1 != 0)
+        for (int j1 = threadIdx.x; j1 < n; j1 += blockDim.x) {
+            const double f1 = freq[(int64_t)qp * n + j1], n1 = nB[(int64_t)qp * n + j1];
+            double acc = 0.0;
+            for (int j2 = 0; j2 < n; ++j2) {
+                const double wt = phx_pair_weight(f0, f1, freq[(int64_t)q2 * n + j2], n1, nB[(int64_t)q2 * n + j2], gp);
+                if (wt != 0.0) {
+                    const double2 x = v[(int64_t)j1 * n + j2];
+                    acc += (x.x * x.x + x.y * x.y) * wt;
+                }
+            }
+            if (acc != 0.0)
+                atomicAdd(&row[(int64_t)(abs(c1) - 1) * n + j1], (c1 > 0 ? 1.0 : -1.0) * scale * acc * f1 / f0);
+        }
+    // column (q'', nu''): sum over nu'
+    if (c2 != 0)
+        for (int j2 = threadIdx.x; j2 < n; j2 += blockDim.x) {
+            const double f2 = freq[(int64_t)q2 * n + j2], n2 = nB[(int64_t)q2 * n + j2];
+            double acc = 0.0;
+            for (int j1 = 0; j1 < n; ++j1) {
+                const double wt = phx_pair_weight(f0, freq[(int64_t)qp * n + j1], f2, nB[(int64_t)qp * n + j1], n2, gp);
+                if (wt != 0.0) {
+                    const double2 x = v[(int64_t)j1 * n + j2];
+                    acc += (x.x * x.x + x.y * x.y) * wt;
+                }
+            }
+            if (acc != 0.0)
+                atomicAdd(&row[(int64_t)(abs(c2) - 1) * n + j2], (c2 > 0 ? 1.0 : -1.0) * scale * acc * f2 / f0);
+        }
+}
+
 }  // namespace
 
 cudaError_t phx_launch_third_index(int iq, const int* mesh, int32_t* qpp, cudaStream_t s) {
@@ -126,7 +174,7 @@ cudaError_t phx_launch_phases(const phx_fc3* f, double* P, cudaStream_t s) {
 // FP64 path for one call.  gacc/wacc: [n_irr][n] device accumulators (zeroed by the caller).
 phx_status phx_gamma_fp64(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec,
                           const double* nB, const int32_t* irr_host, int n_irr, const GammaParams& gp,
-                          double* gacc, double* wacc, cudaStream_t s) {
+                          double* gacc, double* wacc, cudaStream_t s, const G1Target* g1t) {
     const int n = f->n, nq = f->nq;
     const int64_t n2 = (int64_t)n * n, n3 = n2 * n;
     // nu chunk and q' tile sized so that W and the three per-tile buffers stay within ~1.5 GB
@@ -204,6 +252,13 @@ phx_status phx_gamma_fp64(phx_ctx* ctx, const phx_fc3* f, const double* freq, co
                                                                 nB, qpp, gp, gacc + (int64_t)si * n,
                                                                 wacc ? wacc + (int64_t)si * n : nullptr);
                 PHX_CUDA_CHECK(ctx, cudaGetLastError());
+                if (g1t) {
+                    g1_fp64_kernel<<<Qt * nn_nu, 256, 0, s>>>((const double2*)V, t0, iq, n, nu0, nn_nu, freq, nB, qpp,
+                                                              gp, (double*)g1t->mat, g1t->ld, (int64_t)si * n + nu0,
+                                                              g1t->tr_code, g1t->scale);
+                    PHX_CUDA_CHECK(ctx, cudaGetLastError());
+                    ctx->launches += 1;
+                }
                 phx_prof_end(ctx, pe, s, PHX_K_FP64_EPI, 0.0, 16.0 * (double)Qt * Rc);
                 ctx->launches += 4;
             }

@@ -47,8 +47,11 @@ constexpr int kStageBytesPerPlane = kBoxRows * kChunkBytes;
 constexpr int kMaxNp = 192;                    // padded modes (or q' slots) per output half
 constexpr size_t kSmemLimit = 232448;          // 227 KB opt-in
 
-enum { EPI_M = 0, EPI_X = 1, EPI_G = 2, EPI_GT = 3 };   // EPI_GT: EPI_G for up to kMaxT temperatures
+// EPI_GT: EPI_G for up to kMaxT temperatures; EPI_GS: EPI_G plus the off-diagonal scattering
+// rows of Eq. (gamma1)
+enum { EPI_M = 0, EPI_X = 1, EPI_G = 2, EPI_GT = 3, EPI_GS = 4 };
 constexpr int kMaxT = 4;
+constexpr int kG1Slots = 768;     // EPI_GS column-sum buffer: (bands of q in a tile) x (modes of a group)
 enum { P_BF16X3 = 0, P_TF32 = 1 };
 
 struct TcArgs {
@@ -88,6 +91,13 @@ struct TcArgs {
     int n_t;
     int64_t nb_stride;
     int64_t t_stride;
+    // EPI_GS: off-diagonal rows folded onto time-reversal representatives (see G1Target)
+    float* g1;
+    int64_t g1_rows;
+    int64_t g1_ld;
+    int64_t g1_row0;            // row of (this q, band nu0)
+    const int32_t* tr_code;
+    double g1_scale;
 };
 
 template <int PREC>
@@ -121,6 +131,22 @@ __device__ __forceinline__ void store_operand2(void* hi, void* lo, int64_t idx, 
 
 __device__ __forceinline__ void epi_barrier(int threads) { asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory"); }
 
+// Epilogue barrier that also returns whether any participating thread passed pred = true, so
+// that every epilogue thread takes the same decision (a shared flag read after a plain barrier
+// can change between two threads' reads when another role sets it).
+__device__ __forceinline__ bool epi_barrier_any(int threads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(threads)
+        : "memory");
+    return r != 0;
+}
+
 template <int PREC, int EPI, bool kStreamB>
 __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const __grid_constant__ TcArgs args) {
     constexpr int kEpiThreads = 32 * epi_warps<EPI>();
@@ -134,6 +160,8 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
     __shared__ volatile int abort_flag;
     __shared__ float s_f1[kMaxNp], s_n1[kMaxNp], s_if1[kMaxNp];
     __shared__ float s_n1t[EPI == EPI_GT ? kMaxT * kMaxNp : 1];
+    __shared__ float s_a2[EPI == EPI_GS ? kG1Slots : 1];      // column sums (q', nu') per band nu of q
+    __shared__ float s_a3[EPI == EPI_GS ? kBoxRows : 1];      // row sums (q'', nu'') per tile row
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int np = args.np, mg = args.mg, NA = 2 * mg, nk = args.nk, stages = args.stages;
@@ -166,6 +194,10 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
         for (int pl = 0; pl < kPlanes; ++pl) { tc::prefetch_tmap(&args.a_map[pl]); tc::prefetch_tmap(&args.b_map[pl]); }
     }
     if (warp == 1) tc::tmem_alloc(&tmem_base_slot, args.tmem_cols);
+    if (EPI == EPI_GS) {
+        for (int i = threadIdx.x; i < kG1Slots; i += blockDim.x) s_a2[i] = 0.f;
+        for (int i = threadIdx.x; i < kBoxRows; i += blockDim.x) s_a3[i] = 0.f;
+    }
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem_base = tmem_base_slot;
@@ -319,9 +351,8 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                 abort_flag = 1;
                 atomicExch(args.status, (int)PHX_ERR_TIMEOUT);
             }
-            epi_barrier(kEpiThreads);      // every epilogue thread takes the same decision
-            if (abort_flag) break;
-            if ((EPI == EPI_G || EPI == EPI_GT) && p != cur_p) {
+            if (epi_barrier_any(kEpiThreads, !ok || abort_flag != 0)) break;   // one decision for all
+            if ((EPI == EPI_G || EPI == EPI_GT || EPI == EPI_GS) && p != cur_p) {
                 // partner tables of this problem's q' (the previous tile is done: barrier above)
                 q1 = args.t0 + p;
                 q2 = phx_third_index(args.iq, q1, args.m1, args.m2, args.m3);
@@ -344,10 +375,32 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
             const bool valid = row < args.rows;
             const uint32_t taddr = tmem_base + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)(acc * NA);
             float v[16];
-            if (EPI == EPI_M && (args.n & 1) == 0) {
+            if (EPI == EPI_M && (args.n & 1) == 0 && (mg & 15) == 0) {
                 // row (nu, b, c) of W -> M_slot[(nu, b)][c] (re) and [(nu, b)][Kcp + c] (im).  With n
                 // even, lanes (2l, 2l+1) hold rows c, c+1 of the same (nu, b): the pair exchanges one
-                // value per two columns and stores two adjacent elements at once.
+                // value per two columns and stores two adjacent elements at once.  With mg a
+                // multiple of 16 a 16-column chunk lies wholly in the Re or the Im half, so the
+                // destination advances by a fixed stride per column pair.
+                const int nb = row / args.n, ce = (row % args.n) & ~1;
+                const bool odd = lane & 1;
+                const int64_t slot_stride = (int64_t)args.out_rows_per_slot * args.out_kr;
+                const int64_t row_off = (int64_t)nb * args.out_kr + ce;
+                for (int j0 = half * 16; j0 < NA; j0 += kStride) {
+                    tc::tmem_ld16(taddr + j0, v);
+                    const bool re = j0 < mg;
+                    const int s0 = m0 + (re ? j0 : j0 - mg) + (odd ? 1 : 0);   // slot of this lane's first pair
+                    const int n_ok = valid ? args.nq_slots - s0 : 0;            // pairs with slot < nq_slots
+                    int64_t idx = (int64_t)s0 * slot_stride + row_off + (re ? 0 : args.out_kcp);
+#pragma unroll
+                    for (int i = 0; i < 16; i += 2) {
+                        const float recv = __shfl_xor_sync(0xffffffffu, odd ? v[i] : v[i + 1], 1);
+                        const float a0 = odd ? recv : v[i], a1 = odd ? v[i + 1] : recv;
+                        if (i < n_ok) store_operand2<PREC>(args.out_hi, args.out_lo, idx, a0, a1);
+                        idx += 2 * slot_stride;
+                    }
+                }
+            } else if (EPI == EPI_M && (args.n & 1) == 0) {
+                // as above for any mg (a chunk may straddle the Re/Im halves)
                 const int nb = row / args.n, ce = (row % args.n) & ~1;
                 const bool odd = lane & 1;
                 for (int j0 = half * 16; j0 < NA; j0 += kStride) {
@@ -381,23 +434,25 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                         }
                     }
                 }
-            } else if (EPI == EPI_X && (args.n & 1) == 0) {
+            } else if (EPI == EPI_X && (args.n & 1) == 0 && (mg & 15) == 0) {
                 // row (nu, b) -> X[(nu, nu'')][b] (re) and [(nu, nu'')][Kcp + b] (im); paired stores
                 // of rows b, b+1 as in EPI_M
+                // (mg is a multiple of 16 on this path: a chunk lies in one half, fixed stride)
                 const int nu = row / args.n, be = (row % args.n) & ~1;
                 const bool odd = lane & 1;
                 const int64_t base = (int64_t)p * args.out_rows_per_slot + (int64_t)nu * args.n;
                 for (int j0 = half * 16; j0 < NA; j0 += kStride) {
                     tc::tmem_ld16(taddr + j0, v);
+                    const bool re = j0 < mg;
+                    const int mode0 = m0 + (re ? j0 : j0 - mg) + (odd ? 1 : 0);
+                    const int n_ok = valid ? args.n - mode0 : 0;
+                    int64_t idx = (base + mode0) * args.out_kr + (re ? 0 : args.out_kcp) + be;
 #pragma unroll
                     for (int i = 0; i < 16; i += 2) {
                         const float recv = __shfl_xor_sync(0xffffffffu, odd ? v[i] : v[i + 1], 1);
-                        const int j = j0 + i + (odd ? 1 : 0);
                         const float a0 = odd ? recv : v[i], a1 = odd ? v[i + 1] : recv;
-                        const int mode = m0 + (j < mg ? j : j - mg);
-                        if (!valid || mode >= args.n) continue;
-                        const int64_t idx = (base + mode) * args.out_kr + (j < mg ? 0 : args.out_kcp) + be;
-                        store_operand2<PREC>(args.out_hi, args.out_lo, idx, a0, a1);
+                        if (i < n_ok) store_operand2<PREC>(args.out_hi, args.out_lo, idx, a0, a1);
+                        idx += 2 * args.out_kr;
                     }
                 }
             } else if (EPI == EPI_X) {
@@ -474,6 +529,103 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                     if (valid && (lane == 0 || prev != key) && dg != 0.0)
                         atomicAdd(&args.gacc[t * args.t_stride + args.nu0 + nu], dg);
                 }
+            } else if (EPI == EPI_GS) {
+                // EPI_G with the per-element weight e = |V|^2 x (decay + absorption weight) x the
+                // row factors kept: e adds to the linewidth of (q, nu) and, scaled by f'/f and
+                // f''/f when flushed, to the off-diagonal columns (q', nu') and (q'', nu'') of its
+                // row.  Column sums run over the rows of one band nu (a warp holds 32 rows (nu,
+                // nu'')) into s_a2; the row sums go to s_a3.
+                const int nu = row / args.n, n2i = row % args.n;
+                float f0 = 0.f, f2 = 0.f, nn2 = 0.f;
+                if (valid) {
+                    f0 = (float)args.freq[(int64_t)args.iq * args.n + args.nu0 + nu];
+                    f2 = (float)args.freq[(int64_t)q2 * args.n + n2i];
+                    nn2 = (float)args.nB[(int64_t)q2 * args.n + n2i];
+                }
+                const bool live = valid && f0 >= args.f_min && f2 >= args.f_min;
+                const bool gauss = args.shape == PHX_GAUSS;
+                const float a = -1.f / (args.sigma * args.sigma), h2 = 0.25f * args.sigma * args.sigma;
+                const float norm = gauss ? 0.56418958354775628f / args.sigma : 0.5f * args.sigma / 3.14159265358979f;
+                const float rowfac = live ? norm / (1558.5454565440389f * f0 * f2) : 0.0f;
+                const float d02 = f0 - f2, lim = args.window * args.sigma;
+                const float one_n2 = 1.f + nn2;
+                const int key = valid ? nu : -1 - lane;
+                const int slot = nu - (tile * kBoxRows) / args.n;
+                const bool uniform = __all_sync(0xffffffffu, key == __shfl_sync(0xffffffffu, key, 0));
+                // segment links of the column reduction (the same for every column)
+                unsigned seg = 0;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const int off = 1 << k;
+                    const int k2 = __shfl_down_sync(0xffffffffu, key, off);
+                    if (lane + off < 32 && k2 == key) seg |= 1u << k;
+                }
+                // every lane takes part in the shuffle (a full-mask shuffle that lane 0 skipped
+                // would wait for it forever)
+                const int prev_key = __shfl_up_sync(0xffffffffu, key, 1);
+                const bool head = lane == 0 || prev_key != key;
+                float gs = 0.f;
+                float vi[16], e[16];
+                for (int j0 = half * 16; j0 < mg; j0 += kStride) {
+                    tc::tmem_ld16(taddr + j0, v);
+                    tc::tmem_ld16(taddr + mg + j0, vi);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int j = m0 + j0 + i;
+                        const float f1 = s_f1[j], n1 = s_n1[j], if1 = s_if1[j];
+                        const float x = d02 - f1, y = d02 + f1;
+                        const float gd = fabsf(x) < lim ? (gauss ? __expf(a * x * x) : __frcp_rn(x * x + h2)) : 0.f;
+                        const float ga = fabsf(y) < lim ? (gauss ? __expf(a * y * y) : __frcp_rn(y * y + h2)) : 0.f;
+                        const float w = ((one_n2 + n1) * gd + 2.f * (n1 - nn2) * ga) * (if1 * rowfac);
+                        e[i] = fmaf(v[i], v[i], vi[i] * vi[i]) * w;
+                        gs += e[i];
+                    }
+                    if (uniform) {
+                        // one band nu across the warp: a halving exchange leaves lane l with the
+                        // warp sum of column l >> 1 after 16 shuffles
+                        float a8[8], a4[4], a2[2];
+                        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            a8[k] = (b4 ? e[k + 8] : e[k]) + __shfl_xor_sync(0xffffffffu, b4 ? e[k] : e[k + 8], 16);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            a4[k] = (b3 ? a8[k + 4] : a8[k]) + __shfl_xor_sync(0xffffffffu, b3 ? a8[k] : a8[k + 4], 8);
+#pragma unroll
+                        for (int k = 0; k < 2; ++k)
+                            a2[k] = (b2 ? a4[k + 2] : a4[k]) + __shfl_xor_sync(0xffffffffu, b2 ? a4[k] : a4[k + 2], 4);
+                        float a1 = (b1 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? a2[0] : a2[1], 2);
+                        a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+                        const int si = slot * mg + j0 + (lane >> 1);
+                        if (valid && (lane & 1) == 0 && a1 != 0.f) {
+                            if (si >= 0 && si < kG1Slots) atomicAdd(&s_a2[si], a1);
+                            else atomicExch(args.status, (int)PHX_ERR_INVALID);    // bounds self-check
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            float c = e[i];
+#pragma unroll
+                            for (int k = 0; k < 5; ++k) {
+                                const float o = __shfl_down_sync(0xffffffffu, c, 1 << k);
+                                if (seg & (1u << k)) c += o;
+                            }
+                            const int si = slot * mg + j0 + i;
+                            if (valid && head && c != 0.f) {
+                                if (si >= 0 && si < kG1Slots) atomicAdd(&s_a2[si], c);
+                                else atomicExch(args.status, (int)PHX_ERR_INVALID);
+                            }
+                        }
+                    }
+                }
+                if (gs != 0.f) atomicAdd(&s_a3[lgrp * 32 + lane], gs);
+                double dg = (double)gs;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const double og = __shfl_down_sync(0xffffffffu, dg, 1 << k);
+                    if (seg & (1u << k)) dg += og;
+                }
+                if (valid && head && dg != 0.0) atomicAdd(&args.gacc[args.nu0 + nu], dg);
             } else {
                 // row (nu, nu'') holds V[nu'] = [Re | Im]; weight and reduce over nu'
                 const int nu = row / args.n, n2i = row % args.n;
@@ -551,6 +703,45 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
             tc::tc_fence_before();
             tc::mbar_arrive(&tempty_bar[acc]);
             if (args.n_acc == 2) { acc ^= 1; if (acc == 0) acc_phase ^= 1; } else { acc_phase ^= 1; }
+            if (EPI == EPI_GS) {
+                // flush this tile's sums into the off-diagonal rows (FP32 atomics; every entry
+                // receives a few contributions) and clear the buffers for the next tile
+                epi_barrier(kEpiThreads);
+                const int row_a = tile * kBoxRows;
+                const int row_b = min(row_a + kBoxRows, args.rows) - 1;
+                const int nu_a = row_a / args.n, n_slots = row_b / args.n - nu_a + 1;
+                const int c1 = args.tr_code[q1], c2 = args.tr_code[q2];
+                for (int i = et; i < n_slots * mg && i < kG1Slots; i += kEpiThreads) {
+                    const float val = s_a2[i];
+                    if (val == 0.f) continue;
+                    s_a2[i] = 0.f;
+                    const int nl = nu_a + i / mg, m1 = m0 + i % mg;
+                    if (c1 == 0) continue;
+                    const int64_t gr = args.g1_row0 + nl, gc = (int64_t)(abs(c1) - 1) * args.n + m1;
+                    if (m1 >= args.n || gr >= args.g1_rows || gc >= args.g1_ld) {      // bounds self-check
+                        atomicExch(args.status, (int)PHX_ERR_INVALID);
+                        continue;
+                    }
+                    const double f0 = args.freq[(int64_t)args.iq * args.n + args.nu0 + nl];
+                    const double r = (c1 > 0 ? 1.0 : -1.0) * args.g1_scale * args.freq[(int64_t)q1 * args.n + m1] / f0;
+                    atomicAdd(&args.g1[gr * args.g1_ld + gc], (float)(r * val));
+                }
+                for (int i = et; i < kBoxRows; i += kEpiThreads) {
+                    const float val = s_a3[i];
+                    if (val == 0.f) continue;
+                    s_a3[i] = 0.f;
+                    const int rr = row_a + i, nl = rr / args.n, m2 = rr % args.n;
+                    if (c2 == 0) continue;
+                    const int64_t gr = args.g1_row0 + nl, gc = (int64_t)(abs(c2) - 1) * args.n + m2;
+                    if (gr >= args.g1_rows || gc >= args.g1_ld) {
+                        atomicExch(args.status, (int)PHX_ERR_INVALID);
+                        continue;
+                    }
+                    const double f0 = args.freq[(int64_t)args.iq * args.n + args.nu0 + nl];
+                    const double r = (c2 > 0 ? 1.0 : -1.0) * args.g1_scale * args.freq[(int64_t)q2 * args.n + m2] / f0;
+                    atomicAdd(&args.g1[gr * args.g1_ld + gc], (float)(r * val));
+                }
+            }
         }
     }
     __syncthreads();
@@ -924,7 +1115,7 @@ template <int PREC>
 phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcBuffers& B, const double* freq,
                       const double* evec, const double* nB, const int32_t* irr_host, int n_irr, const GammaParams& gp,
                       double* gacc, double* wacc, cudaStream_t s, int n_t = 0, int64_t nb_stride = 0,
-                      int64_t t_stride = 0) {
+                      int64_t t_stride = 0, const G1Target* g1 = nullptr) {
     const int n = P.n, nq = P.nq, kr = P.kr, kcp = P.kcp, kr_d = P.kr_d, kcp_d = P.kcp_d;
     const int np = P.np, mg = P.mg, Q = P.Q, qp_np = P.qp_np, n_nu = P.n_nu;
     const int64_t n2 = (int64_t)n * n;
@@ -981,6 +1172,13 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
     aB.m1 = f->mesh[0]; aB.m2 = f->mesh[1]; aB.m3 = f->mesh[2];
     aB.sigma = (float)gp.sigma; aB.window = (float)gp.window; aB.f_min = (float)gp.f_min; aB.shape = gp.shape;
     aB.n_t = n_t; aB.nb_stride = nb_stride; aB.t_stride = t_stride;
+    if (g1) {
+        // the column-sum buffer holds every band of q that a 128-row tile touches x one group
+        if ((int64_t)(127 / n + 2) * mg > kG1Slots)
+            return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "scattering rows: n = %d needs a larger tile buffer", n);
+        aB.g1 = (float*)g1->mat; aB.g1_ld = g1->ld; aB.tr_code = g1->tr_code; aB.g1_scale = g1->scale;
+        aB.g1_rows = (int64_t)n_irr * n;
+    }
 
     for (int si = 0; si < n_irr; ++si) {
         const int iq = irr_host[si];
@@ -1013,6 +1211,7 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
             aA.a_rows_per_problem = (int)ra; aA.out_rows_per_slot = (int)ra;
             aB.rows = (int)ra; aB.tiles = aA.tiles; aB.a_rows_per_problem = (int)ra;
             aB.nu0 = nu0;
+            aB.g1_row0 = (int64_t)si * n + nu0;
             for (int tq = 0; tq < P.n_tiles_q; ++tq) {
                 const int t0 = tq * Q, Qt = std::min(Q, nq - t0);
                 aD.b_base = tq;
@@ -1033,6 +1232,8 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
                 pp = phx_prof_begin(ctx, s);
                 if (n_t > 0)
                     PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_GT>(ctx, aB, P.stream_b, Qt, sms, s)));
+                else if (g1)
+                    PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_GS>(ctx, aB, P.stream_b, Qt, sms, s)));
                 else
                     PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_G>(ctx, aB, P.stream_b, Qt, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_GEMM_E1, fl_e, op_bytes * (double)Qt * ra * n);
@@ -1046,25 +1247,27 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
 template <int PREC>
 phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec, const double* nB,
                   const int32_t* irr_host, int n_irr, const GammaParams& gp, double* gacc, double* wacc,
-                  cudaStream_t s, int n_t = 0, int64_t nb_stride = 0, int64_t t_stride = 0) {
+                  cudaStream_t s, int n_t = 0, int64_t nb_stride = 0, int64_t t_stride = 0,
+                  const G1Target* g1 = nullptr) {
     TcPlan P;
     PHX_TRY(tc_plan(ctx, f, PREC, 0, &P));
     PHX_TRY(tc_prepare_fc3(ctx, const_cast<phx_fc3*>(f)));
     TcBuffers B;
     PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.bytes_e, P.bytes_p, P.nq, f->nnz, (int64_t)P.n * P.n, &B));
     return tc_enqueue<PREC>(ctx, P, f, B, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s, n_t, nb_stride,
-                            t_stride);
+                            t_stride, g1);
 }
 
 }  // namespace
 
 phx_status phx_gamma_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec, const double* nB,
                         const int32_t* irr_host, int n_irr, const GammaParams& gp, int prec, double* gacc,
-                        double* wacc, cudaStream_t s) {
+                        double* wacc, cudaStream_t s, const G1Target* g1) {
     if (ctx->cc_major != 10)
         return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path needs a Blackwell (sm_10x) device");
-    if (prec == PHX_BF16X3) return run_tc<P_BF16X3>(ctx, f, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s);
-    return run_tc<P_TF32>(ctx, f, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s);
+    if (g1 && wacc) return phx_set_error(ctx, PHX_ERR_INVALID, "scattering rows and WP2 in one pass");
+    if (prec == PHX_BF16X3) return run_tc<P_BF16X3>(ctx, f, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s, 0, 0, 0, g1);
+    return run_tc<P_TF32>(ctx, f, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s, 0, 0, 0, g1);
 }
 
 phx_status phx_gamma_tc_multi_t(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec,

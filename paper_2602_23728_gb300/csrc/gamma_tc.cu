@@ -711,35 +711,75 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                 const int row_b = min(row_a + kBoxRows, args.rows) - 1;
                 const int nu_a = row_a / args.n, n_slots = row_b / args.n - nu_a + 1;
                 const int c1 = args.tr_code[q1], c2 = args.tr_code[q2];
-                for (int i = et; i < n_slots * mg && i < kG1Slots; i += kEpiThreads) {
-                    const float val = s_a2[i];
-                    if (val == 0.f) continue;
-                    s_a2[i] = 0.f;
-                    const int nl = nu_a + i / mg, m1 = m0 + i % mg;
-                    if (c1 == 0) continue;
-                    const int64_t gr = args.g1_row0 + nl, gc = (int64_t)(abs(c1) - 1) * args.n + m1;
-                    if (m1 >= args.n || gr >= args.g1_rows || gc >= args.g1_ld) {      // bounds self-check
-                        atomicExch(args.status, (int)PHX_ERR_INVALID);
-                        continue;
+                if ((args.n & 3) == 0) {
+                    // four adjacent columns per thread: one 16-byte reduction (the row stride is a
+                    // multiple of 128 elements, mg of 16 and n of 4, so a group stays in one row)
+                    const double* fq0 = args.freq + (int64_t)args.iq * args.n + args.nu0;
+                    for (int i = 4 * et; i < n_slots * mg && i + 3 < kG1Slots; i += 4 * kEpiThreads) {
+                        const float4 val = make_float4(s_a2[i], s_a2[i + 1], s_a2[i + 2], s_a2[i + 3]);
+                        if (val.x == 0.f && val.y == 0.f && val.z == 0.f && val.w == 0.f) continue;
+                        s_a2[i] = s_a2[i + 1] = s_a2[i + 2] = s_a2[i + 3] = 0.f;
+                        const int nl = nu_a + i / mg, m1 = m0 + i % mg;
+                        if (c1 == 0) continue;
+                        const int64_t gr = args.g1_row0 + nl, gc = (int64_t)(abs(c1) - 1) * args.n + m1;
+                        if (m1 + 3 >= args.n || gr >= args.g1_rows || gc + 3 >= args.g1_ld) {   // bounds self-check
+                            atomicExch(args.status, (int)PHX_ERR_INVALID);
+                            continue;
+                        }
+                        const double r = (c1 > 0 ? 1.0 : -1.0) * args.g1_scale / fq0[nl];
+                        const double* f1 = args.freq + (int64_t)q1 * args.n + m1;
+                        atomicAdd(reinterpret_cast<float4*>(args.g1 + gr * args.g1_ld + gc),
+                                  make_float4((float)(r * f1[0] * val.x), (float)(r * f1[1] * val.y),
+                                              (float)(r * f1[2] * val.z), (float)(r * f1[3] * val.w)));
                     }
-                    const double f0 = args.freq[(int64_t)args.iq * args.n + args.nu0 + nl];
-                    const double r = (c1 > 0 ? 1.0 : -1.0) * args.g1_scale * args.freq[(int64_t)q1 * args.n + m1] / f0;
-                    atomicAdd(&args.g1[gr * args.g1_ld + gc], (float)(r * val));
-                }
-                for (int i = et; i < kBoxRows; i += kEpiThreads) {
-                    const float val = s_a3[i];
-                    if (val == 0.f) continue;
-                    s_a3[i] = 0.f;
-                    const int rr = row_a + i, nl = rr / args.n, m2 = rr % args.n;
-                    if (c2 == 0) continue;
-                    const int64_t gr = args.g1_row0 + nl, gc = (int64_t)(abs(c2) - 1) * args.n + m2;
-                    if (gr >= args.g1_rows || gc >= args.g1_ld) {
-                        atomicExch(args.status, (int)PHX_ERR_INVALID);
-                        continue;
+                    for (int i = 4 * et; i < kBoxRows; i += 4 * kEpiThreads) {
+                        const float4 val = make_float4(s_a3[i], s_a3[i + 1], s_a3[i + 2], s_a3[i + 3]);
+                        if (val.x == 0.f && val.y == 0.f && val.z == 0.f && val.w == 0.f) continue;
+                        s_a3[i] = s_a3[i + 1] = s_a3[i + 2] = s_a3[i + 3] = 0.f;
+                        const int rr = row_a + i, nl = rr / args.n, m2 = rr % args.n;
+                        if (c2 == 0) continue;
+                        const int64_t gr = args.g1_row0 + nl, gc = (int64_t)(abs(c2) - 1) * args.n + m2;
+                        if (m2 + 3 >= args.n || gr >= args.g1_rows || gc + 3 >= args.g1_ld) {
+                            atomicExch(args.status, (int)PHX_ERR_INVALID);
+                            continue;
+                        }
+                        const double r = (c2 > 0 ? 1.0 : -1.0) * args.g1_scale / fq0[nl];
+                        const double* f2 = args.freq + (int64_t)q2 * args.n + m2;
+                        atomicAdd(reinterpret_cast<float4*>(args.g1 + gr * args.g1_ld + gc),
+                                  make_float4((float)(r * f2[0] * val.x), (float)(r * f2[1] * val.y),
+                                              (float)(r * f2[2] * val.z), (float)(r * f2[3] * val.w)));
                     }
-                    const double f0 = args.freq[(int64_t)args.iq * args.n + args.nu0 + nl];
-                    const double r = (c2 > 0 ? 1.0 : -1.0) * args.g1_scale * args.freq[(int64_t)q2 * args.n + m2] / f0;
-                    atomicAdd(&args.g1[gr * args.g1_ld + gc], (float)(r * val));
+                } else {
+                    for (int i = et; i < n_slots * mg && i < kG1Slots; i += kEpiThreads) {
+                        const float val = s_a2[i];
+                        if (val == 0.f) continue;
+                        s_a2[i] = 0.f;
+                        const int nl = nu_a + i / mg, m1 = m0 + i % mg;
+                        if (c1 == 0) continue;
+                        const int64_t gr = args.g1_row0 + nl, gc = (int64_t)(abs(c1) - 1) * args.n + m1;
+                        if (m1 >= args.n || gr >= args.g1_rows || gc >= args.g1_ld) {      // bounds self-check
+                            atomicExch(args.status, (int)PHX_ERR_INVALID);
+                            continue;
+                        }
+                        const double f0 = args.freq[(int64_t)args.iq * args.n + args.nu0 + nl];
+                        const double r = (c1 > 0 ? 1.0 : -1.0) * args.g1_scale * args.freq[(int64_t)q1 * args.n + m1] / f0;
+                        atomicAdd(&args.g1[gr * args.g1_ld + gc], (float)(r * val));
+                    }
+                    for (int i = et; i < kBoxRows; i += kEpiThreads) {
+                        const float val = s_a3[i];
+                        if (val == 0.f) continue;
+                        s_a3[i] = 0.f;
+                        const int rr = row_a + i, nl = rr / args.n, m2 = rr % args.n;
+                        if (c2 == 0) continue;
+                        const int64_t gr = args.g1_row0 + nl, gc = (int64_t)(abs(c2) - 1) * args.n + m2;
+                        if (gr >= args.g1_rows || gc >= args.g1_ld) {
+                            atomicExch(args.status, (int)PHX_ERR_INVALID);
+                            continue;
+                        }
+                        const double f0 = args.freq[(int64_t)args.iq * args.n + args.nu0 + nl];
+                        const double r = (c2 > 0 ? 1.0 : -1.0) * args.g1_scale * args.freq[(int64_t)q2 * args.n + m2] / f0;
+                        atomicAdd(&args.g1[gr * args.g1_ld + gc], (float)(r * val));
+                    }
                 }
             }
         }
@@ -1017,9 +1057,11 @@ phx_status tc_plan(phx_ctx* ctx, const phx_fc3* f, int prec, int q_override, TcP
     P.nk_d = P.kr_d / kelems;
     // Working set: modes of q in chunks of n_nu (W of a chunk <= 1 GB; measured on GB300 at 96
     // modes, chunking for L2 residency loses more to launch count than it gains) and q' in
-    // tiles of Q (M and X of a tile together <= 920 MB: 64 q' at 96 modes, the best measured
-    // between 13 and 64; larger tiles re-read W fewer times).  PHX_NU_CHUNK / PHX_Q_TILE or
-    // the autotuner override the defaults.
+    // tiles of Q (M and X of a tile together <= 2.5 GB: 128 q' at 96 modes, the most the
+    // Fourier GEMM's double-buffered accumulator holds (2 x 256 of the 512 tensor-memory
+    // columns); each doubling of Q halves the re-reads of W, and 128 ran the whole step 9 %
+    // faster than 64 on GB300).  PHX_NU_CHUNK / PHX_Q_TILE or the autotuner override the
+    // defaults.
     const int64_t n2 = (int64_t)n * n;
     P.n_nu = (int)std::max<int64_t>(1, std::min<int64_t>(n, ((int64_t)1 << 30) / (n2 * P.kr_d * esz * planes)));
     if (const char* env = getenv("PHX_NU_CHUNK")) {
@@ -1027,7 +1069,7 @@ phx_status tc_plan(phx_ctx* ctx, const phx_fc3* f, int prec, int q_override, TcP
         if (v > 0) P.n_nu = std::min(v, n);
     }
     const int64_t per_qp = 2 * (int64_t)P.n_nu * n * P.kr * esz * planes;   // M + X of one q'
-    int Q = (int)std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)920 << 20) / per_qp));
+    int Q = (int)std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)2560 << 20) / per_qp));
     Q = std::min(Q, 128);
     if (const char* env = getenv("PHX_Q_TILE")) {
         const int v = atoi(env);

@@ -32,8 +32,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu capture summarised in
 # profiles/tc_gemm_fcc32_mesh8.md (same per-launch shape as the bench); valid for the kernel
 # source it was taken on
-DRAM_TRAFFIC_PER_LAUNCH = {("dft", "bf16x3"): 652861184, ("gemm_e2", "bf16x3"): 935205888,
-                           ("gemm_e1_gamma", "bf16x3"): 503074560}
+DRAM_TRAFFIC_PER_LAUNCH = {("dft", "bf16x3"): 1077664768, ("gemm_e2", "bf16x3"): 1801995776,
+                           ("gemm_e1_gamma", "bf16x3"): 946169344}
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
 
 
@@ -99,11 +99,11 @@ class ClockSampler:
 class Workload:
     """Inputs of the 32-atom / 8x8x8 workload, resident on the device."""
 
-    def __init__(self, phx, ctx, precision, device):
+    def __init__(self, phx, ctx, precision, device, mesh=(8, 8, 8)):
         import torch
         import phx_inputs as P
         self.torch = torch
-        self.w = w = P.fcc_massdisorder_32()
+        self.w = w = P.fcc_massdisorder_32(mesh=tuple(mesh))
         self.f2, f3 = w.ifc2(), w.ifc3()
         self.f2val = self.f2.val.reshape(-1, 9)
         c = w.crystal
@@ -728,7 +728,7 @@ def run_sc(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     ctx = phx.Context(0)
-    wl = Workload(phx, ctx, args.precision, dev)
+    wl = Workload(phx, ctx, args.precision, dev, mesh=(args.sc_mesh,) * 3)
     w, c = wl.w, wl.c
     n, nq = wl.n, wl.nq
     n_tr = len(wl.irr)
@@ -773,9 +773,9 @@ def run_sc(args):
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "kappa_rta_wmk": float(np.trace(kappa[0]) / 3), "kappa_sc_wmk": float(np.trace(kappa[-1]) / 3),
             "kappa_sc_diag_wmk": np.diag(kappa[-1]).tolist(), "iterations": iters, "converged": r["converged"],
-            "config": {"workload": "fcc32-massdis-mesh8 iterative BTE: 32-atom LJ fcc (masses 39.95/83.8 seed 2), "
-                                   "96 modes, 8x8x8, 50 K, Gauss 0.1 THz; Gamma1 over the 260 time-reversal "
-                                   "representatives (R = %d rows)" % R,
+            "config": {"workload": "fcc32-massdis-mesh%d iterative BTE: 32-atom LJ fcc (masses 39.95/83.8 seed 2), "
+                                   "96 modes, %dx%dx%d, 50 K, Gauss 0.1 THz; Gamma1 over the %d time-reversal "
+                                   "representatives (R = %d rows)" % ((args.sc_mesh,) * 4 + (n_tr, R)),
                        "triplets_per_step": trip, "sc_tol": args.sc_tol, "sc_max_iter": args.sc_iter,
                        "gamma1_bytes": R * ((R + 127) // 128 * 128) * (8 if args.precision == "fp64" else 4),
                        "inputs_vs_l2": "Gamma1 (2.5 GB FP32) and the contraction operands stream well over the "
@@ -861,6 +861,9 @@ def main():
                          "(each its own JSON line); fcc32-sc: the iterative BTE on the headline crystal")
     ap.add_argument("--sc-iter", type=int, default=100, help="fcc32-sc: maximum iterations")
     ap.add_argument("--sc-tol", type=float, default=1e-6, help="fcc32-sc: relative change of Tr(kappa)/3")
+    ap.add_argument("--sc-mesh", type=int, default=8,
+                    help="fcc32-sc: mesh edge (8 = the bench size; 4 keeps the per-launch shape of the "
+                         "contraction for profiler captures)")
     ap.add_argument("--irr-limit", type=int, default=0,
                     help="profiling aid: process only the first N irreducible q per step (0: all)")
     args = ap.parse_args()

@@ -51,7 +51,6 @@ constexpr size_t kSmemLimit = 232448;          // 227 KB opt-in
 // rows of Eq. (gamma1)
 enum { EPI_M = 0, EPI_X = 1, EPI_G = 2, EPI_GT = 3, EPI_GS = 4 };
 constexpr int kMaxT = 4;
-constexpr int kG1Slots = 768;     // EPI_GS column-sum buffer: (bands of q in a tile) x (modes of a group)
 enum { P_BF16X3 = 0, P_TF32 = 1 };
 
 struct TcArgs {
@@ -160,8 +159,7 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
     __shared__ volatile int abort_flag;
     __shared__ float s_f1[kMaxNp], s_n1[kMaxNp], s_if1[kMaxNp];
     __shared__ float s_n1t[EPI == EPI_GT ? kMaxT * kMaxNp : 1];
-    __shared__ float s_a2[EPI == EPI_GS ? kG1Slots : 1];      // column sums (q', nu') per band nu of q
-    __shared__ float s_a3[EPI == EPI_GS ? kBoxRows : 1];      // row sums (q'', nu'') per tile row
+    __shared__ float s_rows[EPI == EPI_GS ? 2 : 1][4][32];   // EPI_GS: part-1 row sums per lane group
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int np = args.np, mg = args.mg, NA = 2 * mg, nk = args.nk, stages = args.stages;
@@ -194,10 +192,6 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
         for (int pl = 0; pl < kPlanes; ++pl) { tc::prefetch_tmap(&args.a_map[pl]); tc::prefetch_tmap(&args.b_map[pl]); }
     }
     if (warp == 1) tc::tmem_alloc(&tmem_base_slot, args.tmem_cols);
-    if (EPI == EPI_GS) {
-        for (int i = threadIdx.x; i < kG1Slots; i += blockDim.x) s_a2[i] = 0.f;
-        for (int i = threadIdx.x; i < kBoxRows; i += blockDim.x) s_a3[i] = 0.f;
-    }
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem_base = tmem_base_slot;
@@ -532,13 +526,17 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
             } else if (EPI == EPI_GS) {
                 // EPI_G with the per-element weight e = |V|^2 x (decay + absorption weight) x the
                 // row factors kept: e adds to the linewidth of (q, nu) and, scaled by f'/f and
-                // f''/f when flushed, to the off-diagonal columns (q', nu') and (q'', nu'') of its
-                // row.  Column sums run over the rows of one band nu (a warp holds 32 rows (nu,
-                // nu'')) into s_a2; the row sums go to s_a3.
+                // f''/f, to the off-diagonal columns (q', nu') and (q'', nu'') of its row.  Column
+                // sums run over the rows of one band nu (a warp holds 32 rows (nu, nu'')) and go
+                // to Gamma1 from registers; the two warps of a lane group add their row sums
+                // through a shared slot and a pairwise barrier.  No CTA-wide barrier per tile.
+                static_assert(EPI != EPI_GS || kEpiParts == 2, "EPI_GS pairs the two warps of a lane group");
                 const int nu = row / args.n, n2i = row % args.n;
                 float f0 = 0.f, f2 = 0.f, nn2 = 0.f;
+                double f0d = 1.0;
                 if (valid) {
-                    f0 = (float)args.freq[(int64_t)args.iq * args.n + args.nu0 + nu];
+                    f0d = args.freq[(int64_t)args.iq * args.n + args.nu0 + nu];
+                    f0 = (float)f0d;
                     f2 = (float)args.freq[(int64_t)q2 * args.n + n2i];
                     nn2 = (float)args.nB[(int64_t)q2 * args.n + n2i];
                 }
@@ -550,9 +548,14 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                 const float d02 = f0 - f2, lim = args.window * args.sigma;
                 const float one_n2 = 1.f + nn2;
                 const int key = valid ? nu : -1 - lane;
-                const int slot = nu - (tile * kBoxRows) / args.n;
-                const bool uniform = __all_sync(0xffffffffu, key == __shfl_sync(0xffffffffu, key, 0));
-                // segment links of the column reduction (the same for every column)
+                const bool vec4 = (args.n & 3) == 0;       // groups of four adjacent entries stay in one row
+                const int c1 = args.tr_code[q1], c2 = args.tr_code[q2];
+                const double rs = args.g1_scale / f0d;     // Gamma1 scale over f of this row's band
+                const int64_t grow = (args.g1_row0 + nu) * args.g1_ld;
+                const bool row_ok = valid && args.g1_row0 + nu < args.g1_rows;
+                // all lanes take part in every shuffle and vote below (none sits behind a condition)
+                const int key0 = __shfl_sync(0xffffffffu, key, 0);
+                const bool uniform = __all_sync(0xffffffffu, valid && key == key0);
                 unsigned seg = 0;
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
@@ -560,8 +563,6 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                     const int k2 = __shfl_down_sync(0xffffffffu, key, off);
                     if (lane + off < 32 && k2 == key) seg |= 1u << k;
                 }
-                // every lane takes part in the shuffle (a full-mask shuffle that lane 0 skipped
-                // would wait for it forever)
                 const int prev_key = __shfl_up_sync(0xffffffffu, key, 1);
                 const bool head = lane == 0 || prev_key != key;
                 float gs = 0.f;
@@ -580,9 +581,10 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                         e[i] = fmaf(v[i], v[i], vi[i] * vi[i]) * w;
                         gs += e[i];
                     }
-                    if (uniform) {
-                        // one band nu across the warp: a halving exchange leaves lane l with the
-                        // warp sum of column l >> 1 after 16 shuffles
+                    if (uniform && vec4) {
+                        // one band across the warp: a halving exchange leaves lane l with the warp
+                        // sum of column l >> 1; lanes 8k then gather columns 4k .. 4k+3 and add
+                        // them to Gamma1 with one 16-byte reduction
                         float a8[8], a4[4], a2[2];
                         const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
 #pragma unroll
@@ -596,12 +598,27 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                             a2[k] = (b2 ? a4[k + 2] : a4[k]) + __shfl_xor_sync(0xffffffffu, b2 ? a4[k] : a4[k + 2], 4);
                         float a1 = (b1 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? a2[0] : a2[1], 2);
                         a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
-                        const int si = slot * mg + j0 + (lane >> 1);
-                        if (valid && (lane & 1) == 0 && a1 != 0.f) {
-                            if (si >= 0 && si < kG1Slots) atomicAdd(&s_a2[si], a1);
-                            else atomicExch(args.status, (int)PHX_ERR_INVALID);    // bounds self-check
+                        const int src = lane & ~7;
+                        const float g1v = __shfl_sync(0xffffffffu, a1, src + 2);
+                        const float g2v = __shfl_sync(0xffffffffu, a1, src + 4);
+                        const float g3v = __shfl_sync(0xffffffffu, a1, src + 6);
+                        const int col = m0 + j0 + 4 * (lane >> 3);
+                        if ((lane & 7) == 0 && row_ok && c1 != 0 && col < args.n &&
+                            (a1 != 0.f || g1v != 0.f || g2v != 0.f || g3v != 0.f)) {
+                            const int64_t gc = (int64_t)(abs(c1) - 1) * args.n + col;
+                            if (gc + 3 < args.g1_ld) {
+                                const double r = c1 > 0 ? rs : -rs;
+                                const double* f1 = args.freq + (int64_t)q1 * args.n + col;
+                                atomicAdd(reinterpret_cast<float4*>(args.g1 + grow + gc),
+                                          make_float4((float)(r * f1[0] * a1), (float)(r * f1[1] * g1v),
+                                                      (float)(r * f1[2] * g2v), (float)(r * f1[3] * g3v)));
+                            } else {
+                                atomicExch(args.status, (int)PHX_ERR_INVALID);   // bounds self-check
+                            }
                         }
                     } else {
+                        // segmented sums over the rows of each band in the warp; the first lane of
+                        // a segment adds it to Gamma1
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             float c = e[i];
@@ -610,15 +627,19 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                                 const float o = __shfl_down_sync(0xffffffffu, c, 1 << k);
                                 if (seg & (1u << k)) c += o;
                             }
-                            const int si = slot * mg + j0 + i;
-                            if (valid && head && c != 0.f) {
-                                if (si >= 0 && si < kG1Slots) atomicAdd(&s_a2[si], c);
-                                else atomicExch(args.status, (int)PHX_ERR_INVALID);
+                            const int col = m0 + j0 + i;
+                            if (row_ok && head && c != 0.f && c1 != 0 && col < args.n) {
+                                const int64_t gc = (int64_t)(abs(c1) - 1) * args.n + col;
+                                if (gc < args.g1_ld)
+                                    atomicAdd(args.g1 + grow + gc,
+                                              (float)((c1 > 0 ? rs : -rs) * args.freq[(int64_t)q1 * args.n + col] * c));
+                                else
+                                    atomicExch(args.status, (int)PHX_ERR_INVALID);
                             }
                         }
                     }
                 }
-                if (gs != 0.f) atomicAdd(&s_a3[lgrp * 32 + lane], gs);
+                // linewidth: segmented sums of this part's row sums
                 double dg = (double)gs;
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
@@ -626,6 +647,39 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                     if (seg & (1u << k)) dg += og;
                 }
                 if (valid && head && dg != 0.0) atomicAdd(&args.gacc[args.nu0 + nu], dg);
+                // column (q'', nu''): this row's sum over nu', the two parts added through a
+                // double-buffered slot (the pairwise barrier orders the write before the read and
+                // the read before the slot's reuse two items later)
+                const int buf = (it - item_begin) & 1;
+                if (half == 1) s_rows[buf][lgrp][lane] = gs;
+                asm volatile("bar.sync %0, 64;" ::"r"(2 + lgrp) : "memory");
+                if (half == 0) {
+                    const float tot = gs + s_rows[buf][lgrp][lane];
+                    if (vec4) {
+                        const float t1 = __shfl_down_sync(0xffffffffu, tot, 1);
+                        const float t2 = __shfl_down_sync(0xffffffffu, tot, 2);
+                        const float t3 = __shfl_down_sync(0xffffffffu, tot, 3);
+                        if ((lane & 3) == 0 && row_ok && c2 != 0 && (tot != 0.f || t1 != 0.f || t2 != 0.f || t3 != 0.f)) {
+                            const int64_t gc = (int64_t)(abs(c2) - 1) * args.n + n2i;
+                            if (gc + 3 < args.g1_ld) {
+                                const double r = c2 > 0 ? rs : -rs;
+                                const double* f2p = args.freq + (int64_t)q2 * args.n + n2i;
+                                atomicAdd(reinterpret_cast<float4*>(args.g1 + grow + gc),
+                                          make_float4((float)(r * f2p[0] * tot), (float)(r * f2p[1] * t1),
+                                                      (float)(r * f2p[2] * t2), (float)(r * f2p[3] * t3)));
+                            } else {
+                                atomicExch(args.status, (int)PHX_ERR_INVALID);
+                            }
+                        }
+                    } else if (row_ok && c2 != 0 && tot != 0.f) {
+                        const int64_t gc = (int64_t)(abs(c2) - 1) * args.n + n2i;
+                        if (gc < args.g1_ld)
+                            atomicAdd(args.g1 + grow + gc,
+                                      (float)((c2 > 0 ? rs : -rs) * args.freq[(int64_t)q2 * args.n + n2i] * tot));
+                        else
+                            atomicExch(args.status, (int)PHX_ERR_INVALID);
+                    }
+                }
             } else {
                 // row (nu, nu'') holds V[nu'] = [Re | Im]; weight and reduce over nu'
                 const int nu = row / args.n, n2i = row % args.n;
@@ -703,85 +757,6 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
             tc::tc_fence_before();
             tc::mbar_arrive(&tempty_bar[acc]);
             if (args.n_acc == 2) { acc ^= 1; if (acc == 0) acc_phase ^= 1; } else { acc_phase ^= 1; }
-            if (EPI == EPI_GS) {
-                // flush this tile's sums into the off-diagonal rows (FP32 atomics; every entry
-                // receives a few contributions) and clear the buffers for the next tile
-                epi_barrier(kEpiThreads);
-                const int row_a = tile * kBoxRows;
-                const int row_b = min(row_a + kBoxRows, args.rows) - 1;
-                const int nu_a = row_a / args.n, n_slots = row_b / args.n - nu_a + 1;
-                const int c1 = args.tr_code[q1], c2 = args.tr_code[q2];
-                if ((args.n & 3) == 0) {
-                    // four adjacent columns per thread: one 16-byte reduction (the row stride is a
-                    // multiple of 128 elements, mg of 16 and n of 4, so a group stays in one row)
-                    const double* fq0 = args.freq + (int64_t)args.iq * args.n + args.nu0;
-                    for (int i = 4 * et; i < n_slots * mg && i + 3 < kG1Slots; i += 4 * kEpiThreads) {
-                        const float4 val = make_float4(s_a2[i], s_a2[i + 1], s_a2[i + 2], s_a2[i + 3]);
-                        if (val.x == 0.f && val.y == 0.f && val.z == 0.f && val.w == 0.f) continue;
-                        s_a2[i] = s_a2[i + 1] = s_a2[i + 2] = s_a2[i + 3] = 0.f;
-                        const int nl = nu_a + i / mg, m1 = m0 + i % mg;
-                        if (c1 == 0) continue;
-                        const int64_t gr = args.g1_row0 + nl, gc = (int64_t)(abs(c1) - 1) * args.n + m1;
-                        if (m1 + 3 >= args.n || gr >= args.g1_rows || gc + 3 >= args.g1_ld) {   // bounds self-check
-                            atomicExch(args.status, (int)PHX_ERR_INVALID);
-                            continue;
-                        }
-                        const double r = (c1 > 0 ? 1.0 : -1.0) * args.g1_scale / fq0[nl];
-                        const double* f1 = args.freq + (int64_t)q1 * args.n + m1;
-                        atomicAdd(reinterpret_cast<float4*>(args.g1 + gr * args.g1_ld + gc),
-                                  make_float4((float)(r * f1[0] * val.x), (float)(r * f1[1] * val.y),
-                                              (float)(r * f1[2] * val.z), (float)(r * f1[3] * val.w)));
-                    }
-                    for (int i = 4 * et; i < kBoxRows; i += 4 * kEpiThreads) {
-                        const float4 val = make_float4(s_a3[i], s_a3[i + 1], s_a3[i + 2], s_a3[i + 3]);
-                        if (val.x == 0.f && val.y == 0.f && val.z == 0.f && val.w == 0.f) continue;
-                        s_a3[i] = s_a3[i + 1] = s_a3[i + 2] = s_a3[i + 3] = 0.f;
-                        const int rr = row_a + i, nl = rr / args.n, m2 = rr % args.n;
-                        if (c2 == 0) continue;
-                        const int64_t gr = args.g1_row0 + nl, gc = (int64_t)(abs(c2) - 1) * args.n + m2;
-                        if (m2 + 3 >= args.n || gr >= args.g1_rows || gc + 3 >= args.g1_ld) {
-                            atomicExch(args.status, (int)PHX_ERR_INVALID);
-                            continue;
-                        }
-                        const double r = (c2 > 0 ? 1.0 : -1.0) * args.g1_scale / fq0[nl];
-                        const double* f2 = args.freq + (int64_t)q2 * args.n + m2;
-                        atomicAdd(reinterpret_cast<float4*>(args.g1 + gr * args.g1_ld + gc),
-                                  make_float4((float)(r * f2[0] * val.x), (float)(r * f2[1] * val.y),
-                                              (float)(r * f2[2] * val.z), (float)(r * f2[3] * val.w)));
-                    }
-                } else {
-                    for (int i = et; i < n_slots * mg && i < kG1Slots; i += kEpiThreads) {
-                        const float val = s_a2[i];
-                        if (val == 0.f) continue;
-                        s_a2[i] = 0.f;
-                        const int nl = nu_a + i / mg, m1 = m0 + i % mg;
-                        if (c1 == 0) continue;
-                        const int64_t gr = args.g1_row0 + nl, gc = (int64_t)(abs(c1) - 1) * args.n + m1;
-                        if (m1 >= args.n || gr >= args.g1_rows || gc >= args.g1_ld) {      // bounds self-check
-                            atomicExch(args.status, (int)PHX_ERR_INVALID);
-                            continue;
-                        }
-                        const double f0 = args.freq[(int64_t)args.iq * args.n + args.nu0 + nl];
-                        const double r = (c1 > 0 ? 1.0 : -1.0) * args.g1_scale * args.freq[(int64_t)q1 * args.n + m1] / f0;
-                        atomicAdd(&args.g1[gr * args.g1_ld + gc], (float)(r * val));
-                    }
-                    for (int i = et; i < kBoxRows; i += kEpiThreads) {
-                        const float val = s_a3[i];
-                        if (val == 0.f) continue;
-                        s_a3[i] = 0.f;
-                        const int rr = row_a + i, nl = rr / args.n, m2 = rr % args.n;
-                        if (c2 == 0) continue;
-                        const int64_t gr = args.g1_row0 + nl, gc = (int64_t)(abs(c2) - 1) * args.n + m2;
-                        if (gr >= args.g1_rows || gc >= args.g1_ld) {
-                            atomicExch(args.status, (int)PHX_ERR_INVALID);
-                            continue;
-                        }
-                        const double f0 = args.freq[(int64_t)args.iq * args.n + args.nu0 + nl];
-                        const double r = (c2 > 0 ? 1.0 : -1.0) * args.g1_scale * args.freq[(int64_t)q2 * args.n + m2] / f0;
-                        atomicAdd(&args.g1[gr * args.g1_ld + gc], (float)(r * val));
-                    }
-                }
-            }
         }
     }
     __syncthreads();
@@ -1215,9 +1190,6 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
     aB.sigma = (float)gp.sigma; aB.window = (float)gp.window; aB.f_min = (float)gp.f_min; aB.shape = gp.shape;
     aB.n_t = n_t; aB.nb_stride = nb_stride; aB.t_stride = t_stride;
     if (g1) {
-        // the column-sum buffer holds every band of q that a 128-row tile touches x one group
-        if ((int64_t)(127 / n + 2) * mg > kG1Slots)
-            return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "scattering rows: n = %d needs a larger tile buffer", n);
         aB.g1 = (float*)g1->mat; aB.g1_ld = g1->ld; aB.tr_code = g1->tr_code; aB.g1_scale = g1->scale;
         aB.g1_rows = (int64_t)n_irr * n;
     }

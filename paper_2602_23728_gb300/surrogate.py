@@ -100,6 +100,16 @@ def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh,
     t0 = _timer(torch)
     model = ctx.mlp(4, width, depth, ensemble, seed)
     final_loss = model.train(Xf, yf, epochs, lr)
+    # a member whose final loss stays far above the others' has not converged (it would bias the
+    # ensemble mean and inflate its spread): train the ensemble again from another seed, twice
+    # at most
+    for retry in range(2):
+        fl = np.asarray(final_loss, dtype=np.float64)
+        if ensemble < 2 or fl.max() <= 4.0 * np.median(fl):
+            break
+        model.close()
+        model = ctx.mlp(4, width, depth, ensemble, seed + 1 + retry)
+        final_loss = model.train(Xf, yf, epochs, lr)
     t["train"] = _timer(torch) - t0
 
     t0 = _timer(torch)

@@ -807,6 +807,25 @@ def run_sc(args):
                 "frac": ach / peaks["hbm_gbs"]}
     roof.update({"traffic": None, "kernel": top, "peak_note": f"of {peak_src}"})
     line["roofline"] = roof
+    if args.kappa_fp64:
+        # the same BTE step with every contraction in FP64 (and once in TF32): the kappa error of
+        # each precision, RTA iterate and converged iterate
+        ref = {}
+        for prec in ("fp64", "tf32"):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rr = step(prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ref[prec] = (rr["kappa"], e0.elapsed_time(e1), rr["n_iter"])
+        k64 = ref["fp64"][0]
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        line["kappa_vs_fp64_path"] = {
+            "fp64_step_ms": ref["fp64"][1], "kappa_sc_fp64_wmk": float(np.trace(k64[-1]) / 3),
+            "fp64_iterations": ref["fp64"][2],
+            args.precision: {"kappa_rta_rel_err": rel(kappa[0], k64[0]), "kappa_sc_rel_err": rel(kappa[-1], k64[-1])},
+            "tf32": {"kappa_rta_rel_err": rel(ref["tf32"][0][0], k64[0]),
+                     "kappa_sc_rel_err": rel(ref["tf32"][0][-1], k64[-1]), "step_ms": ref["tf32"][1]}}
     if not args.no_cpu_baseline:
         # the oracle's scattering rows of one representative over a bounded q' sample
         f = wl.freq.cpu().numpy()

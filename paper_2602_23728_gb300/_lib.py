@@ -183,6 +183,13 @@ def make_cell(lattice, masses):
     return c, m
 
 
+def time_reversal_count(mesh):
+    """Number of orbits {q, -q} of a Gamma-centred mesh (the unknowns' q-points of
+    phx_kappa_sc): the points with q = -q mod G (k_i in {0, n_i/2}) plus half of the rest."""
+    n_self = int(np.prod([2 if int(k) % 2 == 0 else 1 for k in mesh]))
+    return (int(np.prod([int(k) for k in mesh])) + n_self) // 2
+
+
 def irreducible(mesh, rotations):
     """Irreducible set (host): returns irr, full_to_irr, weights as int32 arrays."""
     mesh_a = np.asarray(mesh, dtype=np.int32)
@@ -481,9 +488,7 @@ class Context:
         mfp [n_tr, n, 3], gamma1 [R, R] or None)."""
         br = Broadening(SHAPES[shape], float(sigma), float(window))
         cell, m = make_cell(lattice, masses)
-        mesh = fc3.mesh
-        n_self = int(np.prod([2 if k % 2 == 0 else 1 for k in mesh]))
-        n_tr = (int(np.prod(mesh)) + n_self) // 2
+        n_tr = time_reversal_count(fc3.mesh)
         R = n_tr * fc3.n
         if not _is_torch(freq):
             freq = _host(freq, np.float64)

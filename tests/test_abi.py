@@ -62,6 +62,16 @@ def test_irreducible_matches_oracle(phx, mesh, which):
     assert np.array_equal(wt, owt)
 
 
+@pytest.mark.parametrize("mesh", [(1, 1, 1), (2, 2, 2), (3, 3, 3), (4, 2, 2), (5, 4, 3), (8, 8, 8)])
+def test_time_reversal_count_sizes_the_bte_unknowns(phx, mesh):
+    """The binding sizes phx_kappa_sc's outputs by the number of orbits {q, -q}: equal to the
+    oracle's time-reversal set and to the library's irreducible set without rotations."""
+    irr, _, _ = O.bte.time_reversal_set(mesh)
+    lib_irr, _, _ = phx.irreducible(mesh, P.identity_rotation())
+    assert phx.time_reversal_count(mesh) == len(irr) == len(lib_irr)
+    assert np.array_equal(irr, lib_irr)
+
+
 def test_irreducible_rejects_incompatible_rotation(phx):
     rot = np.array([[[0, 1, 0], [1, 0, 0], [0, 0, 1]]], dtype=np.int32)   # swaps axes of a 4x6 mesh
     with pytest.raises(phx.PhxError):

@@ -343,7 +343,8 @@ phx_status phx_kappa_rta(phx_ctx* ctx, const phx_cell* cell, int32_t nq, int32_t
  *    and w f''/f at column (q'' = -q-q', nu''); a column of a point listed through -q is
  *    added with sign -1.  Gamma1 stays on the device, R x R in FP64 (prec = PHX_FP64) or
  *    FP32 (tensor-core precisions); inputs whose Gamma1 exceeds 96 GB return
- *    PHX_ERR_UNSUPPORTED.
+ *    PHX_ERR_UNSUPPORTED.  Its entries are accumulated with atomic adds (FP64 or FP32), so
+ *    two calls on the same inputs agree to rounding, not bit for bit.
  *  - Iteration (Eq. sc_iter) lambda^(k+1) = (v - Gamma1 lambda^(k)) / Gamma0 stops at the
  *    first k >= 1 with |Tr kappa^(k) - Tr kappa^(k-1)| < tol |Tr kappa^(k-1)| (*converged =
  *    1), or after max_iter iterations (*converged = 0).

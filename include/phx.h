@@ -116,7 +116,8 @@ phx_status phx_irreducible(const int32_t mesh[3], int32_t n_rot, const int32_t* 
 /* ---------------------------------------------------------------- harmonic
  * Eqs. (dynmat_reciprocal), (eigenvalue_crystal), (groupvel): for nq reduced q-points
  * q_frac[3*k..3*k+2] build D(q) = sum_R Phi2 exp(-2 pi i q.R)/sqrt(m m), diagonalise it in
- * FP64 (batched Jacobi on the GPU) and return
+ * FP64 on the GPU (batched Householder reduction + QL for n <= 96, cyclic Jacobi above) and
+ * return
  *   freq_thz[nq][n]     signed frequency sign(lambda) sqrt(|lambda|)/(2 pi)          [mem]
  *   evec[nq][n][n]      complex eigenvectors (layout and gauge above)                [mem]
  *   vel[nq][n][3]       Re<e|dD/dq|e>/(2w) with the analytic derivative (0 if f<=0)   [mem, may be NULL]
@@ -396,7 +397,7 @@ typedef enum {
     PHX_K_FOLD = 3,         /* Phi3 fold into the lattice-difference operand (S3)          */
     PHX_K_FP64_GEMM = 4,    /* FP64 complex GEMMs of the FP64 path                          */
     PHX_K_FP64_EPI = 5,     /* FP64 weight/reduction kernel                                 */
-    PHX_K_EIGEN = 6,        /* eigensolvers (batched Jacobi; large-cell tridiagonal path)   */
+    PHX_K_EIGEN = 6,        /* eigensolvers (batched Householder + QL or Jacobi)            */
     PHX_K_CELL_SPARSE = 7,  /* Gamma-only cell: W_a = F e_a and X_a = W_a E (CUDA cores)      */
     PHX_K_CELL_TRANSPOSE = 8, /* Gamma-only cell: operand layout transposes                   */
     PHX_K_CELL_GEMM = 9,    /* Gamma-only cell: E^T X_a tiles + fused role-weight epilogue   */

@@ -29,12 +29,95 @@ sys.path.insert(0, ROOT)
 METRIC = "phonon triplets/s (V3+gamma) on 1 GB300, mixed/batched vs FP64 path, at stated kappa error"
 UNIT = "triplets/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu capture summarised in
-# profiles/tc_gemm_fcc32_mesh8.md (same per-launch shape as the bench); valid for the kernel
-# source it was taken on
-DRAM_TRAFFIC_PER_LAUNCH = {("dft", "bf16x3"): 1077664768, ("gemm_e2", "bf16x3"): 1801995776,
-                           ("gemm_e1_gamma", "bf16x3"): 946169344}
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
+# kernel classes that run on the tensor cores (their recorded flops are algorithmic: 8 flops per
+# useful complex multiply-add, padding excluded)
+TENSOR_CLASSES = ("dft", "chain", "gemm_e2", "gemm_e1_gamma", "cell_gemm")
+# DRAM bytes per launch measured by ncu, with the hash of the CUDA sources they were taken on
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+KERNEL_SOURCES = ("chain_tc.cuh", "common.h", "gamma_common.cuh", "gamma_tc.cu", "tc_ptx.cuh")
+GOLDEN_KAPPA = os.path.join(ROOT, "tests", "golden", "fcc32_mesh8_kappa.txt")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2602_23728_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, precision, workload):
+    """ncu DRAM bytes per launch of a kernel class on a workload, or None when no capture was
+    taken on the current kernel sources."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    src = kernel_source_hash()
+    with open(TRAFFIC_FILE) as fh:
+        for line in fh:
+            f = line.split()
+            if len(f) == 5 and not line.startswith("#") and f[:3] == [workload, kernel, precision] and f[4] == src:
+                return float(f[3])
+    return None
+
+
+def tensor_peak(peaks, precision, sustained=True):
+    """Dense tensor peak in TFLOP/s of FP32-equivalent products for a precision (None for FP64)."""
+    bf16 = peaks.get("bf16_tflops_sustained" if sustained else "bf16_tflops", peaks.get("bf16_tflops"))
+    if precision == "bf16x3":
+        return bf16 / 3.0, "bf16 %s / 3 (three bf16 products per FP32-equivalent product)" % (
+            "sustained" if sustained else "burst")
+    if precision == "tf32":
+        return bf16 * NOMINAL_TF32_OVER_BF16, "bf16 %s x nominal tf32/bf16 (1.1/2.25)" % (
+            "sustained" if sustained else "burst")
+    return None, "FP64 CUDA-core path"
+
+
+def roofline_of(prof, steps, ms_step, precision, peaks, src, workload):
+    """Roofline of the kernel class with the most device time in a profiled pass of `steps`
+    steps: tensor-bound classes against the tensor peak of the precision (algorithmic flops),
+    with the HBM figure (algorithmic bytes over the copy bandwidth) as a second field."""
+    per = {k: v for k, v in prof.items() if k != "launches" and v[1] > 0}
+    if not per:
+        return None
+    name = max(per, key=lambda k: per[k][0])
+    tot_ms, nl, fl, by = per[name]
+    t = tot_ms / 1e3
+    peak, note = tensor_peak(peaks, precision)
+    hbm = {"achieved": by / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": by / t / 1e9 / peaks["hbm_gbs"], "bytes_per_launch": by / nl,
+           "peak_source": f"{src}: copy bandwidth"}
+    traffic = measured_traffic(name, precision, workload)
+    if name in TENSOR_CLASSES and peak:
+        ach = fl / t / 1e12
+        roof = {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": traffic, "peak_source": f"{src}: {note}", "hbm": hbm}
+    else:
+        roof = {"bound": "hbm", "kernel": name, "achieved": hbm["achieved"], "peak": hbm["peak"], "unit": "GB/s",
+                "frac": hbm["frac"], "traffic": traffic, "peak_source": hbm["peak_source"]}
+    roof.update({"algorithmic_flops_per_launch": fl / nl, "algorithmic_bytes_per_launch": by / nl,
+                 "launches_per_step": nl / steps, "avg_launch_ms": tot_ms / nl,
+                 "share_of_step": tot_ms / steps / ms_step})
+    return roof
+
+
+def golden_kappa(w, f2, f3):
+    """The oracle's RTA conductivity stored under tests/golden/ for this workload, or None."""
+    import phx_inputs as P
+    if not os.path.exists(GOLDEN_KAPPA):
+        return None
+    digest, kappa = None, None
+    with open(GOLDEN_KAPPA) as fh:
+        for line in fh:
+            if line.startswith("# inputs "):
+                digest = line.split()[2]
+            elif line.startswith("kappa "):
+                kappa = np.array([float(x) for x in line.split()[1:]]).reshape(3, 3)
+                break
+    if kappa is None or digest != P.workload_digest(w, f2, f3):
+        return None
+    return kappa
 
 
 def load_peaks():
@@ -104,7 +187,8 @@ class Workload:
         import phx_inputs as P
         self.torch = torch
         self.w = w = P.fcc_massdisorder_32(mesh=tuple(mesh))
-        self.f2, f3 = w.ifc2(), w.ifc3()
+        self.f2, self.f3 = w.ifc2(), w.ifc3()
+        f3 = self.f3
         self.f2val = self.f2.val.reshape(-1, 9)
         c = w.crystal
         self.c = c
@@ -319,7 +403,7 @@ def run_phx(args):
     trip = wl.triplets()
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ctx.profile_enable(True)
+    ctx.profile_enable(False)            # no per-launch events in the timed loop; zeroes the launch count
     with ClockSampler(local) as clk:
         barrier()
         ev0.record(stream)
@@ -327,12 +411,21 @@ def run_phx(args):
             wl.step()
         ev1.record(stream)
         barrier()
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
+    launches = ctx.profile_read()["launches"]
     ms = ev0.elapsed_time(ev1) / args.steps
     ms_max, trip_all = reduce_over_ranks(ms, trip, world, dist, device)
     value = trip_all / (ms_max / 1e3)
     kappa = wl.kappa.copy()
+    # per-kernel-class times from one separate step with events around every launch
+    ctx.profile_enable(True)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    wl.step()
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    ms_prof = pe0.elapsed_time(pe1)
 
     # end to end: the same step through the API with pinned host buffers
     bufs = wl.host_buffers()
@@ -346,39 +439,17 @@ def run_phx(args):
     e2e_ms, _ = reduce_over_ranks(e2e_ms, trip, world, dist, device)
     h2d, d2h = wl.host_bytes(bufs)
 
-    # roofline of the dominant kernel class, from events recorded around its launches; the
-    # bound follows from its algorithmic intensity against the measured ridge point
+    # roofline of the kernel class with the most device time (events of the profiled step)
     peaks, src = load_peaks()
-    gemms = {k: prof[k] for k in ("dft", "gemm_e2", "gemm_e1_gamma", "fp64_gemm") if prof[k][1] > 0}
-    roof = None
-    if gemms:
-        name = max(gemms, key=lambda k: gemms[k][0])
-        tot_ms, nl, fl, by = gemms[name]
-        bf16_sus = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        if args.precision == "bf16x3":
-            peak, note = bf16_sus / 3.0, "bf16 sustained / 3 (three bf16 products per FP32-equivalent product)"
-        elif args.precision == "tf32":
-            peak, note = bf16_sus * NOMINAL_TF32_OVER_BF16, "bf16 sustained x nominal tf32/bf16 (1.1/2.25)"
-        else:
-            peak, note = None, "FP64 CUDA-core path"
-        ridge = peak * 1e12 / (peaks["hbm_gbs"] * 1e9) if peak else None      # flop per byte
-        intensity = fl / by if by > 0 else None
-        t = tot_ms / 1e3
-        traffic = DRAM_TRAFFIC_PER_LAUNCH.get((name, args.precision))
-        if ridge is not None and intensity is not None and intensity < ridge:
-            achieved = by / t / 1e9
-            roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                    "peak_source": f"{src}: copy bandwidth", "tensor_frac": fl / t / 1e12 / peak}
-        else:
-            achieved = fl / t / 1e12
-            roof = {"bound": "tensor", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": (achieved / peak) if peak else None, "traffic": traffic,
-                    "peak_source": f"{src}: {note}"}
-        roof.update({"algorithmic_bytes_per_launch": by / nl, "algorithmic_flops_per_launch": fl / nl,
-                     "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
-                     "launches_per_step": nl / args.steps, "avg_launch_ms": tot_ms / nl,
-                     "share_of_step": tot_ms / args.steps / ms})
+    roof = roofline_of(prof, 1, ms_prof, args.precision, peaks, src, "fcc32")
+    # the whole step's contraction: 16 n flops per triplet (two complex contractions of n terms,
+    # 8 flops per complex multiply-add) over the step time, against the same tensor peak
+    peak_t, _ = tensor_peak(peaks, args.precision)
+    step_fl = 16.0 * wl.n * trip
+    step_contraction = {"flops_per_step": step_fl, "achieved": step_fl / (ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                        "frac": (step_fl / (ms / 1e3) / 1e12 / peak_t) if peak_t else None}
+    k_ref = golden_kappa(wl.w, wl.f2, wl.f3)
+    kappa_err = float(np.linalg.norm(kappa - k_ref) / np.linalg.norm(k_ref)) if k_ref is not None else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
@@ -389,10 +460,15 @@ def run_phx(args):
                        "eigenvector tables 75 MB per step)", "parallelism": f"replicas x{world}"},
             "e2e": {"value": trip_all / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": int(prof["launches"]),
+            "gpu_launches": int(launches),
             "roofline": roof,
+            "step_contraction": step_contraction,
             "kappa_wmk": [kappa[0, 0], kappa[1, 1], kappa[2, 2]],
-            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if k != "launches" and v[1] > 0}}
+            "kappa_rel_err_vs_oracle": kappa_err,
+            "kappa_error_note": "Frobenius-relative error of this step's RTA kappa against the FP64 oracle's "
+                                "(all 260 irreducible q, stored under tests/golden/ with a digest of the inputs)",
+            "kernel_ms_per_step": {k: v[0] for k, v in prof.items() if k != "launches" and v[1] > 0},
+            "profiled_step_ms": ms_prof}
     clocks = clk.summary()
     if clocks:
         line["clocks"] = clocks
@@ -634,7 +710,7 @@ def run_cell(args):
     n_live = int((freq[0] >= w.f_min_thz).sum().item())
     trip = n_live * n * n
     stream = torch.cuda.current_stream()
-    ctx.profile_enable(True)
+    ctx.profile_enable(False)            # no per-launch events in the timed loop; zeroes the launch count
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         torch.cuda.synchronize()
@@ -644,10 +720,12 @@ def run_cell(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
+    launches = ctx.profile_read()["launches"]
+    ctx.profile_enable(True)             # one separate step with events around every launch
     kappa_q = step(args.precision)
     torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
     g_mixed = gam.cpu().numpy().copy()
     f_h = freq[0].cpu().numpy()
     e_h = evec[0].cpu().numpy()
@@ -663,7 +741,7 @@ def run_cell(args):
     rel = float((np.abs(g_mixed - g64)[big] / g64[big]).max())
     peaks, peak_src = load_peaks()
     per = {k: v for k, v in prof.items() if k != "launches" and v[1] > 0}
-    ms_k = {k: v[0] / args.steps for k, v in per.items()}
+    ms_k = {k: v[0] for k, v in per.items()}
     top = max(("cell_sparse", "cell_gemm", "cell_transpose"), key=lambda k: ms_k.get(k, 0.0))
     ms_top, n_top, fl_top, by_top = per[top]
     if top == "cell_gemm":
@@ -699,7 +777,7 @@ def run_cell(args):
                                        "of several GB: each step streams well over the 129 MB L2"},
             "roofline": roof,
             "fp64_gpu_path": {"value": trip / (ms64 / 1e3), "ms": ms64, "gamma_rel_err_vs_fp64": rel},
-            "kernel_ms_per_step": ms_k, "gpu_launches": int(prof["launches"]), "setup_s": t_setup}
+            "kernel_ms_per_step": ms_k, "gpu_launches": int(launches), "setup_s": t_setup}
     if not args.no_cpu_baseline:
         modes = [int(np.nonzero(f_h >= 0.5)[0][0]), int(np.argmax(f_h > 1.0))]
         t0 = time.perf_counter()
@@ -750,7 +828,7 @@ def run_sc(args):
     torch.cuda.synchronize()
     trip = wl.triplets()
     stream = torch.cuda.current_stream()
-    ctx.profile_enable(True)
+    ctx.profile_enable(False)            # no per-launch events in the timed loop; zeroes the launch count
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     iters = []
     with ClockSampler(0) as clk:
@@ -762,11 +840,15 @@ def run_sc(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
+    launches = ctx.profile_read()["launches"]
+    ctx.profile_enable(True)             # one separate step with events around every launch
+    r = step(args.precision)
+    torch.cuda.synchronize()
     prof = ctx.profile_read()
     ctx.profile_enable(False)
     peaks, peak_src = load_peaks()
     per = {k: v for k, v in prof.items() if k != "launches" and v[1] > 0}
-    ms_k = {k: v[0] / args.steps for k, v in per.items()}
+    ms_k = {k: v[0] for k, v in per.items()}
     kappa = r["kappa"]
     line = {"metric": METRIC, "value": trip / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -780,7 +862,7 @@ def run_sc(args):
                        "gamma1_bytes": R * ((R + 127) // 128 * 128) * (8 if args.precision == "fp64" else 4),
                        "inputs_vs_l2": "Gamma1 (2.5 GB FP32) and the contraction operands stream well over the "
                                        "129 MB L2 every pass"},
-            "kernel_ms_per_step": ms_k, "gpu_launches": int(prof["launches"])}
+            "kernel_ms_per_step": ms_k, "gpu_launches": int(launches)}
     if "sc_step" in per:
         ms_s, n_s, fl_s, by_s = per["sc_step"]
         ach = by_s / (ms_s / 1e3) / 1e9
@@ -788,25 +870,7 @@ def run_sc(args):
                                     "frac": ach / peaks["hbm_gbs"], "launches": n_s, "traffic": None,
                                     "kernel": "sc_step_kernel",
                                     "peak_note": f"of {peak_src} copy bandwidth"}
-    top = max(per, key=lambda k: per[k][0])
-    ms_t, n_t, fl_t, by_t = per[top]
-    if top in ("dft", "gemm_e2", "gemm_e1_gamma"):
-        peak_t = peaks["bf16_tflops_sustained"] / 3.0 if args.precision == "bf16x3" else \
-            peaks["bf16_tflops_sustained"] * NOMINAL_TF32_OVER_BF16
-        ridge = peak_t * 1e12 / (peaks["hbm_gbs"] * 1e9)
-        if fl_t / max(by_t, 1.0) >= ridge:
-            ach = fl_t / (ms_t / 1e3) / 1e12
-            roof = {"bound": "tensor", "achieved": ach, "peak": peak_t, "unit": "TFLOP/s", "frac": ach / peak_t}
-        else:
-            ach = by_t / (ms_t / 1e3) / 1e9
-            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"]}
-    else:
-        ach = by_t / (ms_t / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"]}
-    roof.update({"traffic": None, "kernel": top, "peak_note": f"of {peak_src}"})
-    line["roofline"] = roof
+    line["roofline"] = roofline_of(prof, 1, ms, args.precision, peaks, peak_src, "fcc32-sc")
     if args.kappa_fp64:
         # the same BTE step with every contraction in FP64 (and once in TF32): the kappa error of
         # each precision, RTA iterate and converged iterate

@@ -101,6 +101,23 @@ const char* phx_last_error(const phx_ctx* ctx);
 /* Library version string, e.g. "phx 1.0 sm_103a". */
 const char* phx_version(void);
 
+/* Per-context options (no counterpart in the paper; they select among equivalent kernels
+ * or bound the device waits):
+ *   PHX_OPT_CHAIN: which kernel runs the two eigenvector contractions of the tensor-core
+ *     linewidth path (Eq. (phi3_proj)): 0 = automatic (the chained kernel, which keeps the
+ *     intermediate X in tensor memory, for 64 < n <= 96 modes; otherwise two GEMMs with X
+ *     in device memory), 1 = the chained kernel wherever it fits (n <= 96), 2 = never.  The
+ *     multi-temperature and scattering-row passes always use the two GEMMs.
+ *   PHX_OPT_WAIT_LIMIT_NS: bound of every device barrier wait of the tensor-core kernels
+ *     (default 2e9 ns); a wait that runs out makes the kernel retire and the call return
+ *     PHX_ERR_TIMEOUT (host-memory calls; device-memory calls leave the status to the next
+ *     host-memory call on the context).
+ *   PHX_OPT_STARVE: test hook; nonzero makes the tensor-core kernels' load producers issue
+ *     nothing, so the first barrier wait runs out with no copy or MMA in flight.
+ * Errors: PHX_ERR_INVALID for an unknown option or a value out of range. */
+typedef enum { PHX_OPT_CHAIN = 0, PHX_OPT_WAIT_LIMIT_NS = 1, PHX_OPT_STARVE = 2 } phx_option;
+phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value);
+
 /* ---------------------------------------------------------------- grid (host only)
  * Irreducible set of a Gamma-centred mesh n1 x n2 x n3 (flat index (k1*n2+k2)*n3+k3)
  * under n_rot integer rotations (rot[9*r + 3*row + col], acting on reduced q) plus time
@@ -406,7 +423,8 @@ typedef enum {
     PHX_K_EIG_BACK = 12,    /* large-cell eigensolver: back-transformation + output          */
     PHX_K_EIG_BISECT = 13,  /* large-cell eigensolver: Sturm multisection (eigenvalues)      */
     PHX_K_SC_STEP = 14,     /* iterative BTE: one Gamma1 x mean-free-path pass (HBM-bound)   */
-    PHX_K_COUNT = 15
+    PHX_K_CHAIN = 15,       /* chained e_q'' and e_q' contractions + fused weights (one kernel) */
+    PHX_K_COUNT = 16
 } phx_kernel_class;
 
 /* Turn profiling on (1) or off (0); turning it on clears the counters.  Off by default. */

@@ -95,6 +95,8 @@ lib.phx_kappa_sc.argtypes = [_P, C.POINTER(Cell), _P, _P, _P, _P, C.c_double, Br
                              C.c_double, _P, _P, _P, _P, _P, _P, _I, _P]
 lib.phx_kappa_sc.restype = C.c_int
 
+lib.phx_set_option.argtypes = [_P, _I, C.c_int64]
+lib.phx_set_option.restype = C.c_int
 lib.phx_profile_enable.argtypes = [_P, _I]
 lib.phx_profile_enable.restype = C.c_int
 lib.phx_profile_read.argtypes = [_P, _I, _P, _P, _P, _P]
@@ -127,9 +129,11 @@ lib.phx_mlp_predict.restype = C.c_int
 
 KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4, "fp64_epilogue": 5,
            "eigensolver": 6, "cell_sparse": 7, "cell_transpose": 8, "cell_gemm": 9, "eig_tridiag": 10,
-           "eig_vectors": 11, "eig_back": 12, "eig_bisect": 13, "sc_step": 14}
+           "eig_vectors": 11, "eig_back": 12, "eig_bisect": 13, "sc_step": 14, "chain": 15}
 
-EXPORTED = ["phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
+OPTIONS = {"chain": 0, "wait_limit_ns": 1, "starve": 2}
+
+EXPORTED = ["phx_set_option", "phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
             "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_isotope", "phx_kappa_qhgk", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta", "phx_kappa_sc",
             "phx_kappa_rta_noalloc", "phx_gamma_batched", "phx_features", "phx_mlp_create", "phx_mlp_destroy",
             "phx_mlp_num_params", "phx_mlp_get_params", "phx_mlp_set_params", "phx_mlp_loss_grad", "phx_mlp_train",
@@ -267,6 +271,11 @@ class Context:
             pass
 
     # ------------------------------------------------------------------ profiling
+    def set_option(self, name, value):
+        """Context option: 'chain' (0 auto, 1 chained kernel wherever it fits, 2 never),
+        'wait_limit_ns' (bound of every device barrier wait), 'starve' (test hook)."""
+        self._check(lib.phx_set_option(self.h, OPTIONS[name], int(value)))
+
     def profile_enable(self, on=True):
         self._check(lib.phx_profile_enable(self.h, 1 if on else 0))
 

@@ -185,6 +185,26 @@ static void prof_collect(phx_ctx* ctx) {
     ctx->recs.clear();
 }
 
+phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value) {
+    if (!ctx) return PHX_ERR_INVALID;
+    switch (option) {
+        case PHX_OPT_CHAIN:
+            if (value < 0 || value > 2) return phx_set_error(ctx, PHX_ERR_INVALID, "PHX_OPT_CHAIN %lld", (long long)value);
+            ctx->opt_chain = (int)value;
+            return PHX_OK;
+        case PHX_OPT_WAIT_LIMIT_NS:
+            if (value < 1000 || value > 60000000000ll)
+                return phx_set_error(ctx, PHX_ERR_INVALID, "PHX_OPT_WAIT_LIMIT_NS %lld outside [1e3, 6e10]", (long long)value);
+            ctx->opt_wait_ns = (unsigned long long)value;
+            return PHX_OK;
+        case PHX_OPT_STARVE:
+            ctx->opt_starve = value != 0;
+            return PHX_OK;
+        default:
+            return phx_set_error(ctx, PHX_ERR_INVALID, "unknown option %d", option);
+    }
+}
+
 phx_status phx_profile_enable(phx_ctx* ctx, int32_t on) {
     if (!ctx) return PHX_ERR_INVALID;
     cudaSetDevice(ctx->device);

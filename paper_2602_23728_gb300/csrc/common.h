@@ -50,6 +50,10 @@ struct phx_ctx {
     std::vector<uint8_t> graph_key;
     int64_t graph_launches = 0;
     std::map<std::vector<int>, int> tune_q;
+    // options (phx_set_option)
+    int opt_chain = 0;                            // 0 auto, 1 force the chained kernel, 2 never
+    unsigned long long opt_wait_ns = 2000000000ull;   // bound of every device barrier wait
+    int opt_starve = 0;                           // test hook: tensor-core producers issue nothing
 };
 
 // Profiling helpers: begin returns a record slot (or -1 when profiling is off).

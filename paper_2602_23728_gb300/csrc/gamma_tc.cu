@@ -97,6 +97,8 @@ struct TcArgs {
     int64_t g1_row0;            // row of (this q, band nu0)
     const int32_t* tr_code;
     double g1_scale;
+    unsigned long long wait_ns; // bound of every barrier wait
+    int starve;                 // test hook: the producer issues nothing (waits then run out)
 };
 
 template <int PREC>
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
 
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
-        if (lane == 0) {
+        if (lane == 0 && !args.starve) {
             int stage = 0;
             uint32_t phase = 0;
             bool pending[kMaxStages];
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                 const int brow = (args.b_idx ? args.b_idx[p] : args.b_base) * (2 * np) + g * mg;
                 if (!kStreamB && p != cur_p) {
                     // a new problem: wait until the MMAs using the previous B have completed
-                    if (n_loaded > 0 && !tc::mbar_wait(&bempty_bar, (n_loaded - 1) & 1, &abort_flag)) {
+                    if (n_loaded > 0 && !tc::mbar_wait(&bempty_bar, (n_loaded - 1) & 1, &abort_flag, args.wait_ns)) {
                         abort_flag = 1;
                         atomicExch(args.status, (int)PHX_ERR_TIMEOUT);
                         break;
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                 }
                 const int arow = p * args.a_rows_per_problem + tile * kBoxRows;
                 for (int kc = 0; kc < nk; ++kc) {
-                    if (!tc::mbar_wait(&empty_bar[stage], phase ^ 1, &abort_flag)) {
+                    if (!tc::mbar_wait(&empty_bar[stage], phase ^ 1, &abort_flag, args.wait_ns)) {
                         abort_flag = 1;
                         atomicExch(args.status, (int)PHX_ERR_TIMEOUT);
                         break;
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                     if (pending[s]) {
                         const uint64_t t0 = tc::global_ns();
                         while (!tc::mbar_try_wait(&full_bar[s], pend_phase[s]) &&
-                               tc::global_ns() - t0 < tc::kWaitLimitNs) {
+                               tc::global_ns() - t0 < args.wait_ns) {
                         }
                     }
             }
@@ -275,20 +277,20 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                 const int p = it / per_p;
                 if (!kStreamB && p != cur_p) {
                     if (cur_p >= 0) tc::mma_commit(&bempty_bar);       // B free once these MMAs finish
-                    if (!tc::mbar_wait(&bfull_bar, n_bloads & 1, &abort_flag)) {
+                    if (!tc::mbar_wait(&bfull_bar, n_bloads & 1, &abort_flag, args.wait_ns)) {
                         abort_flag = 1; atomicExch(args.status, (int)PHX_ERR_TIMEOUT); break;
                     }
                     tc::tc_fence_after();
                     ++n_bloads;
                     cur_p = p;
                 }
-                if (!tc::mbar_wait(&tempty_bar[acc], acc_phase ^ 1, &abort_flag)) {
+                if (!tc::mbar_wait(&tempty_bar[acc], acc_phase ^ 1, &abort_flag, args.wait_ns)) {
                     abort_flag = 1; atomicExch(args.status, (int)PHX_ERR_TIMEOUT); break;
                 }
                 tc::tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(acc * NA);
                 for (int kc = 0; kc < nk; ++kc) {
-                    if (!tc::mbar_wait(&full_bar[stage], phase, &abort_flag)) {
+                    if (!tc::mbar_wait(&full_bar[stage], phase, &abort_flag, args.wait_ns)) {
                         abort_flag = 1; atomicExch(args.status, (int)PHX_ERR_TIMEOUT); ok = false; break;
                     }
                     tc::tc_fence_after();
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
             // every MMA of this thread has completed once drain_bar flips
             tc::mma_commit(&drain_bar);
             const uint64_t t0 = tc::global_ns();
-            while (!tc::mbar_try_wait(&drain_bar, 0) && tc::global_ns() - t0 < tc::kWaitLimitNs) {
+            while (!tc::mbar_try_wait(&drain_bar, 0) && tc::global_ns() - t0 < args.wait_ns) {
             }
         }
     } else {
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
         for (int it = item_begin; it < item_end; ++it) {
             const int p = it / per_p, tile = (it % per_p) / args.n_groups, g = it % args.n_groups;
             const int m0 = g * mg;                        // first output mode of this column group
-            const bool ok = tc::mbar_wait(&tfull_bar[acc], acc_phase, &abort_flag);
+            const bool ok = tc::mbar_wait(&tfull_bar[acc], acc_phase, &abort_flag, args.wait_ns);
             if (!ok) {
                 abort_flag = 1;
                 atomicExch(args.status, (int)PHX_ERR_TIMEOUT);
@@ -766,7 +768,30 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
     }
 }
 
+#include "chain_tc.cuh"
+
 // ---------------------------------------------------------------- operand preparation kernels
+
+// Eigenvector row table of every mesh point for the chained kernel: row (q, j) = [Re e_q(k, j)
+// (k < kcp) | Im e_q(k, j)], zero for k >= n.
+template <int PREC>
+__global__ void prep_evec_rows(const double2* __restrict__ evec, int nq, int n, int kcp, void* hi, void* lo) {
+    const int kr = 2 * kcp;
+    const int64_t total = (int64_t)nq * n * kr;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int kk = (int)(t % kr);
+        const int64_t row = t / kr;
+        const int j = (int)(row % n);
+        const int64_t q = row / n;
+        const int k = kk < kcp ? kk : kk - kcp;
+        float val = 0.f;
+        if (k < n) {
+            const double2 e = evec[(q * n + k) * n + j];
+            val = (float)(kk < kcp ? e.x : e.y);
+        }
+        store_operand<PREC>(hi, lo, t, val);
+    }
+}
 
 // B tables of the eigenvectors of every mesh point: rows [Re out (np) | Im out (np)], K =
 // [Re e(c) (Kcp) | Im e(c) (Kcp)] (see the header comment for the signs).
@@ -959,6 +984,21 @@ cudaError_t launch_gemm(phx_ctx* ctx, TcArgs& a, int n_problems, int ctas, cudaS
     return cudaGetLastError();
 }
 
+template <int PREC>
+cudaError_t launch_chain(ChainArgs& a, size_t smem, int ctas, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(chain_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(kSmemLimit - 8192));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (a.n_items <= 0) return cudaSuccess;
+    dim3 grid((unsigned)std::min(a.n_items, ctas), 1);
+    chain_kernel<PREC><<<grid, kChainThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int PREC, int EPI>
 cudaError_t launch_gemm_any(phx_ctx* ctx, TcArgs& a, bool stream_b, int n_problems, int ctas, cudaStream_t s) {
     return stream_b ? launch_gemm<PREC, EPI, true>(ctx, a, n_problems, ctas, s)
@@ -994,11 +1034,37 @@ struct TcPlan {
     int kcp_d = 0, kr_d = 0, nk_d = 0, st_d = 0;   // Fourier GEMM
     int n_nu = 0, Q = 0, qp_np = 0, n_tiles_q = 0;
     int64_t rows_w = 0, rows_a = 0;
+    // chained eigenvector contractions (chain_kernel) instead of the e_q'' and e_q' GEMMs
+    bool chain = false;
+    int c_ra = 0, c_rb3 = 0, c_stages = 0;
+    size_t c_smem = 0;
     // workspace bytes per operand plane
-    size_t bytes_w = 0, bytes_m = 0, bytes_e = 0, bytes_p = 0;
+    size_t bytes_w = 0, bytes_m = 0, bytes_e = 0, bytes_p = 0, bytes_t = 0;
 };
 
-phx_status tc_plan(phx_ctx* ctx, const phx_fc3* f, int prec, int q_override, TcPlan* pl) {
+// Shapes of the chained kernel for n <= 96 modes (K half kcp): tensor memory holds D2 (2 kcp
+// columns) and D3 (Re | Im of all rb3 = n rounded to 16 partner modes); shared memory holds the
+// two eigenvector tables and every M chunk of one item (stages >= nk).
+bool chain_shapes(TcPlan& P) {
+    if (P.kcp > 96 || P.n > 96) return false;
+    const int planes = P.prec == P_BF16X3 ? 2 : 1;
+    P.c_rb3 = round_up(P.n, 16);
+    P.c_ra = round_up(P.n, 8);
+    const size_t fixed = (size_t)planes * P.nk * kChunkBytes * (P.c_ra + P.c_rb3);
+    const size_t stage = (size_t)planes * P.kcp * kChunkBytes;
+    const size_t avail = kSmemLimit - 8192 - 1024;
+    if (P.nk > kMaxStages || fixed + (size_t)P.nk * stage > avail) return false;
+    P.c_stages = (int)std::min<size_t>(kMaxStages, (avail - fixed) / stage);
+    P.c_smem = 1024 + fixed + (size_t)P.c_stages * stage;
+    // the stage-2 MMA reads 128 rows from every A block (rows >= ra land in the next block and
+    // only feed output rows that are discarded): that read must stay inside the allocation
+    const size_t a_read_end = 1024 + (size_t)(planes * P.nk - 1) * P.c_ra * kChunkBytes + 128 * kChunkBytes;
+    if (a_read_end > P.c_smem) P.c_smem = a_read_end;
+    if (P.c_smem > kSmemLimit - 8192) return false;
+    return true;
+}
+
+phx_status tc_plan(phx_ctx* ctx, const phx_fc3* f, int prec, int q_override, TcPlan* pl, bool allow_chain = true) {
     TcPlan P;
     P.prec = prec;
     const int n = f->n, nq = f->nq;
@@ -1066,6 +1132,15 @@ phx_status tc_plan(phx_ctx* ctx, const phx_fc3* f, int prec, int q_override, TcP
     P.bytes_m = (size_t)Q * P.rows_a * P.kr * esz;
     P.bytes_e = (size_t)nq * 2 * P.np * P.kr * esz;
     P.bytes_p = (size_t)P.n_tiles_q * 2 * P.qp_np * P.kr_d * esz;
+    // Chained contractions: by default where they beat the three-GEMM chain (64 < n <= 96: the
+    // MMA rows are modes, so small n would leave most of the 128 rows idle); PHX_OPT_CHAIN
+    // forces them on (any n they fit) or off.
+    const int oc = ctx->opt_chain;
+    if (allow_chain && oc != 2 && (oc == 1 || (n > 64 && n <= 96))) P.chain = chain_shapes(P);
+    if (P.chain) {
+        P.bytes_t = (size_t)nq * n * P.kr * esz;
+        P.bytes_e = 0;
+    }
     *pl = P;
     return PHX_OK;
 }
@@ -1098,15 +1173,15 @@ phx_status tc_prepare_fc3(phx_ctx* ctx, phx_fc3* f) {
 }
 
 struct TcBuffers {
-    Operand W, M, X, E, P;
+    Operand W, M, X, E, P, T;
     int32_t* qpp = nullptr;
     float2* wph = nullptr;
     float2* eqf = nullptr;
 };
 
 // Workspace large enough for the given byte counts (per plane) and element counts.
-phx_status tc_alloc(phx_ctx* ctx, int prec, size_t bw, size_t bm, size_t be, size_t bp, int64_t max_nq,
-                    int64_t max_nnz, int64_t max_n2, TcBuffers* b) {
+phx_status tc_alloc(phx_ctx* ctx, int prec, size_t bw, size_t bm, size_t bx, size_t be, size_t bp, size_t bt,
+                    int64_t max_nq, int64_t max_nnz, int64_t max_n2, TcBuffers* b) {
     const int planes = prec == P_BF16X3 ? 2 : 1;
     auto get = [&](const char* name, size_t bytes, Operand* o) -> bool {
         std::string nh = std::string(name) + ".hi", nl = std::string(name) + ".lo";
@@ -1114,8 +1189,8 @@ phx_status tc_alloc(phx_ctx* ctx, int prec, size_t bw, size_t bm, size_t be, siz
         o->lo = planes == 2 ? phx_ws(ctx, nl.c_str(), bytes) : nullptr;
         return o->hi && (planes == 1 || o->lo);
     };
-    if (!get("tc.W", bw, &b->W) || !get("tc.M", bm, &b->M) || !get("tc.X", bm, &b->X) || !get("tc.E", be, &b->E) ||
-        !get("tc.P", bp, &b->P))
+    if (!get("tc.W", bw, &b->W) || !get("tc.M", bm, &b->M) || !get("tc.X", bx, &b->X) || !get("tc.E", be, &b->E) ||
+        !get("tc.P", bp, &b->P) || !get("tc.T", bt, &b->T))
         return PHX_ERR_NOMEM;
     b->qpp = (int32_t*)phx_ws(ctx, "tc.qpp", (size_t)max_nq * 4);
     b->wph = (float2*)phx_ws(ctx, "tc.wph", (size_t)std::max<int64_t>(max_nnz, 1) * sizeof(float2));
@@ -1142,10 +1217,13 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
     // padding columns of M, X and W must read as zero for this job's layout
     for (int pl = 0; pl < planes; ++pl) {
         PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.M.lo : B.M.hi, 0, P.bytes_m, s));
-        PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.X.lo : B.X.hi, 0, P.bytes_m, s));
+        if (!P.chain) PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.X.lo : B.X.hi, 0, P.bytes_m, s));
         PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.W.lo : B.W.hi, 0, P.bytes_w, s));
     }
-    prep_evec_tables<PREC><<<2048, 256, 0, s>>>((const double2*)evec, nq, n, np, kcp, B.E.hi, B.E.lo);
+    if (P.chain)
+        prep_evec_rows<PREC><<<2048, 256, 0, s>>>((const double2*)evec, nq, n, kcp, B.T.hi, B.T.lo);
+    else
+        prep_evec_tables<PREC><<<2048, 256, 0, s>>>((const double2*)evec, nq, n, np, kcp, B.E.hi, B.E.lo);
     PHX_CUDA_CHECK(ctx, cudaGetLastError());
     prep_phase_tables<PREC><<<256, 256, 0, s>>>(f->d_int, f->n_d, f->mesh[0], f->mesh[1], f->mesh[2], Q,
                                                 P.n_tiles_q, qp_np, kcp_d, B.P.hi, B.P.lo);
@@ -1153,22 +1231,40 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
     ctx->launches += 2;
 
     TcArgs aD{}, aA{}, aB{};
+    ChainArgs aC{};
     const int64_t m_rows = (int64_t)Q * P.rows_a;
     for (int pl = 0; pl < planes; ++pl) {
         const void* w = pl ? B.W.lo : B.W.hi;
         const void* m = pl ? B.M.lo : B.M.hi;
-        const void* x = pl ? B.X.lo : B.X.hi;
-        const void* e = pl ? B.E.lo : B.E.hi;
         const void* ph = pl ? B.P.lo : B.P.hi;
         bool ok = make_map(&aD.a_map[pl], w, PREC, P.rows_w, kr_d, kBoxRows) &&
-                  make_map(&aD.b_map[pl], ph, PREC, (int64_t)P.n_tiles_q * 2 * qp_np, kr_d, qp_np) &&
-                  make_map(&aA.a_map[pl], m, PREC, m_rows, kr, kBoxRows) &&
-                  make_map(&aA.b_map[pl], e, PREC, (int64_t)nq * 2 * np, kr, mg) &&
-                  make_map(&aB.a_map[pl], x, PREC, m_rows, kr, kBoxRows) &&
-                  make_map(&aB.b_map[pl], e, PREC, (int64_t)nq * 2 * np, kr, mg);
+                  make_map(&aD.b_map[pl], ph, PREC, (int64_t)P.n_tiles_q * 2 * qp_np, kr_d, qp_np);
+        if (P.chain) {
+            const void* t = pl ? B.T.lo : B.T.hi;
+            ok = ok && make_map(&aC.ta_map[pl], t, PREC, (int64_t)nq * n, kr, P.c_ra) &&
+                 make_map(&aC.tb_map[pl], t, PREC, (int64_t)nq * n, kr, P.c_rb3) &&
+                 make_map(&aC.m_map[pl], m, PREC, m_rows, kr, kcp);
+        } else {
+            const void* x = pl ? B.X.lo : B.X.hi;
+            const void* e = pl ? B.E.lo : B.E.hi;
+            ok = ok && make_map(&aA.a_map[pl], m, PREC, m_rows, kr, kBoxRows) &&
+                 make_map(&aA.b_map[pl], e, PREC, (int64_t)nq * 2 * np, kr, mg) &&
+                 make_map(&aB.a_map[pl], x, PREC, m_rows, kr, kBoxRows) &&
+                 make_map(&aB.b_map[pl], e, PREC, (int64_t)nq * 2 * np, kr, mg);
+        }
         if (!ok) return phx_set_error(ctx, PHX_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
     const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
+    const unsigned long long wait_ns = ctx->opt_wait_ns;
+    const int starve = ctx->opt_starve;
+    aD.wait_ns = aA.wait_ns = aB.wait_ns = aC.wait_ns = wait_ns;
+    aD.starve = aA.starve = aB.starve = aC.starve = starve;
+    if (P.chain) {
+        aC.n = n; aC.kcp = kcp; aC.nkc = P.nk; aC.ra = P.c_ra; aC.rb3 = P.c_rb3; aC.stages = P.c_stages;
+        aC.freq = freq; aC.nB = nB;
+        aC.sigma = (float)gp.sigma; aC.window = (float)gp.window; aC.f_min = (float)gp.f_min; aC.shape = gp.shape;
+        aC.status = (int32_t*)ctx->status_word;
+    }
     aD.np = qp_np; aD.mg = qp_np; aD.n_groups = 1; aD.nk = P.nk_d; aD.stages = P.st_d;
     aD.n_acc = (4 * qp_np <= 512) ? 2 : 1;
     aD.tmem_cols = tmem_cols_for(2 * qp_np, aD.n_acc);
@@ -1207,6 +1303,7 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
         aB.iq = iq;
         aB.gacc = gacc + (int64_t)si * n;
         aB.wacc = wacc ? wacc + (int64_t)si * n : nullptr;
+        aC.iq = iq; aC.gacc = aB.gacc; aC.wacc = aB.wacc;
         for (int nu0 = 0; nu0 < n; nu0 += n_nu) {
             const int nnu = std::min(n_nu, n - nu0);
             const int64_t rw = (int64_t)nnu * n2, ra = (int64_t)nnu * n;
@@ -1237,6 +1334,16 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
                 int pp = phx_prof_begin(ctx, s);
                 PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_M, false>(ctx, aD, 1, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_DFT, fl_d, op_bytes * ((double)rw * f->n_d + (double)Qt * ra * n));
+                if (P.chain) {
+                    aC.n_items = Qt * nnu; aC.nnu = nnu; aC.rows_per_slot = (int)ra;
+                    aC.qpp = B.qpp + t0; aC.t0 = t0; aC.nu0 = nu0;
+                    pp = phx_prof_begin(ctx, s);
+                    PHX_CUDA_CHECK(ctx, launch_chain<PREC>(aC, P.c_smem, sms, s));
+                    // two contractions; bytes: the M operand read once
+                    phx_prof_end(ctx, pp, s, PHX_K_CHAIN, 2.0 * fl_e, op_bytes * (double)Qt * ra * n);
+                    ctx->launches += 2;
+                    continue;
+                }
                 aA.b_idx = B.qpp + t0;
                 pp = phx_prof_begin(ctx, s);
                 PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_X>(ctx, aA, P.stream_b, Qt, sms, s)));
@@ -1264,10 +1371,11 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
                   cudaStream_t s, int n_t = 0, int64_t nb_stride = 0, int64_t t_stride = 0,
                   const G1Target* g1 = nullptr) {
     TcPlan P;
-    PHX_TRY(tc_plan(ctx, f, PREC, 0, &P));
+    PHX_TRY(tc_plan(ctx, f, PREC, 0, &P, n_t == 0 && g1 == nullptr));   // chained kernel: plain linewidths only
     PHX_TRY(tc_prepare_fc3(ctx, const_cast<phx_fc3*>(f)));
     TcBuffers B;
-    PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.bytes_e, P.bytes_p, P.nq, f->nnz, (int64_t)P.n * P.n, &B));
+    PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.chain ? 0 : P.bytes_m, P.bytes_e, P.bytes_p, P.bytes_t, P.nq,
+                     f->nnz, (int64_t)P.n * P.n, &B));
     return tc_enqueue<PREC>(ctx, P, f, B, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s, n_t, nb_stride,
                             t_stride, g1);
 }
@@ -1320,7 +1428,8 @@ phx_status autotune_q(phx_ctx* ctx, const phx_job& job, cudaStream_t s, int* bes
         if (P.Q == last_q) continue;                 // clamped to the mesh size already tried
         last_q = P.Q;
         TcBuffers B;
-        PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.bytes_e, P.bytes_p, P.nq, f->nnz, (int64_t)P.n * P.n, &B));
+        PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.chain ? 0 : P.bytes_m, P.bytes_e, P.bytes_p, P.bytes_t, P.nq,
+                     f->nnz, (int64_t)P.n * P.n, &B));
         float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {
             PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_in, s));
@@ -1368,19 +1477,20 @@ phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, const phx_
         PHX_TRY(tc_plan(ctx, jb.fc3, PREC, q, &plans[j]));
     }
     // workspace for the largest job, allocated before any capture
-    size_t bw = 0, bm = 0, be = 0, bp = 0;
+    size_t bw = 0, bm = 0, bx = 0, be = 0, bp = 0, bt = 0;
     int64_t mnq = 1, mnnz = 1, mn2 = 1, mnb = 1, mg = 1;
     for (int j = 0; j < n_jobs; ++j) {
         const TcPlan& P = plans[j];
         bw = std::max(bw, P.bytes_w); bm = std::max(bm, P.bytes_m); be = std::max(be, P.bytes_e);
-        bp = std::max(bp, P.bytes_p);
+        bp = std::max(bp, P.bytes_p); bt = std::max(bt, P.bytes_t);
+        if (!P.chain) bx = std::max(bx, P.bytes_m);
         mnq = std::max<int64_t>(mnq, P.nq); mnnz = std::max<int64_t>(mnnz, jobs[j].fc3->nnz);
         mn2 = std::max<int64_t>(mn2, (int64_t)P.n * P.n);
         mnb = std::max<int64_t>(mnb, (int64_t)P.nq * P.n);
         mg = std::max<int64_t>(mg, (int64_t)jobs[j].n_irr * P.n);
     }
     TcBuffers B;
-    PHX_TRY(tc_alloc(ctx, PREC, bw, bm, be, bp, mnq, mnnz, mn2, &B));
+    PHX_TRY(tc_alloc(ctx, PREC, bw, bm, bx, be, bp, bt, mnq, mnnz, mn2, &B));
     double* nB = (double*)phx_ws(ctx, "b.nB", (size_t)mnb * 8);
     double* gacc = (double*)phx_ws(ctx, "b.gacc", (size_t)mg * 8);
     double* acc9 = (double*)phx_ws(ctx, "b.acc9", (size_t)n_jobs * 9 * 8);

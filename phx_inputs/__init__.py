@@ -338,6 +338,22 @@ class Workload:
         return ifc3_lj(self.crystal, self.pot)
 
 
+def workload_digest(w: Workload, f2: IFC2, f3: IFC3) -> str:
+    """Short SHA-256 over the arrays and scalars that define a workload (IFC entries, masses,
+    lattice, mesh, temperature, broadening): a stored result made from these inputs carries
+    it, and a reader compares it with the digest of its own inputs before using the result."""
+    import hashlib
+    h = hashlib.sha256()
+    c = w.crystal
+    for a in (np.asarray(f2.idx, np.int64), np.asarray(f2.val, np.float64), np.asarray(f3.idx, np.int64),
+              np.asarray(f3.val, np.float64), np.asarray(c.masses, np.float64), np.asarray(c.lattice, np.float64),
+              np.asarray(w.mesh, np.int64),
+              np.asarray([w.temperature, w.sigma_thz, w.window, w.f_min_thz], np.float64)):
+        h.update(np.ascontiguousarray(a).tobytes())
+    h.update(w.shape.encode())
+    return h.hexdigest()[:16]
+
+
 def fcc_monatomic_5() -> Workload:
     """1-atom fcc LJ argon, 5x5x5 mesh, 30 K, Gaussian sigma 0.1 THz, O_h symmetry."""
     c = fcc_primitive()

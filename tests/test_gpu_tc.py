@@ -113,3 +113,38 @@ def test_tc_large_cells_streamed_b(ctx, phx, mult, prec):
     print(f"{prec}: {3 * c.n_atoms} modes gamma max rel err {_err(g, go):.3e}")
     assert go.max() > 0
     assert _err(g, go) < TOL[prec]
+
+
+@pytest.mark.parametrize("kind", ["fcc1", "two_atom"])
+@pytest.mark.parametrize("chain", [1, 2])
+def test_tc_kappa_rta_within_bar(ctx, phx, kind, chain):
+    """Eq. (rta) from BF16x3 linewidths against the same conductivity from the FP64 oracle's
+    linewidths on the same eigenvectors and velocity products: relative error <= 1e-5
+    (Frobenius norm of the 3x3 tensor), through both tensor-core contraction kernels."""
+    if kind == "fcc1":
+        w = P.fcc_monatomic_5()
+        c, mesh, T, sig, rot = w.crystal, w.mesh, w.temperature, w.sigma_thz, w.rotations
+        f2, f3 = w.ifc2(), w.ifc3()
+    else:
+        c0 = P.fcc_primitive_multiple(5.26, (2, 1, 1))
+        c = P.Crystal(c0.lattice, c0.positions, np.array([39.95, 83.8]))
+        mesh, T, sig, rot = (3, 4, 5), 45.0, 0.15, P.identity_rotation()
+        pot = P.LennardJones()
+        f2, f3 = P.ifc2_lj(c, pot), P.ifc3_lj(c, pot)
+    q = O.grid.mesh_qred(mesh)
+    freq, evec, _, vv = ctx.harmonic(c.lattice, c.masses, f2.idx, f2.val.reshape(-1, 9), q, want_vel=False,
+                                     want_vv=True)
+    irr, f2i, _ = phx.irreducible(mesh, rot)
+    h = ctx.fc3(c.lattice, c.masses, f3.idx, f3.val, mesh)
+    ctx.set_option("chain", chain)
+    g = ctx.gamma(h, freq, evec, irr, T, "gauss", sig, precision="bf16x3")
+    ctx.set_option("chain", 0)
+    gf = ctx.unfold(freq, irr, g, f2i)
+    K = ctx.kappa_rta(c.lattice, c.masses, freq, gf, T, vv=vv)
+    fc3 = O.anharmonic.FC3(f3.idx, f3.val, c.masses)
+    go = O.anharmonic.gamma(fc3, mesh, freq, evec, irr, T, "gauss", sig)
+    go = np.array([O.anharmonic.degenerate_average(freq[i], go[s]) for s, i in enumerate(irr)])
+    Ko = O.transport.kappa_rta_vv(freq, vv, O.transport.unfold(go, f2i), T, c.volume)
+    err = float(np.linalg.norm(K - Ko) / np.linalg.norm(Ko))
+    print(f"{kind} chain={chain}: BF16x3 kappa rel err {err:.3e}")
+    assert err <= 1e-5

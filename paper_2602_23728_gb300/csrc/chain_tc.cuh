@@ -41,7 +41,7 @@ struct ChainArgs {
     int nkc;                    // 128-byte K chunks per operand row and plane
     int ra;                     // rows of the stage-2 A block in shared memory (n rounded to 8)
     int rb3;                    // rows of the stage-3 B block = partner modes per MMA (n rounded to 16)
-    int stages;                 // M chunk ring (>= nkc)
+    int stages;                 // M chunk ring: stages / nkc item slots of nkc chunks (>= 1)
     int n_items;                // q' slots x bands of this launch (slot-major)
     int nnu;                    // bands nu per slot
     int rows_per_slot;          // rows of M per q' slot
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
     __shared__ __align__(8) uint64_t a2_full, a2_empty, b3_full, b3_empty;
-    __shared__ __align__(8) uint64_t d2_full[2], a3_ready[2], d2_free, d3_full, d3_empty, drain_bar;
+    __shared__ __align__(8) uint64_t d2_full[2], a3_ready[2], s3_done, d3_empty, drain_bar;
     __shared__ uint32_t tmem_base_slot;
     __shared__ volatile int abort_flag;
     __shared__ float s_f1[kMaxNp], s_n1[kMaxNp], s_if1[kMaxNp];
@@ -83,8 +83,10 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
     const uint32_t blk_m = (uint32_t)kcp * kChunkBytes;
     uint8_t* sA2 = smem;                                       // [plane][chunk][ra rows][128 B]
     uint8_t* sB3 = sA2 + (size_t)kPlanes * nkc * blk_a;        // [plane][chunk][rb3 rows][128 B]
-    uint8_t* sB2 = sB3 + (size_t)kPlanes * nkc * blk_b;        // [stage][plane][kcp rows][128 B]
+    uint8_t* sB2 = sB3 + (size_t)kPlanes * nkc * blk_b;        // [slot][chunk][plane][kcp rows][128 B]
     const uint32_t stage_bytes = kPlanes * blk_m;
+    const uint32_t slot_bytes = (uint32_t)nkc * stage_bytes;
+    const int n_slots = stages / nkc;                          // items of M in flight
     const int hs = kcp * (PREC == P_BF16X3 ? 2 : 4) / 32;      // 32-byte K steps per half
     const uint64_t wl = args.wait_ns;
 
@@ -94,12 +96,11 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
     const int L = item_end - item_begin;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < stages; ++s) { tc::mbar_init(&full_bar[s], 1); tc::mbar_init(&empty_bar[s], 1); }
+        for (int s = 0; s < n_slots; ++s) { tc::mbar_init(&full_bar[s], 1); tc::mbar_init(&empty_bar[s], 1); }
         tc::mbar_init(&a2_full, 1); tc::mbar_init(&a2_empty, 1);
         tc::mbar_init(&b3_full, 1); tc::mbar_init(&b3_empty, 1);
         for (int h = 0; h < 2; ++h) { tc::mbar_init(&d2_full[h], 1); tc::mbar_init(&a3_ready[h], kChainEpiThreads); }
-        tc::mbar_init(&d2_free, 1);
-        tc::mbar_init(&d3_full, 1); tc::mbar_init(&d3_empty, kChainEpiThreads);
+        tc::mbar_init(&s3_done, 1); tc::mbar_init(&d3_empty, kChainEpiThreads);
         tc::mbar_init(&drain_bar, 1);
         abort_flag = 0;
         tc::fence_mbar_init();
@@ -150,16 +151,16 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                     ++n_a2;
                 }
                 const int mrow = p * args.rows_per_slot + nu * n;
-                for (int c = 0; c < nkc; ++c) {
-                    if (!tc::mbar_wait(&empty_bar[stage], phase ^ 1, &abort_flag, wl)) { fail(); ok = false; break; }
-                    uint8_t* st = sB2 + (size_t)stage * stage_bytes;
-                    tc::mbar_expect_tx(&full_bar[stage], stage_bytes);
+                // every chunk of the item's M block into one slot (one barrier, one release)
+                if (!tc::mbar_wait(&empty_bar[stage], phase ^ 1, &abort_flag, wl)) { fail(); break; }
+                uint8_t* sl = sB2 + (size_t)stage * slot_bytes;
+                tc::mbar_expect_tx(&full_bar[stage], slot_bytes);
+                for (int c = 0; c < nkc; ++c)
                     for (int pl = 0; pl < kPlanes; ++pl)
-                        tc::tma_load_2d(st + (size_t)pl * blk_m, &args.m_map[pl], &full_bar[stage], c * kelems, mrow);
-                    pending[stage] = true; pend_phase[stage] = phase;
-                    if (++stage == stages) { stage = 0; phase ^= 1; }
-                }
-                if (!ok) break;
+                        tc::tma_load_2d(sl + (size_t)c * stage_bytes + (size_t)pl * blk_m, &args.m_map[pl], &full_bar[stage],
+                                        c * kelems, mrow);
+                pending[stage] = true; pend_phase[stage] = phase;
+                if (++stage == n_slots) { stage = 0; phase ^= 1; }
                 if (new_p) {
                     // stage-3 table of q' once the previous slot's stage-3 MMAs are done
                     if (n_b3 > 0 && !tc::mbar_wait(&b3_empty, (n_b3 - 1) & 1, &abort_flag, wl)) { fail(); break; }
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
             }
             if (abort_flag) {
                 // let loads already issued land before the CTA retires (bounded)
-                for (int s = 0; s < stages; ++s)
+                for (int s = 0; s < n_slots; ++s)
                     if (pending[s]) {
                         const uint64_t t0 = tc::global_ns();
                         while (!tc::mbar_try_wait(&full_bar[s], pend_phase[s]) && tc::global_ns() - t0 < wl) {
@@ -209,24 +210,15 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
             for (int li = 0; ok && li < L; ++li) {
                 const bool new_p = li == 0 || slot_of(li) != slot_of(li - 1);
                 const bool last_p = li + 1 == L || slot_of(li + 1) != slot_of(li);
-                // ---- stage 2: D2 = T[q''] M_nu^T; all M chunks of the item are resident (stages >= nkc)
+                // ---- stage 2: D2 = T[q''] M_nu^T from one slot holding every M chunk of the item
                 if (new_p && !tc::mbar_wait(&a2_full, n_a2++ & 1, &abort_flag, wl)) { ok = false; break; }
-                if (li > 0 && !tc::mbar_wait(&d2_free, (li - 1) & 1, &abort_flag, wl)) { ok = false; break; }
-                {
-                    int st = stage0;
-                    uint32_t ph = phase0;
-                    for (int c = 0; c < nkc; ++c) {
-                        if (!tc::mbar_wait(&full_bar[st], ph, &abort_flag, wl)) { ok = false; break; }
-                        if (++st == stages) { st = 0; ph ^= 1; }
-                    }
-                    if (!ok) break;
-                }
+                if (li > 0 && !tc::mbar_wait(&s3_done, (li - 1) & 1, &abort_flag, wl)) { ok = false; break; }
+                if (!tc::mbar_wait(&full_bar[stage0], phase0, &abort_flag, wl)) { ok = false; break; }
                 tc::tc_fence_after();
                 for (int part = 0; part < 2; ++part) {        // 0: Re outputs, 1: Im outputs
                     const uint32_t dd = d2 + (uint32_t)(part * kcp);
-                    int st = stage0;
                     for (int c = 0; c < nkc; ++c) {
-                        const uint64_t bb = b2d + ((uint32_t)st * stage_bytes >> 4);
+                        const uint64_t bb = b2d + (((uint32_t)stage0 * slot_bytes + (uint32_t)c * stage_bytes) >> 4);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             const int t = c * 4 + k;                      // K step of B (the M rows)
@@ -242,13 +234,11 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                                 tc::mma_tf32(dd, ah, bh, id, acc);
                             }
                         }
-                        if (part == 1) tc::mma_commit(&empty_bar[st]);
-                        if (++st == stages) st = 0;
                     }
                     tc::mma_commit(&d2_full[part]);
                 }
-                for (int c = 0; c < nkc; ++c)
-                    if (++stage0 == stages) { stage0 = 0; phase0 ^= 1; }
+                tc::mma_commit(&empty_bar[stage0]);
+                if (++stage0 == n_slots) { stage0 = 0; phase0 ^= 1; }
                 if (last_p) tc::mma_commit(&a2_empty);
                 // ---- stage 3: D3 = X^T T[q']^T, A from tensor memory, K halves as they are converted
                 if (new_p && !tc::mbar_wait(&b3_full, n_b3++ & 1, &abort_flag, wl)) { ok = false; break; }
@@ -278,8 +268,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                     }
                 }
                 if (!ok) break;
-                tc::mma_commit(&d3_full);
-                tc::mma_commit(&d2_free);
+                tc::mma_commit(&s3_done);           // D3 complete and the stage-3 A operand free
                 if (last_p) tc::mma_commit(&b3_empty);
             }
             if (!ok) fail();
@@ -366,7 +355,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
             const float inv_f02 = live ? 1.0f / (1558.5454565440389f * f0 * f2) : 0.0f;
             const float d02 = f0 - f2, one_n2 = 1.f + nn2;
             float gs = 0.f, ws = 0.f;
-            bool ok = tc::mbar_wait(&d3_full, li & 1, &abort_flag, wl);
+            bool ok = tc::mbar_wait(&s3_done, li & 1, &abort_flag, wl);
             ok = __all_sync(0xffffffffu, ok);
             if (ok) {
                 tc::tc_fence_after();

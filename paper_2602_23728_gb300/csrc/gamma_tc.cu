@@ -1054,7 +1054,8 @@ bool chain_shapes(TcPlan& P) {
     const size_t stage = (size_t)planes * P.kcp * kChunkBytes;
     const size_t avail = kSmemLimit - 8192 - 1024;
     if (P.nk > kMaxStages || fixed + (size_t)P.nk * stage > avail) return false;
-    P.c_stages = (int)std::min<size_t>(kMaxStages, (avail - fixed) / stage);
+    // whole items of M chunks (the kernel's ring holds stages / nk items)
+    P.c_stages = (int)std::min<size_t>(kMaxStages, (avail - fixed) / stage) / P.nk * P.nk;
     P.c_smem = 1024 + fixed + (size_t)P.c_stages * stage;
     // the stage-2 MMA reads 128 rows from every A block (rows >= ra land in the next block and
     // only feed output rows that are discarded): that read must stay inside the allocation

@@ -684,7 +684,7 @@ def run_cell(args):
     dev = torch.device("cuda", 0)
     ctx = phx.Context(0)
     t_setup = time.perf_counter()
-    w = P.gamma_disordered_1000()
+    w = P.gamma_disordered_1000(reps=(args.cell_reps,) * 3)
     c = w.crystal
     f2, f3 = P.ifc_lj_vectorised(c, w.pot)
     h = ctx.fc3(c.lattice, c.masses, f3.idx, f3.val, (1, 1, 1))
@@ -947,6 +947,9 @@ def main():
     ap.add_argument("--sc-mesh", type=int, default=8,
                     help="fcc32-sc: mesh edge (8 = the bench size; 4 keeps the per-launch shape of the "
                          "contraction for profiler captures)")
+    ap.add_argument("--cell-reps", type=int, default=10,
+                    help="cell1000: primitive cells per edge of the disordered cell (10 = the 1000-atom "
+                         "workload; 6 = a 216-atom cell of the same kind for profiler captures)")
     ap.add_argument("--irr-limit", type=int, default=0,
                     help="profiling aid: process only the first N irreducible q per step (0: all)")
     args = ap.parse_args()

@@ -323,6 +323,14 @@ phx_status phx_mlp_train(phx_mlp* m, const double* X, const double* y, int32_t r
 /* Ensemble mean and standard deviation of log(gamma) per row (device; stdv may be NULL). */
 phx_status phx_mlp_predict(phx_mlp* m, const double* X, int32_t rows, double* mean, double* stdv,
                            void* stream);
+/* Linewidths from a prediction, for rows grouped by irreducible q-point (n_groups groups of n
+ * rows, row = group * n + band): gamma[r] = exp(mean[r]) * wp2[r] (wp2 NULL: factor 1) where
+ * freq_thz[r] >= f_min_thz, else 0; score[g] (optional, needs stdv) = the largest stdv over
+ * the live rows of group g (0 if none), the ensemble-spread measure that picks the q-points
+ * sent back to the exact kernel.  Device arrays; enqueued on stream. */
+phx_status phx_mlp_reconstruct(phx_ctx* ctx, int32_t n_groups, int32_t n, const double* mean, const double* stdv,
+                               const double* wp2, const double* freq_thz, double f_min_thz, double* gamma,
+                               double* score, void* stream);
 
 /* ---------------------------------------------------------------- transport
  * Map irreducible linewidths to the full mesh (Sec. "Overview of New Capabilities"):

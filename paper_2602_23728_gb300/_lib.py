@@ -126,6 +126,8 @@ lib.phx_mlp_train.argtypes = [_P, _P, _P, _I, _I, C.c_double, _P, _P]
 lib.phx_mlp_train.restype = C.c_int
 lib.phx_mlp_predict.argtypes = [_P, _P, _I, _P, _P, _P]
 lib.phx_mlp_predict.restype = C.c_int
+lib.phx_mlp_reconstruct.argtypes = [_P, _I, _I, _P, _P, _P, _P, C.c_double, _P, _P, _P]
+lib.phx_mlp_reconstruct.restype = C.c_int
 
 KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4, "fp64_epilogue": 5,
            "eigensolver": 6, "cell_sparse": 7, "cell_transpose": 8, "cell_gemm": 9, "eig_tridiag": 10,
@@ -137,7 +139,7 @@ EXPORTED = ["phx_set_option", "phx_profile_enable", "phx_profile_read", "phx_cre
             "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_isotope", "phx_kappa_qhgk", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta", "phx_kappa_sc",
             "phx_kappa_rta_noalloc", "phx_gamma_batched", "phx_features", "phx_mlp_create", "phx_mlp_destroy",
             "phx_mlp_num_params", "phx_mlp_get_params", "phx_mlp_set_params", "phx_mlp_loss_grad", "phx_mlp_train",
-            "phx_mlp_predict"]
+            "phx_mlp_predict", "phx_mlp_reconstruct"]
 
 
 class PhxError(RuntimeError):
@@ -438,6 +440,24 @@ class Context:
     def mlp(self, n_in=4, width=128, depth=3, ensemble=4, seed=0):
         return MLP(self, n_in, width, depth, ensemble, seed)
 
+    def mlp_reconstruct(self, n, mean, std, wp2, freq_rows, f_min=0.01):
+        """phx_mlp_reconstruct on CUDA tensors: (gamma [rows], score [rows / n]) from the
+        ensemble's log prediction (wp2 None: no residual factor)."""
+        import torch
+        rows = mean.shape[0]
+        if rows % n:
+            raise ValueError("mlp_reconstruct: rows must be a multiple of n")
+        for a in (mean, std, wp2, freq_rows):
+            if a is not None and (not a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous()
+                                  or a.numel() != rows):
+                raise ValueError("mlp_reconstruct: contiguous float64 CUDA tensors of one row count")
+        gamma = torch.empty(rows, dtype=torch.float64, device=mean.device)
+        score = torch.empty(rows // n, dtype=torch.float64, device=mean.device) if std is not None else None
+        self._check(lib.phx_mlp_reconstruct(self.h, rows // n, n, _ptr(mean), _ptr(std), _ptr(wp2), _ptr(freq_rows),
+                                            float(f_min), _ptr(gamma), _ptr(score),
+                                            torch.cuda.current_stream(mean.device).cuda_stream))
+        return gamma, score
+
     # ------------------------------------------------------------------ transport
     def unfold(self, freq_full, irr_q, gamma_irr, full_to_irr, out=None):
         """phx_unfold: irreducible linewidths (degenerate-averaged) onto the full mesh."""
@@ -587,10 +607,26 @@ def kappa_rta_noalloc(lattice, masses, freq, gamma_full, temperature, out, vel=N
     if not all(a is None or (_is_torch(a) and a.is_cuda and a.is_contiguous()) for a in arrays):
         raise ValueError("phx_kappa_rta_noalloc takes contiguous CUDA tensors only")
     import torch
-    stream = torch.cuda.current_stream(freq.device).cuda_stream
-    st = lib.phx_kappa_rta_noalloc(C.byref(cell), freq.shape[0], freq.shape[1], _ptr(freq), _ptr(vel), _ptr(vv),
-                                   _ptr(gamma_full), float(temperature), float(f_min), int(is_classic), _ptr(out),
-                                   stream)
+    if any(a is not None and a.dtype != torch.float64 for a in arrays):
+        raise ValueError("phx_kappa_rta_noalloc takes float64 tensors only")
+    if any(a is not None and a.device != freq.device for a in arrays):
+        raise ValueError("phx_kappa_rta_noalloc: all tensors must be on one device")
+    if freq.dim() != 2 or tuple(gamma_full.shape) != tuple(freq.shape):
+        raise ValueError("phx_kappa_rta_noalloc: freq and gamma_full must both be [nq, n]")
+    if (vel is None) == (vv is None):
+        raise ValueError("phx_kappa_rta_noalloc: give exactly one of vel [nq, n, 3] and vv [nq, n, 3, 3]")
+    if vel is not None and tuple(vel.shape) != tuple(freq.shape) + (3,):
+        raise ValueError("phx_kappa_rta_noalloc: vel must be [nq, n, 3]")
+    if vv is not None and tuple(vv.shape) != tuple(freq.shape) + (3, 3):
+        raise ValueError("phx_kappa_rta_noalloc: vv must be [nq, n, 3, 3]")
+    if out.numel() < 9:
+        raise ValueError("phx_kappa_rta_noalloc: out must hold 9 doubles")
+    # the library takes its scratch array's address on the current device: make it the tensors'
+    with torch.cuda.device(freq.device):
+        stream = torch.cuda.current_stream(freq.device).cuda_stream
+        st = lib.phx_kappa_rta_noalloc(C.byref(cell), freq.shape[0], freq.shape[1], _ptr(freq), _ptr(vel), _ptr(vv),
+                                       _ptr(gamma_full), float(temperature), float(f_min), int(is_classic),
+                                       _ptr(out), stream)
     if st != 0:
         raise PhxError(st, "phx_kappa_rta_noalloc failed")
     return out

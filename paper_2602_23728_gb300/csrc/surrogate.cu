@@ -278,6 +278,38 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     return x ^ (x >> 31);
 }
 
+// Linewidths from the ensemble's log prediction: one block per group of n rows (one
+// irreducible q-point).  gamma = exp(mean) (x WP2 for the residual target) on rows whose mode
+// is at or above f_min, 0 below; score = the largest ensemble spread over the group's live rows.
+__global__ void __launch_bounds__(256) reconstruct_kernel(int n, const double* __restrict__ mean,
+                                                          const double* __restrict__ stdv,
+                                                          const double* __restrict__ wp2,
+                                                          const double* __restrict__ freq, double f_min,
+                                                          double* __restrict__ gamma, double* __restrict__ score) {
+    __shared__ double red[8];
+    const int64_t r0 = (int64_t)blockIdx.x * n;
+    double mx = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int64_t r = r0 + j;
+        const bool live = freq[r] >= f_min;
+        double g = 0.0;
+        if (live) {
+            g = exp(mean[r]);
+            if (wp2) g *= wp2[r];
+            if (stdv) mx = fmax(mx, stdv[r]);
+        }
+        gamma[r] = g;
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0 && score) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+        score[blockIdx.x] = v;
+    }
+}
+
 __global__ void init_kernel(float* __restrict__ p, int64_t count, uint64_t seed, float a) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t r = splitmix64(seed ^ splitmix64((uint64_t)t));
@@ -605,6 +637,21 @@ phx_status phx_mlp_predict(phx_mlp* m, const double* X, int32_t rows, double* me
     ensemble_kernel<<<(rows + 255) / 256, 256, 0, s>>>(m->dbuf0, rows, m->E, m->ymu, m->ysd, mean, stdv);
     PHX_CUDA_CHECK(m->ctx, cudaGetLastError());
     m->ctx->launches += 2 + (m->depth + 1);
+    return PHX_OK;
+}
+
+phx_status phx_mlp_reconstruct(phx_ctx* ctx, int32_t n_groups, int32_t n, const double* mean, const double* stdv,
+                               const double* wp2, const double* freq_thz, double f_min_thz, double* gamma,
+                               double* score, void* stream) {
+    if (!ctx) return PHX_ERR_INVALID;
+    if (n_groups <= 0 || n <= 0 || !mean || !freq_thz || !gamma)
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_mlp_reconstruct: bad argument");
+    if (score && !stdv) return phx_set_error(ctx, PHX_ERR_INVALID, "phx_mlp_reconstruct: score needs stdv");
+    cudaSetDevice(ctx->device);
+    reconstruct_kernel<<<n_groups, 256, 0, (cudaStream_t)stream>>>(n, mean, stdv, wp2, freq_thz, f_min_thz, gamma,
+                                                                   score);
+    PHX_CUDA_CHECK(ctx, cudaGetLastError());
+    ctx->launches += 1;
     return PHX_OK;
 }
 

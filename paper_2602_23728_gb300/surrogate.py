@@ -114,18 +114,17 @@ def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh,
 
     t0 = _timer(torch)
     mean, std = model.predict(X_all)
+    # linewidths (exp of the prediction, times WP2 for the residual target, 0 below f_min) and
+    # the per-q-point ensemble spread, on the device
+    pred_d, score_d = ctx.mlp_reconstruct(n, mean, std, wp2_all if residual else None, f_all.contiguous(), f_min)
     t["infer"] = _timer(torch) - t0
-    mean_h, std_h = mean.cpu().numpy(), std.cpu().numpy()
-    pred = np.exp(mean_h)
-    if residual:
-        pred = pred * wp2_all.cpu().numpy()
-    pred = np.where(live, pred, 0.0)
-    yh = y_all.cpu().numpy()
-    hold_err = np.abs(pred[hold_rows] - yh[hold_rows]) / yh[hold_rows]
+    score = score_d.cpu().numpy()
+    # held-out check (reported, not used by the path)
+    hold_d = torch.from_numpy(hold_rows).to(dev)
+    hold_err = (torch.abs(pred_d[hold_d] - y_all[hold_d]) / y_all[hold_d]).cpu().numpy()
 
     # exact fallback on the q-points whose most uncertain mode ranks in the top
     # (100 - uncertainty_pct) % of the q-points outside the subgrid
-    score = np.where(live, std_h, 0.0).reshape(len(irr), n).max(axis=1)
     cand = np.array([k for k in range(len(irr)) if not train_mask0[k]], dtype=np.int64)
     n_fb = int(np.ceil((100.0 - uncertainty_pct) / 100.0 * len(cand)))
     fb_q = sorted(int(irr[k]) for k in cand[np.argsort(-score[cand])[:n_fb]]) if n_fb > 0 else []
@@ -140,7 +139,7 @@ def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh,
     t["fallback"] = _timer(torch) - t0
 
     g_sur = gamma_irr.clone()
-    pred_t = torch.from_numpy(pred.reshape(len(irr), n)).to(dev)
+    pred_t = pred_d.reshape(len(irr), n)
     mask = torch.from_numpy(~exact_rows).to(dev)
     g_sur[mask] = pred_t[mask]
     f2i_d = torch.from_numpy(f2i.astype(np.int32)).to(dev)

@@ -663,7 +663,7 @@ def run_surrogate(args):
                               "nearest_subgrid_interpolation": r["kappa_rel_err_interp"]},
             "heldout_rel_err": {"median": r["heldout_median_rel_err"], "max": r["heldout_max_rel_err"]},
             "timings_s": t, "n_fallback_q": r["n_fallback_q"], "n_irr": r["n_irr"],
-            "final_loss": list(map(float, r["final_loss"]))}
+            "final_loss": list(map(float, r["final_loss"])), "epochs_run": r["epochs_run"]}
     print(json.dumps(line, default=float), flush=True)
     ctx.close()
     return 0

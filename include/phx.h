@@ -320,6 +320,14 @@ phx_status phx_mlp_loss_grad(phx_mlp* m, const double* X, const double* y, int32
  * standardisation from this batch.  Final losses to loss[ensemble] (host, may be NULL). */
 phx_status phx_mlp_train(phx_mlp* m, const double* X, const double* y, int32_t rows, int32_t epochs,
                          double lr, double* loss, void* stream);
+/* As phx_mlp_train with early stopping: the last n_val rows of (X, y) are held out (not in the
+ * gradient or the standardisation); their loss is evaluated every epoch and checked every
+ * check_every epochs; training stops after `patience` checks in a row without a 0.1 %
+ * improvement of the ensemble-mean held-out loss, or after max_epochs, and the parameters
+ * of the best check are kept.  Epochs run to *epochs_run (host, may be NULL). */
+phx_status phx_mlp_train_es(phx_mlp* m, const double* X, const double* y, int32_t rows, int32_t n_val,
+                            int32_t max_epochs, double lr, int32_t check_every, int32_t patience, double* loss,
+                            int32_t* epochs_run, void* stream);
 /* Ensemble mean and standard deviation of log(gamma) per row (device; stdv may be NULL). */
 phx_status phx_mlp_predict(phx_mlp* m, const double* X, int32_t rows, double* mean, double* stdv,
                            void* stream);

@@ -124,6 +124,8 @@ lib.phx_mlp_loss_grad.argtypes = [_P, _P, _P, _I, _P, _P, _P]
 lib.phx_mlp_loss_grad.restype = C.c_int
 lib.phx_mlp_train.argtypes = [_P, _P, _P, _I, _I, C.c_double, _P, _P]
 lib.phx_mlp_train.restype = C.c_int
+lib.phx_mlp_train_es.argtypes = [_P, _P, _P, _I, _I, _I, C.c_double, _I, _I, _P, _P, _P]
+lib.phx_mlp_train_es.restype = C.c_int
 lib.phx_mlp_predict.argtypes = [_P, _P, _I, _P, _P, _P]
 lib.phx_mlp_predict.restype = C.c_int
 lib.phx_mlp_reconstruct.argtypes = [_P, _I, _I, _P, _P, _P, _P, C.c_double, _P, _P, _P]
@@ -139,7 +141,7 @@ EXPORTED = ["phx_set_option", "phx_profile_enable", "phx_profile_read", "phx_cre
             "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_isotope", "phx_kappa_qhgk", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta", "phx_kappa_sc",
             "phx_kappa_rta_noalloc", "phx_gamma_batched", "phx_features", "phx_mlp_create", "phx_mlp_destroy",
             "phx_mlp_num_params", "phx_mlp_get_params", "phx_mlp_set_params", "phx_mlp_loss_grad", "phx_mlp_train",
-            "phx_mlp_predict", "phx_mlp_reconstruct"]
+            "phx_mlp_predict", "phx_mlp_reconstruct", "phx_mlp_train_es"]
 
 
 class PhxError(RuntimeError):
@@ -577,6 +579,16 @@ class MLP:
         self.ctx._check(lib.phx_mlp_train(self.h, _ptr(X), _ptr(y), int(X.shape[0]), int(epochs), float(lr),
                                           loss.ctypes.data, self._stream(X)))
         return loss
+
+    def train_es(self, X, y, n_val, max_epochs, lr=3e-3, check_every=50, patience=4):
+        """Early-stopped training: the last n_val rows of X, y are the held-out set.  Returns
+        (final training loss per member, epochs run)."""
+        loss = np.zeros(self.ensemble)
+        ran = C.c_int32(0)
+        self.ctx._check(lib.phx_mlp_train_es(self.h, _ptr(X), _ptr(y), int(X.shape[0]), int(n_val), int(max_epochs),
+                                             float(lr), int(check_every), int(patience), loss.ctypes.data,
+                                             C.addressof(ran), self._stream(X)))
+        return loss, ran.value
 
     def predict(self, X, mean=None, std=None):
         import torch

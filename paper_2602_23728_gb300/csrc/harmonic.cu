@@ -243,9 +243,9 @@ jacobi_kernel(double2* __restrict__ Ag, double2* __restrict__ Vg, int n, double*
 //     w = p - (beta v^H p / 2) v, p = beta A22 v.  Writes the reflectors (row k of R holds v_k),
 //     beta, the diagonal and the complex subdiagonal.
 //  ql_back_kernel    (one small CTA per matrix, many per SM so their serial parts overlap) the
-//     subdiagonal made real by the phases delta_{k+1} = delta_k e_k/|e_k|, implicit QL with
-//     Wilkinson shifts (thread 0 forms a sweep's rotations, every thread applies them to its
-//     row of Z), eigenvalue ranks, back-transformation E = H_0 ... H_{n-3} diag(delta) Z written
+//     subdiagonal made real by the phases delta_{k+1} = delta_k e_k/|e_k|, implicit symmetric QR
+//     steps with Wilkinson shifts (thread 0 forms a round's rotations, every thread applies them
+//     to its rows of Z), eigenvalue ranks, back-transformation E = H_0 ... H_{n-3} diag(delta) Z written
 //     straight into the sorted output column, then the gauge (largest-modulus component real
 //     and positive, as the Jacobi solver).
 // About 15 n^3 real flops per matrix against ~200 n^3 for the cyclic Jacobi sweeps.
@@ -386,63 +386,69 @@ ql_back_kernel(const double2* __restrict__ Rg, const double* __restrict__ scratc
     }
     for (int64_t t = tid; t < nn; t += nt) Z[t] = (t / n == t % n) ? 1.0 : 0.0;
     __syncthreads();
-    for (int l = 0; l < n; ++l) {
-        for (int iter = 0; iter <= kQlMaxIter; ++iter) {
-            if (tid == 0) {
-                int m = l;
-                for (; m < n - 1; ++m) {
-                    const double dd = fabs(d[m]) + fabs(d[m + 1]);
-                    if (fabs(e[m]) <= 2.2204460492503131e-16 * dd) break;
-                }
-                sweep_lo = l;
-                sweep_hi = m;
-                if (m != l) {
-                    if (iter == kQlMaxIter) { sweep_fail = 1; sweep_hi = l; }
-                    else {
-                        double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-                        double r = hypot(g, 1.0);
-                        g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
-                        double sn = 1.0, cs = 1.0, p = 0.0;
-                        int i = m - 1;
-                        bool underflow = false;
-                        for (; i >= l; --i) {
-                            const double f = sn * e[i], b = cs * e[i];
-                            r = hypot(f, g);
-                            e[i + 1] = r;
-                            if (r == 0.0) { d[i + 1] -= p; e[m] = 0.0; underflow = true; break; }
-                            sn = f / r;
-                            cs = g / r;
-                            g = d[i + 1] - p;
-                            r = (d[i] - g) * sn + 2.0 * cs * b;
-                            p = sn * r;
-                            d[i + 1] = g + p;
-                            g = cs * r - b;
-                            rc[i] = cs;
-                            rs[i] = sn;
-                        }
-                        if (underflow) sweep_lo = i + 1;     // rotations i+1 .. m-1 were formed
-                        else { d[l] -= p; e[l] = g; e[m] = 0.0; }
+    // Symmetric tridiagonal QR iteration (Golub & Van Loan, "Matrix Computations", the implicit
+    // symmetric QR step with Wilkinson shift inside the symmetric QR algorithm): every round
+    // zeroes the negligible off-diagonals, takes the lowest unreduced block [lo, hi], and chases
+    // one bulge from its top to its bottom with Givens rotations Q_k on rows/columns (k, k+1),
+    // T <- Q_k T Q_k^T, Z <- Z Q_k^T.  Thread 0 updates (d, e) and records (c_k, s_k); every
+    // thread then applies the round's rotations to its rows of Z.
+    const int max_rounds = kQlMaxIter * (n > 0 ? n : 1);
+    for (int round = 0;; ++round) {
+        if (tid == 0) {
+            int hi = -1, lo = 0;
+            for (int k = 0; k + 1 < n; ++k)
+                if (fabs(e[k]) <= 2.2204460492503131e-16 * (fabs(d[k]) + fabs(d[k + 1]))) e[k] = 0.0;
+            for (int k = n - 2; k >= 0; --k)
+                if (e[k] != 0.0) { hi = k + 1; break; }
+            if (hi > 0) {
+                lo = hi - 1;
+                while (lo > 0 && e[lo - 1] != 0.0) --lo;
+            }
+            if (hi < 0 || round >= max_rounds) {
+                sweep_lo = sweep_hi = 0;                     // done (or given up)
+                if (hi >= 0) sweep_fail = 1;
+            } else {
+                // Wilkinson shift: the eigenvalue of the block's trailing 2x2 nearer d[hi]
+                const double dl = 0.5 * (d[hi - 1] - d[hi]), b = e[hi - 1];
+                const double den = dl + copysign(hypot(dl, b), dl);
+                const double mu = d[hi] - (den != 0.0 ? b * (b / den) : b);
+                double x = d[lo] - mu, z = e[lo];
+                for (int k = lo; k < hi; ++k) {
+                    const double r = hypot(x, z);
+                    const double c = r > 0.0 ? x / r : 1.0, sn = r > 0.0 ? z / r : 0.0;
+                    if (k > lo) e[k - 1] = r;                    // the bulge at (k+1, k-1) folds into e[k-1]
+                    const double a = d[k], bb = e[k], dd = d[k + 1];
+                    d[k] = c * c * a + 2.0 * c * sn * bb + sn * sn * dd;
+                    d[k + 1] = sn * sn * a - 2.0 * c * sn * bb + c * c * dd;
+                    e[k] = c * sn * (dd - a) + (c * c - sn * sn) * bb;
+                    if (k + 1 < hi) {                            // new bulge at (k+2, k)
+                        x = e[k];
+                        z = sn * e[k + 1];
+                        e[k + 1] *= c;
                     }
+                    rc[k] = c;
+                    rs[k] = sn;
                 }
+                sweep_lo = lo;
+                sweep_hi = hi;
             }
-            __syncthreads();
-            const int lo = sweep_lo, hi = sweep_hi;
-            if (hi == l && lo == l) break;
-            // rotations hi-1 .. lo on columns (i, i+1) of every row; column i+1's new value is
-            // stored, column i's is carried to the next rotation in a register
-            for (int row = tid; row < n; row += nt) {
-                if (hi <= lo) break;
-                double carry = Z[(int64_t)hi * n + row];
-                for (int i = hi - 1; i >= lo; --i) {
-                    const double c = rc[i], sg = rs[i];
-                    const double zi = Z[(int64_t)i * n + row];
-                    Z[(int64_t)(i + 1) * n + row] = sg * zi + c * carry;
-                    carry = c * zi - sg * carry;
-                }
-                Z[(int64_t)lo * n + row] = carry;
-            }
-            __syncthreads();
         }
+        __syncthreads();
+        const int lo = sweep_lo, hi = sweep_hi;
+        if (hi <= lo) break;
+        // Z <- Z Q_lo^T ... Q_{hi-1}^T on columns (k, k+1): column k is final after rotation k,
+        // column k+1 is carried to the next rotation in a register
+        for (int row = tid; row < n; row += nt) {
+            double carry = Z[(int64_t)lo * n + row];
+            for (int k = lo; k < hi; ++k) {
+                const double c = rc[k], sn = rs[k];
+                const double zk1 = Z[(int64_t)(k + 1) * n + row];
+                Z[(int64_t)k * n + row] = c * carry + sn * zk1;
+                carry = c * zk1 - sn * carry;
+            }
+            Z[(int64_t)hi * n + row] = carry;
+        }
+        __syncthreads();
     }
     if (tid == 0 && sweep_fail) atomicExch(status, (int)PHX_ERR_NUMERIC);
     for (int i = tid; i < n; i += nt) {

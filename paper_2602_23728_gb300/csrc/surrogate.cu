@@ -254,6 +254,22 @@ __global__ void loss_grad_all_kernel(const float* __restrict__ yhat, const float
     }
 }
 
+// As loss_grad_all_kernel with the last M - Mt rows held out: gradient 2 r / Mt on the first Mt
+// rows, 0 on the rest, whose mean squared error goes to vloss[e].
+__global__ void loss_grad_split_kernel(const float* __restrict__ yhat, const float* __restrict__ y, int Mt, int M,
+                                       int E, int64_t L, float* __restrict__ dy, double* __restrict__ vloss) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M * E; t += gridDim.x * blockDim.x) {
+        const int e = t / M, i = t % M;
+        const float r = yhat[e * L + i] - y[i];
+        if (i < Mt) {
+            dy[e * L + i] = 2.f * r / Mt;
+        } else {
+            dy[e * L + i] = 0.f;
+            atomicAdd(&vloss[e], (double)(r * r) / (M - Mt));
+        }
+    }
+}
+
 // ensemble statistics of log gamma (de-standardised): mean and std over members
 __global__ void ensemble_kernel(const float* __restrict__ yhat, int M, int E, const float* __restrict__ mu,
                                 const float* __restrict__ sd, double* __restrict__ mean, double* __restrict__ stdv) {
@@ -336,6 +352,8 @@ struct phx_mlp {
     float *act = nullptr, *pre = nullptr;      // [depth+2][E][rows][width]
     float *xin = nullptr, *ystd = nullptr, *dbuf0 = nullptr, *dbuf1 = nullptr;
     double* loss = nullptr;
+    double* vloss = nullptr;                   // held-out loss per member (early stopping)
+    float* best = nullptr;                     // parameters at the best held-out loss
     int* step = nullptr;                       // Adam step counter (device)
 };
 
@@ -451,6 +469,8 @@ phx_status phx_mlp_create(phx_ctx* ctx, int32_t n_in, int32_t width, int32_t dep
               cudaMalloc(&m->mu, sizeof(float) * 64) == cudaSuccess && cudaMalloc(&m->sd, sizeof(float) * 64) == cudaSuccess &&
               cudaMalloc(&m->ymu, sizeof(float)) == cudaSuccess && cudaMalloc(&m->ysd, sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->loss, sizeof(double) * ensemble) == cudaSuccess &&
+              cudaMalloc(&m->vloss, sizeof(double) * ensemble) == cudaSuccess &&
+              cudaMalloc(&m->best, pb) == cudaSuccess &&
               cudaMalloc(&m->step, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -482,6 +502,7 @@ void phx_mlp_destroy(phx_mlp* m) {
     if (!m) return;
     cudaFree(m->par); cudaFree(m->grad); cudaFree(m->m1); cudaFree(m->m2);
     cudaFree(m->mu); cudaFree(m->sd); cudaFree(m->ymu); cudaFree(m->ysd); cudaFree(m->loss); cudaFree(m->step);
+    cudaFree(m->vloss); cudaFree(m->best);
     cudaFree(m->act); cudaFree(m->pre); cudaFree(m->xin); cudaFree(m->ystd); cudaFree(m->dbuf0); cudaFree(m->dbuf1);
     delete m;
 }
@@ -537,13 +558,19 @@ phx_status phx_mlp_loss_grad(phx_mlp* m, const double* X, const double* y, int32
     return PHX_OK;
 }
 
-// Full-batch Adam training of every member on (X, log y): sets the input/target
-// standardisation from the batch, then `epochs` steps.  Final losses to loss[E] (host, may be
-// NULL).
-phx_status phx_mlp_train(phx_mlp* m, const double* X, const double* y, int32_t rows, int32_t epochs, double lr,
-                         double* loss, void* stream) {
-    if (!m || !X || !y || rows <= 0 || epochs < 0 || !(lr > 0.0)) return PHX_ERR_INVALID;
+}  // extern "C"
+
+// Full-batch Adam training of every member on the first rows - n_val rows of (X, log y): sets
+// the input/target standardisation from them, then runs epochs.  With n_val > 0 the last n_val
+// rows are held out: their loss is evaluated every epoch, checked every check_every epochs,
+// and training stops once it has not improved by 0.1 % for `patience` checks in a row; the
+// parameters at the best check are restored.  Final training losses to loss[E] (host, may be
+// NULL), epochs run to *epochs_run (may be NULL).
+static phx_status mlp_train_impl(phx_mlp* m, const double* X, const double* y, int32_t rows, int32_t n_val,
+                                 int32_t epochs, double lr, int32_t check_every, int32_t patience, double* loss,
+                                 int32_t* epochs_run, void* stream) {
     phx_ctx* ctx = m->ctx;
+    const int rows_tr = rows - n_val;
     cudaStream_t user = (cudaStream_t)stream;
     PHX_TRY(mlp_reserve(m, rows));
     if (!ctx->cap_stream) {
@@ -554,8 +581,8 @@ phx_status phx_mlp_train(phx_mlp* m, const double* X, const double* y, int32_t r
     cudaStream_t s = ctx->cap_stream;
     PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_in, user));
     PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(s, ctx->ev_in, 0));
-    moments_kernel<<<m->n_in, 256, 0, s>>>(X, rows, m->n_in, 1, m->mu, m->sd);
-    moments_kernel<<<1, 256, 0, s>>>(y, rows, 1, 1, m->ymu, m->ysd);
+    moments_kernel<<<m->n_in, 256, 0, s>>>(X, rows_tr, m->n_in, 1, m->mu, m->sd);
+    moments_kernel<<<1, 256, 0, s>>>(y, rows_tr, 1, 1, m->ymu, m->ysd);
     input_kernel<<<256, 256, 0, s>>>(X, rows, m->n_in, m->mu, m->sd, m->xin);
     target_kernel<<<64, 256, 0, s>>>(y, rows, m->ymu, m->ysd, m->ystd);
     PHX_CUDA_CHECK(ctx, cudaGetLastError());
@@ -568,13 +595,20 @@ phx_status phx_mlp_train(phx_mlp* m, const double* X, const double* y, int32_t r
     const int64_t L = (int64_t)rows * m->width;
     const int64_t layer = (int64_t)m->E * L;
     const float* yhat = m->act + (int64_t)(m->depth + 1) * layer;
-    // one epoch (forward, loss gradient, backward, Adam, step counter) as a graph
+    // one epoch (forward, loss gradient, backward, Adam, step counter) as a graph; held-out rows
+    // run forward with a zero gradient (their rows add nothing to the weight gradients)
     cudaGraphExec_t exec = nullptr;
+    int done = 0;
     if (epochs > 0) {
         PHX_CUDA_CHECK(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         phx_status st = mlp_forward(m, rows, s);
         if (st == PHX_OK) {
-            loss_grad_all_kernel<<<64, 256, 0, s>>>(yhat, m->ystd, rows, m->E, L, m->dbuf0, nullptr);
+            if (n_val > 0) {
+                cudaMemsetAsync(m->vloss, 0, sizeof(double) * m->E, s);
+                loss_grad_split_kernel<<<64, 256, 0, s>>>(yhat, m->ystd, rows_tr, rows, m->E, L, m->dbuf0, m->vloss);
+            } else {
+                loss_grad_all_kernel<<<64, 256, 0, s>>>(yhat, m->ystd, rows, m->E, L, m->dbuf0, nullptr);
+            }
             if (cudaGetLastError() != cudaSuccess) st = PHX_ERR_CUDA;
         }
         if (st == PHX_OK) st = mlp_backward(m, rows, s);
@@ -593,19 +627,46 @@ phx_status phx_mlp_train(phx_mlp* m, const double* X, const double* y, int32_t r
         const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
         cudaGraphDestroy(g);
         if (ei != cudaSuccess) return phx_set_error(ctx, PHX_ERR_CUDA, "phx_mlp_train: instantiate failed");
+        double best = 1e300;
+        int bad = 0;
+        bool have_best = false;
+        std::vector<double> vl(m->E);
         for (int ep = 0; ep < epochs; ++ep) {
             const cudaError_t el = cudaGraphLaunch(exec, s);
             if (el != cudaSuccess) {
                 cudaGraphExecDestroy(exec);
                 return phx_set_error(ctx, PHX_ERR_CUDA, "phx_mlp_train: %s", cudaGetErrorString(el));
             }
+            done = ep + 1;
+            if (n_val > 0 && check_every > 0 && done % check_every == 0) {
+                // held-out loss of the parameters before this epoch's update (the forward pass
+                // of the epoch ran on them)
+                PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(vl.data(), m->vloss, sizeof(double) * m->E, cudaMemcpyDeviceToHost, s));
+                PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
+                double mean = 0.0;
+                for (double v : vl) mean += v / m->E;
+                if (mean < best * (1.0 - 1e-3)) {
+                    best = mean;
+                    bad = 0;
+                    have_best = true;
+                    // the loss was taken on the parameters before this epoch's update; the copy
+                    // kept is one Adam step later
+                    PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(m->best, m->par, sizeof(float) * np_all,
+                                                        cudaMemcpyDeviceToDevice, s));
+                } else if (++bad >= patience) {
+                    break;
+                }
+            }
         }
-        ctx->launches += (int64_t)epochs * (6 + 4 * (m->depth + 1));
+        if (have_best)
+            PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(m->par, m->best, sizeof(float) * np_all, cudaMemcpyDeviceToDevice, s));
+        ctx->launches += (int64_t)done * (6 + 4 * (m->depth + 1));
     }
-    // final loss with the trained parameters
+    if (epochs_run) *epochs_run = done;
+    // final loss with the trained parameters (training rows)
     PHX_TRY(mlp_forward(m, rows, s));
     PHX_CUDA_CHECK(ctx, cudaMemsetAsync(m->loss, 0, sizeof(double) * m->E, s));
-    loss_grad_all_kernel<<<64, 256, 0, s>>>(yhat, m->ystd, rows, m->E, L, m->dbuf0, m->loss);
+    loss_grad_all_kernel<<<64, 256, 0, s>>>(yhat, m->ystd, rows_tr, m->E, L, m->dbuf0, m->loss);
     PHX_CUDA_CHECK(ctx, cudaGetLastError());
     if (exec) {
         PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
@@ -618,6 +679,24 @@ phx_status phx_mlp_train(phx_mlp* m, const double* X, const double* y, int32_t r
         PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
     }
     return PHX_OK;
+}
+
+extern "C" {
+
+phx_status phx_mlp_train(phx_mlp* m, const double* X, const double* y, int32_t rows, int32_t epochs, double lr,
+                         double* loss, void* stream) {
+    if (!m || !X || !y || rows <= 0 || epochs < 0 || !(lr > 0.0)) return PHX_ERR_INVALID;
+    return mlp_train_impl(m, X, y, rows, 0, epochs, lr, 0, 0, loss, nullptr, stream);
+}
+
+phx_status phx_mlp_train_es(phx_mlp* m, const double* X, const double* y, int32_t rows, int32_t n_val,
+                            int32_t max_epochs, double lr, int32_t check_every, int32_t patience, double* loss,
+                            int32_t* epochs_run, void* stream) {
+    if (!m) return PHX_ERR_INVALID;
+    if (!X || !y || rows <= 0 || n_val < 1 || n_val >= rows || max_epochs < 0 || !(lr > 0.0) || check_every < 1 ||
+        patience < 1)
+        return phx_set_error(m->ctx, PHX_ERR_INVALID, "phx_mlp_train_es: bad argument");
+    return mlp_train_impl(m, X, y, rows, n_val, max_epochs, lr, check_every, patience, loss, epochs_run, stream);
 }
 
 // Ensemble prediction of log(gamma): mean[rows] and std[rows] (device, std may be NULL).

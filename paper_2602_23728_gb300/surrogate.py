@@ -31,13 +31,18 @@ def subgrid_points(mesh, step):
 
 def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh, step, rotations, temperature,
         shape="gauss", sigma=0.1, f_min=0.01, precision="bf16x3", epochs=3000, lr=3e-3, heldout_frac=0.05,
-        uncertainty_pct=95.0, ensemble=4, width=128, depth=3, seed=0, exact_reference=True, residual=True):
+        uncertainty_pct=95.0, ensemble=4, width=128, depth=3, seed=0, exact_reference=True, residual=True,
+        early_stop=True, val_frac=0.1, check_every=50, patience=4):
     """Surrogate linewidths and RTA conductivity on `mesh` trained on the subgrid of spacing
     `step`.  Returns a dict with the conductivities (surrogate, exact when asked, nearest-
     subgrid baseline), errors, timings and counts.
 
     residual: the network learns log(gamma / WP2) (the phase-space-averaged coupling, smooth in
-    the descriptors) instead of log(gamma); gamma = WP2 * exp(prediction)."""
+    the descriptors) instead of log(gamma); gamma = WP2 * exp(prediction).
+
+    early_stop: a seeded val_frac of the training rows is kept out of the gradient and training
+    stops once its loss has not improved for `patience` checks of `check_every` epochs (at most
+    `epochs`); otherwise exactly `epochs` full-batch Adam steps."""
     import torch
     dev = torch.device("cuda", ctx.device)
     n = 3 * len(masses)
@@ -89,6 +94,7 @@ def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh,
     n_hold = max(1, int(round(heldout_frac * len(tr_rows))))
     perm = rng.permutation(len(tr_rows))
     hold_rows, fit_rows = tr_rows[perm[:n_hold]], tr_rows[perm[n_hold:]]
+    n_val = max(1, int(round(val_frac * len(fit_rows)))) if early_stop else 0   # the last n_val fit rows
     y_all = gamma_irr.reshape(-1)
     wp2_all = X_all[:, 2].contiguous()
     Xf = X_all[torch.from_numpy(fit_rows).to(dev)].contiguous()
@@ -97,9 +103,14 @@ def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh,
         yf = yf / torch.clamp(wp2_all[torch.from_numpy(fit_rows).to(dev)], min=1e-300)
     yf = yf.contiguous()
 
+    def fit(model):
+        if early_stop:
+            return model.train_es(Xf, yf, n_val, epochs, lr, check_every, patience)
+        return model.train(Xf, yf, epochs, lr), epochs
+
     t0 = _timer(torch)
     model = ctx.mlp(4, width, depth, ensemble, seed)
-    final_loss = model.train(Xf, yf, epochs, lr)
+    final_loss, epochs_run = fit(model)
     # a member whose final loss stays far above the others' has not converged (it would bias the
     # ensemble mean and inflate its spread): train the ensemble again from another seed, twice
     # at most
@@ -109,7 +120,8 @@ def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh,
             break
         model.close()
         model = ctx.mlp(4, width, depth, ensemble, seed + 1 + retry)
-        final_loss = model.train(Xf, yf, epochs, lr)
+        final_loss, ep = fit(model)
+        epochs_run += ep
     t["train"] = _timer(torch) - t0
 
     t0 = _timer(torch)
@@ -173,8 +185,8 @@ def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh,
 
     out = dict(kappa_surrogate=k_sur, kappa_interp=k_base, kappa_coarse=k_coarse, timings=t, final_loss=final_loss,
                heldout_median_rel_err=float(np.median(hold_err)), heldout_max_rel_err=float(hold_err.max()),
-               n_irr=len(irr), n_train_q=len(train_q), n_fallback_q=len(fb_q), n_train_rows=len(fit_rows),
-               n_heldout_rows=len(hold_rows))
+               n_irr=len(irr), n_train_q=len(train_q), n_fallback_q=len(fb_q), n_train_rows=len(fit_rows) - n_val,
+               n_val_rows=n_val, n_heldout_rows=len(hold_rows), epochs_run=epochs_run)
     if exact_reference:
         t0 = _timer(torch)
         g_ex = ctx.gamma(h, freq, evec, irr_d, temperature, shape, sigma, 2.0, f_min, precision=precision,

@@ -86,3 +86,22 @@ def test_surrogate_gain_over_coarse_mesh(ctx, phx):
     assert r["kappa_rel_err_surrogate"] < r["kappa_rel_err_coarse"]
     assert r["kappa_rel_err_surrogate"] < 0.05
     assert r["heldout_median_rel_err"] < 0.25
+
+
+def test_train_early_stopping_stops_on_unlearnable_target(ctx, phx):
+    """Targets that are pure noise: the held-out loss cannot keep improving, so training stops
+    long before the epoch limit, at a check boundary, with finite losses and usable weights."""
+    import torch
+    rng = np.random.default_rng(3)
+    X = rng.uniform(0.5, 2.0, size=(400, 4))
+    y = np.exp(rng.normal(size=400))
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    m = ctx.mlp(4, 64, 2, 2, 5)
+    try:
+        loss, ran = m.train_es(Xd, yd, 80, 5000, 3e-3, check_every=25, patience=3)
+        assert 0 < ran < 5000 and ran % 25 == 0
+        assert np.all(np.isfinite(loss))
+        mean, std = m.predict(Xd)
+        assert torch.isfinite(mean).all() and torch.isfinite(std).all()
+    finally:
+        m.close()

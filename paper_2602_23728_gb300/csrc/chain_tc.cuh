@@ -58,13 +58,26 @@ struct ChainArgs {
     int32_t* status;
     unsigned long long wait_ns; // bound of every barrier wait
     int starve;                 // test hook: the producer issues nothing (waits then run out)
+    // CHAIN_GT: n_t temperatures (occupation tables nb_stride apart, accumulators t_stride apart)
+    int n_t;
+    int64_t nb_stride, t_stride;
+    // CHAIN_GS: off-diagonal scattering rows of Eq. (gamma1), folded onto time-reversal
+    // representatives (row g1_row0 + nu of this chunk; see G1Target)
+    float* g1;
+    int64_t g1_rows, g1_ld, g1_row0;
+    const int32_t* tr_code;
+    float g1_scale;
 };
+
+// epilogue variants: linewidths (+ WP2), linewidths at several temperatures, linewidths plus
+// the off-diagonal scattering rows
+enum { CHAIN_G = 0, CHAIN_GT = 1, CHAIN_GS = 2 };
 
 constexpr int kChainThreads = 256;
 constexpr int kChainEpiThreads = 192;     // warps 0-2 and 4-6
 constexpr int kChainMmaWarp = 3, kChainTmaWarp = 7;
 
-template <int PREC>
+template <int PREC, int MODE>
 __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_constant__ ChainArgs args) {
     constexpr int kPlanes = (PREC == P_BF16X3) ? 2 : 1;
     constexpr uint32_t kFmt = (PREC == P_BF16X3) ? 1u : 2u;
@@ -75,6 +88,8 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
     __shared__ uint32_t tmem_base_slot;
     __shared__ volatile int abort_flag;
     __shared__ float s_f1[kMaxNp], s_n1[kMaxNp], s_if1[kMaxNp];
+    __shared__ float s_n1t[MODE == CHAIN_GT ? kMaxT : 1][MODE == CHAIN_GT ? kMaxNp : 1];
+    __shared__ float s_col[MODE == CHAIN_GS ? 2 : 1][MODE == CHAIN_GS ? kMaxNp : 1];   // Gamma1 column sums
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int n = args.n, kcp = args.kcp, nkc = args.nkc, ra = args.ra, rb3 = args.rb3;
@@ -328,14 +343,40 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
         const float sg = args.sigma, lim = args.window * sg;
         const float ga_a = -1.f / (sg * sg), h2 = 0.25f * sg * sg;
         const float norm = gauss ? 0.56418958354775628f / sg : 0.5f * sg / 3.14159265358979f;
+        float nn2t[kMaxT];
+#pragma unroll
+        for (int t = 0; t < kMaxT; ++t) nn2t[t] = 0.f;
+        int c1 = 0, c2 = 0;                              // CHAIN_GS: time-reversal codes of q', q''
+        // CHAIN_GS: the column sums of item li are complete once every epilogue thread has passed
+        // the barrier at the start of item li + 1; they are flushed to Gamma1 there (before the
+        // partner tables change) from a buffer the next item does not use
+        int prev_nu = -1, prev_c1 = 0;
+        float prev_rs = 0.f;
+        auto flush_cols = [&](int buf) {
+            for (int j = et; j < rb3; j += kChainEpiThreads) {
+                const float val = s_col[buf][j];
+                s_col[buf][j] = 0.f;
+                if (val == 0.f || prev_c1 == 0 || j >= n || args.g1_row0 + prev_nu >= args.g1_rows) continue;
+                const int64_t gc = (int64_t)(abs(prev_c1) - 1) * n + j;
+                if (gc < args.g1_ld)
+                    atomicAdd(args.g1 + (args.g1_row0 + prev_nu) * args.g1_ld + gc,
+                              (prev_c1 > 0 ? prev_rs : -prev_rs) * s_f1[j] * val);
+                else
+                    atomicExch(args.status, (int)PHX_ERR_INVALID);     // bounds self-check
+            }
+        };
+        if (MODE == CHAIN_GS)
+            for (int j = et; j < 2 * kMaxNp; j += kChainEpiThreads) (&s_col[0][0])[j] = 0.f;
         convert(0);
         for (int li = 0; li < L; ++li) {
             const int it = item_begin + li;
             const int p = it / nnu, nu = it % nnu;
             if (epi_barrier_any(kChainEpiThreads, abort_flag != 0)) break;   // one decision for all
+            if (MODE == CHAIN_GS && li > 0) flush_cols((li - 1) & 1);
             if (p != cur_p) {
                 // partner tables of this slot's q' (every thread has finished the previous item:
                 // barrier above) and this thread's row constants at q''
+                if (MODE == CHAIN_GS) epi_barrier(kChainEpiThreads);    // flush read the old tables
                 const int q1 = args.t0 + p, q2 = args.qpp[p];
                 for (int j = et; j < rb3; j += kChainEpiThreads) {
                     const bool v = j < n;
@@ -343,9 +384,19 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                     s_f1[j] = f1;
                     s_n1[j] = v ? (float)args.nB[(int64_t)q1 * n + j] : 0.0f;
                     s_if1[j] = (v && f1 >= args.f_min) ? 1.0f / f1 : 0.0f;   // 0 masks padding and soft partners
+                    if (MODE == CHAIN_GT)
+                        for (int t = 0; t < kMaxT; ++t)
+                            s_n1t[t][j] = (v && t < args.n_t) ? (float)args.nB[t * args.nb_stride + (int64_t)q1 * n + j]
+                                                              : 0.0f;
                 }
                 f2 = nu2 < n ? (float)args.freq[(int64_t)q2 * n + nu2] : 0.f;
                 nn2 = nu2 < n ? (float)args.nB[(int64_t)q2 * n + nu2] : 0.f;
+                if (MODE == CHAIN_GT)
+#pragma unroll
+                    for (int t = 0; t < kMaxT; ++t)
+                        nn2t[t] = (nu2 < n && t < args.n_t) ? (float)args.nB[t * args.nb_stride + (int64_t)q2 * n + nu2]
+                                                            : 0.f;
+                if (MODE == CHAIN_GS) { c1 = args.tr_code[q1]; c2 = args.tr_code[q2]; }
                 epi_barrier(kChainEpiThreads);
                 cur_p = p;
             }
@@ -353,8 +404,12 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
             const bool live = nu2 < n && f0 >= args.f_min && f2 >= args.f_min;
             // w = [...] / (2 pi)^4 / (f0 f1 f2): delta(w) = g(f)/(2 pi) and 1/(w0 w1 w2)
             const float inv_f02 = live ? 1.0f / (1558.5454565440389f * f0 * f2) : 0.0f;
+            const float rowfac = norm * inv_f02;
             const float d02 = f0 - f2, one_n2 = 1.f + nn2;
             float gs = 0.f, ws = 0.f;
+            float gst[kMaxT];
+#pragma unroll
+            for (int t = 0; t < kMaxT; ++t) gst[t] = 0.f;
             bool ok = tc::mbar_wait(&s3_done, li & 1, &abort_flag, wl);
             ok = __all_sync(0xffffffffu, ok);
             if (ok) {
@@ -362,7 +417,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                 if (quarter_live) {
                     const uint32_t d3 = tmem_base + lane_off + d3_col0;
                     for (int c0 = part * 16; c0 < rb3; c0 += 32) {
-                        float v[16], vi[16];
+                        float v[16], vi[16], e[16];
                         tc::tmem_ld16(d3 + c0, v);
                         tc::tmem_ld16(d3 + rb3 + c0, vi);
 #pragma unroll
@@ -372,9 +427,42 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                             const float x = d02 - f1, y = d02 + f1;
                             const float gd = fabsf(x) < lim ? (gauss ? __expf(ga_a * x * x) : __frcp_rn(x * x + h2)) : 0.f;
                             const float ga = fabsf(y) < lim ? (gauss ? __expf(ga_a * y * y) : __frcp_rn(y * y + h2)) : 0.f;
-                            const float w = ((one_n2 + n1) * gd + 2.f * (n1 - nn2) * ga) * if1;
-                            gs = fmaf(fmaf(v[i], v[i], vi[i] * vi[i]), w, gs);
-                            ws += w;
+                            const float v2 = fmaf(v[i], v[i], vi[i] * vi[i]);
+                            if (MODE == CHAIN_GT) {
+#pragma unroll
+                                for (int t = 0; t < kMaxT; ++t) {
+                                    const float n1t = s_n1t[t][jj];
+                                    gst[t] = fmaf(v2 * if1, (1.f + nn2t[t] + n1t) * gd + 2.f * (n1t - nn2t[t]) * ga, gst[t]);
+                                }
+                            } else {
+                                const float w = ((one_n2 + n1) * gd + 2.f * (n1 - nn2) * ga) * if1;
+                                if (MODE == CHAIN_GS) {
+                                    // full element weight; rows without a live mode add nothing (select,
+                                    // not product: such lanes of D3 may hold anything)
+                                    e[i] = live ? v2 * w * rowfac : 0.f;
+                                    gs += e[i];
+                                } else {
+                                    gs = fmaf(v2, w, gs);
+                                    ws += w;
+                                }
+                            }
+                        }
+                        if (MODE == CHAIN_GS) {
+                            // halving exchange: lanes 2c, 2c+1 end with the warp's sum of column c0 + c
+                            float a8[8], a4[4], a2[2];
+                            const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+                            for (int k = 0; k < 8; ++k)
+                                a8[k] = (b4 ? e[k + 8] : e[k]) + __shfl_xor_sync(0xffffffffu, b4 ? e[k] : e[k + 8], 16);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                a4[k] = (b3 ? a8[k + 4] : a8[k]) + __shfl_xor_sync(0xffffffffu, b3 ? a8[k] : a8[k + 4], 8);
+#pragma unroll
+                            for (int k = 0; k < 2; ++k)
+                                a2[k] = (b2 ? a4[k + 2] : a4[k]) + __shfl_xor_sync(0xffffffffu, b2 ? a4[k] : a4[k + 2], 4);
+                            float a1 = (b1 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? a2[0] : a2[1], 2);
+                            a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+                            if (!(lane & 1) && a1 != 0.f) atomicAdd(&s_col[li & 1][c0 + (lane >> 1)], a1);
                         }
                     }
                 }
@@ -385,17 +473,46 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
             }
             if (li + 1 < L) convert(li + 1);
             // all rows of the item belong to band nu: one warp sum, one atomic per warp
-            double dg = live ? (double)(gs * norm * inv_f02) : 0.0;
-            double dw = live ? (double)(ws * norm * inv_f02) : 0.0;
+            if (MODE == CHAIN_GT) {
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                dg += __shfl_xor_sync(0xffffffffu, dg, off);
-                dw += __shfl_xor_sync(0xffffffffu, dw, off);
+                for (int t = 0; t < kMaxT; ++t) {
+                    if (t >= args.n_t) break;
+                    double dg = live ? (double)(gst[t] * rowfac) : 0.0;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) dg += __shfl_xor_sync(0xffffffffu, dg, off);
+                    if (lane == 0 && ok && !abort_flag && dg != 0.0) atomicAdd(&args.gacc[t * args.t_stride + args.nu0 + nu], dg);
+                }
+            } else {
+                double dg = MODE == CHAIN_GS ? (double)gs : (live ? (double)(gs * rowfac) : 0.0);
+                double dw = live ? (double)(ws * rowfac) : 0.0;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    dg += __shfl_xor_sync(0xffffffffu, dg, off);
+                    if (MODE == CHAIN_G) dw += __shfl_xor_sync(0xffffffffu, dw, off);
+                }
+                if (lane == 0 && ok && !abort_flag) {
+                    if (dg != 0.0) atomicAdd(&args.gacc[args.nu0 + nu], dg);
+                    if (MODE == CHAIN_G && args.wacc && dw != 0.0) atomicAdd(&args.wacc[args.nu0 + nu], dw);
+                }
             }
-            if (lane == 0 && ok && !abort_flag) {
-                if (dg != 0.0) atomicAdd(&args.gacc[args.nu0 + nu], dg);
-                if (args.wacc && dw != 0.0) atomicAdd(&args.wacc[args.nu0 + nu], dw);
+            if (MODE == CHAIN_GS) {
+                // column (q'', nu''): this lane's row sum (over this warp's partner columns)
+                const float rs = args.g1_scale / f0;
+                if (ok && live && c2 != 0 && gs != 0.f && args.g1_row0 + nu < args.g1_rows) {
+                    const int64_t gc = (int64_t)(abs(c2) - 1) * n + nu2;
+                    if (gc < args.g1_ld)
+                        atomicAdd(args.g1 + (args.g1_row0 + nu) * args.g1_ld + gc, (c2 > 0 ? rs : -rs) * f2 * gs);
+                    else
+                        atomicExch(args.status, (int)PHX_ERR_INVALID);
+                }
+                prev_nu = nu;
+                prev_c1 = c1;
+                prev_rs = rs;
             }
+        }
+        if (MODE == CHAIN_GS) {
+            epi_barrier(kChainEpiThreads);
+            if (!abort_flag && prev_nu >= 0) flush_cols((L - 1) & 1);
         }
     }
     __syncthreads();

@@ -984,19 +984,26 @@ cudaError_t launch_gemm(phx_ctx* ctx, TcArgs& a, int n_problems, int ctas, cudaS
     return cudaGetLastError();
 }
 
-template <int PREC>
+template <int PREC, int MODE>
 cudaError_t launch_chain(ChainArgs& a, size_t smem, int ctas, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(chain_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(chain_kernel<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(kSmemLimit - 8192));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (a.n_items <= 0) return cudaSuccess;
     dim3 grid((unsigned)std::min(a.n_items, ctas), 1);
-    chain_kernel<PREC><<<grid, kChainThreads, smem, s>>>(a);
+    chain_kernel<PREC, MODE><<<grid, kChainThreads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_chain_mode(ChainArgs& a, int mode, size_t smem, int ctas, cudaStream_t s) {
+    if (mode == CHAIN_GT) return launch_chain<PREC, CHAIN_GT>(a, smem, ctas, s);
+    if (mode == CHAIN_GS) return launch_chain<PREC, CHAIN_GS>(a, smem, ctas, s);
+    return launch_chain<PREC, CHAIN_G>(a, smem, ctas, s);
 }
 
 template <int PREC, int EPI>
@@ -1265,7 +1272,13 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
         aC.freq = freq; aC.nB = nB;
         aC.sigma = (float)gp.sigma; aC.window = (float)gp.window; aC.f_min = (float)gp.f_min; aC.shape = gp.shape;
         aC.status = (int32_t*)ctx->status_word;
+        aC.n_t = n_t; aC.nb_stride = nb_stride; aC.t_stride = t_stride;
+        if (g1) {
+            aC.g1 = (float*)g1->mat; aC.g1_ld = g1->ld; aC.tr_code = g1->tr_code; aC.g1_scale = (float)g1->scale;
+            aC.g1_rows = (int64_t)n_irr * n;
+        }
     }
+    const int chain_mode = n_t > 0 ? CHAIN_GT : (g1 ? CHAIN_GS : CHAIN_G);
     aD.np = qp_np; aD.mg = qp_np; aD.n_groups = 1; aD.nk = P.nk_d; aD.stages = P.st_d;
     aD.n_acc = (4 * qp_np <= 512) ? 2 : 1;
     aD.tmem_cols = tmem_cols_for(2 * qp_np, aD.n_acc);
@@ -1338,8 +1351,9 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
                 if (P.chain) {
                     aC.n_items = Qt * nnu; aC.nnu = nnu; aC.rows_per_slot = (int)ra;
                     aC.qpp = B.qpp + t0; aC.t0 = t0; aC.nu0 = nu0;
+                    aC.g1_row0 = (int64_t)si * n + nu0;
                     pp = phx_prof_begin(ctx, s);
-                    PHX_CUDA_CHECK(ctx, launch_chain<PREC>(aC, P.c_smem, sms, s));
+                    PHX_CUDA_CHECK(ctx, launch_chain_mode<PREC>(aC, chain_mode, P.c_smem, sms, s));
                     // two contractions; bytes: the M operand read once
                     phx_prof_end(ctx, pp, s, PHX_K_CHAIN, 2.0 * fl_e, op_bytes * (double)Qt * ra * n);
                     ctx->launches += 2;
@@ -1372,7 +1386,7 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
                   cudaStream_t s, int n_t = 0, int64_t nb_stride = 0, int64_t t_stride = 0,
                   const G1Target* g1 = nullptr) {
     TcPlan P;
-    PHX_TRY(tc_plan(ctx, f, PREC, 0, &P, n_t == 0 && g1 == nullptr));   // chained kernel: plain linewidths only
+    PHX_TRY(tc_plan(ctx, f, PREC, 0, &P));
     PHX_TRY(tc_prepare_fc3(ctx, const_cast<phx_fc3*>(f)));
     TcBuffers B;
     PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.chain ? 0 : P.bytes_m, P.bytes_e, P.bytes_p, P.bytes_t, P.nq,

@@ -117,8 +117,15 @@ def test_fp64_matches_oracle(ctx, case):
 
 
 @pytest.mark.parametrize("precision,bar", [("bf16x3", True), ("tf32", False)])
-def test_tensor_core_within_bar(ctx, case, precision, bar):
-    r = _run(ctx, case, precision, want_gamma1=True)
+@pytest.mark.parametrize("chain", [1, 2])
+def test_tensor_core_within_bar(ctx, case, precision, bar, chain):
+    """chain 1: Gamma0 and Gamma1 from the chained tensor-core kernel (forced on below its
+    default mode range), 2: from the two GEMMs."""
+    ctx.set_option("chain", chain)
+    try:
+        r = _run(ctx, case, precision, want_gamma1=True)
+    finally:
+        ctx.set_option("chain", 0)
     e0 = _big_rel(r["gamma0"], case["g0"])
     e1 = _row_l1(r["gamma1"], case["g1"], case["g0"])
     e1f = float(np.linalg.norm(r["gamma1"] - case["g1"]) / np.linalg.norm(case["g1"]))

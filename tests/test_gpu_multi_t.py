@@ -29,20 +29,30 @@ def setup():
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32", "fp64"])
-def test_multi_t_equals_single_calls(setup, prec):
+@pytest.mark.parametrize("prec,chain", [("bf16x3", 2), ("tf32", 2), ("fp64", 0), ("bf16x3", 1), ("tf32", 1)])
+def test_multi_t_equals_single_calls(setup, prec, chain):
+    """chain 1: the chained tensor-core kernel (forced on at 6 modes), 2: the two GEMMs."""
     s = setup
-    g = s["ctx"].gamma_multi_t(s["h"], s["freq"], s["evec"], s["irr"], TEMPS, precision=prec)
-    assert g.shape == (len(TEMPS), len(s["irr"]), s["freq"].shape[1])
-    for t, T in enumerate(TEMPS):
-        one = s["ctx"].gamma(s["h"], s["freq"], s["evec"], s["irr"], T, precision=prec)
-        assert np.abs(g[t] - one).max() <= 1e-5 * one.max()
-    assert np.all(np.diff(g.max(axis=(1, 2))) > 0)       # more phonons, faster scattering
+    s["ctx"].set_option("chain", chain)
+    try:
+        g = s["ctx"].gamma_multi_t(s["h"], s["freq"], s["evec"], s["irr"], TEMPS, precision=prec)
+        assert g.shape == (len(TEMPS), len(s["irr"]), s["freq"].shape[1])
+        for t, T in enumerate(TEMPS):
+            one = s["ctx"].gamma(s["h"], s["freq"], s["evec"], s["irr"], T, precision=prec)
+            assert np.abs(g[t] - one).max() <= 1e-5 * one.max()
+        assert np.all(np.diff(g.max(axis=(1, 2))) > 0)       # more phonons, faster scattering
+    finally:
+        s["ctx"].set_option("chain", 0)
 
 
-def test_multi_t_matches_oracle(setup):
+@pytest.mark.parametrize("chain", [1, 2])
+def test_multi_t_matches_oracle(setup, chain):
     s = setup
-    g = s["ctx"].gamma_multi_t(s["h"], s["freq"], s["evec"], s["irr"], TEMPS, precision="bf16x3")
+    s["ctx"].set_option("chain", chain)
+    try:
+        g = s["ctx"].gamma_multi_t(s["h"], s["freq"], s["evec"], s["irr"], TEMPS, precision="bf16x3")
+    finally:
+        s["ctx"].set_option("chain", 0)
     fc3 = O.anharmonic.FC3(s["f3"].idx, s["f3"].val, s["c"].masses)
     sub = [0, 3, 7]
     ref0, v2 = O.anharmonic.gamma(fc3, s["mesh"], s["freq"], s["evec"], s["irr"][sub], TEMPS[0], keep_v2=True)

@@ -24,9 +24,9 @@
 // ones even with one accumulator of each kind.
 //
 // Warp roles (the tensor-memory lane quarter of warp w is w % 4; quarter 3 holds no mode):
-// warps 0-2 and 4-6 convert D2 and run the weighting epilogue on D3, warp 3 owns tensor
-// memory and issues the MMAs, warp 7 issues TMA loads (tables per q' slot, M chunks per
-// item).  Per item: stage 2 issues the Re-output MMAs, commits, then the Im-output MMAs, so
+// warps 0-2, 4-6 and 8-10 (three per quarter) convert D2 and run the weighting epilogue on
+// D3, warp 3 owns tensor memory and issues the MMAs, warp 7 issues TMA loads (tables per q'
+// slot, M chunks per item), warp 11 idles.  Per item: stage 2 issues the Re-output MMAs, commits, then the Im-output MMAs, so
 // the epilogue converts the Re half of X^T while the Im half accumulates; stage 3 consumes
 // the two halves in K order; the weighting of item i overlaps stage 2 of item i + 1.
 // Every wait is bounded.
@@ -73,9 +73,18 @@ struct ChainArgs {
 // the off-diagonal scattering rows
 enum { CHAIN_G = 0, CHAIN_GT = 1, CHAIN_GS = 2 };
 
-constexpr int kChainThreads = 256;
-constexpr int kChainEpiThreads = 192;     // warps 0-2 and 4-6
-constexpr int kChainMmaWarp = 3, kChainTmaWarp = 7;
+// 2^x by the special-function unit (approximate, flushes denormals; the weights use it on
+// arguments <= 0 only)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr int kChainThreads = 384;
+constexpr int kChainEpiParts = 3;                          // epilogue warps per tensor-memory lane quarter
+constexpr int kChainEpiThreads = 32 * 3 * kChainEpiParts;  // warps 0-2, 4-6, 8-10
+constexpr int kChainMmaWarp = 3, kChainTmaWarp = 7, kChainIdleWarp = 11;
 
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_constant__ ChainArgs args) {
@@ -87,9 +96,13 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
     __shared__ __align__(8) uint64_t d2_full[2], a3_ready[2], s3_done, d3_empty, drain_bar;
     __shared__ uint32_t tmem_base_slot;
     __shared__ volatile int abort_flag;
-    __shared__ float s_f1[kMaxNp], s_n1[kMaxNp], s_if1[kMaxNp];
+    __shared__ float4 s_tab[kMaxNp];       // per partner mode nu' at q': (f', n', 1/f' or 0, -)
     __shared__ float s_n1t[MODE == CHAIN_GT ? kMaxT : 1][MODE == CHAIN_GT ? kMaxNp : 1];
-    __shared__ float s_col[MODE == CHAIN_GS ? 2 : 1][MODE == CHAIN_GS ? kMaxNp : 1];   // Gamma1 column sums
+    // CHAIN_GS: per item (double-buffered) the Gamma1 column sums over nu'' (partners at q') and
+    // the row sums over nu' (partners at q''), and the q'' frequencies of the slot
+    __shared__ float s_col[MODE == CHAIN_GS ? 2 : 1][MODE == CHAIN_GS ? kMaxNp : 1];
+    __shared__ float s_row[MODE == CHAIN_GS ? 2 : 1][MODE == CHAIN_GS ? kMaxNp : 1];
+    __shared__ float s_f2[MODE == CHAIN_GS ? kMaxNp : 1];
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int n = args.n, kcp = args.kcp, nkc = args.nkc, ra = args.ra, rb3 = args.rb3;
@@ -293,11 +306,11 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
             while (!tc::mbar_try_wait(&drain_bar, 0) && tc::global_ns() - t0 < wl) {
             }
         }
-    } else if (L > 0) {
-        // ------------------------------------------------------------ epilogue (warps 0-2, 4-6)
-        const int et = (warp & 3) * 32 + (warp >> 2) * 96 + lane;   // 0 .. 191
+    } else if (warp != kChainIdleWarp && L > 0) {
+        // ------------------------------------------------------------ epilogue (warps 0-2, 4-6, 8-10)
+        const int et = (warp & 3) * 32 + (warp >> 2) * 96 + lane;   // 0 .. kChainEpiThreads - 1
         const int qd = warp & 3;                          // tensor-memory lane quarter (0..2)
-        const int part = warp >> 2;                       // 0 or 1
+        const int part = warp >> 2;                       // 0 .. kChainEpiParts - 1
         const int nu2 = qd * 32 + lane;                   // row of this thread (band nu'')
         const uint32_t lane_off = (uint32_t)(qd * 32) << 16;
         const bool quarter_live = qd * 32 < n;
@@ -314,7 +327,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                 tc::tc_fence_after();
                 if (quarter_live) {
                     const uint32_t base = tmem_base + lane_off + (uint32_t)(h * kcp);
-                    for (int ch = part; ch < kcp / 32; ch += 2) {
+                    for (int ch = part; ch < kcp / 32; ch += kChainEpiParts) {
                         float v[32];
                         tc::tmem_ld16(base + 32 * ch, v);
                         tc::tmem_ld16(base + 32 * ch + 16, v + 16);
@@ -341,8 +354,10 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
 
         const bool gauss = args.shape == PHX_GAUSS;
         const float sg = args.sigma, lim = args.window * sg;
-        const float ga_a = -1.f / (sg * sg), h2 = 0.25f * sg * sg;
+        // Gaussian: exp(-x^2/s^2) = 2^(ga2 x^2) with ga2 = -log2(e)/s^2 (one ex2 instruction)
+        const float ga2 = -1.4426950408889634f / (sg * sg), h2 = 0.25f * sg * sg;
         const float norm = gauss ? 0.56418958354775628f / sg : 0.5f * sg / 3.14159265358979f;
+        const bool want_w = MODE == CHAIN_G && args.wacc != nullptr;
         float nn2t[kMaxT];
 #pragma unroll
         for (int t = 0; t < kMaxT; ++t) nn2t[t] = 0.f;
@@ -350,29 +365,48 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
         // CHAIN_GS: the column sums of item li are complete once every epilogue thread has passed
         // the barrier at the start of item li + 1; they are flushed to Gamma1 there (before the
         // partner tables change) from a buffer the next item does not use
-        int prev_nu = -1, prev_c1 = 0;
+        int prev_nu = -1, prev_c1 = 0, prev_c2 = 0;
         float prev_rs = 0.f;
-        auto flush_cols = [&](int buf) {
-            for (int j = et; j < rb3; j += kChainEpiThreads) {
-                const float val = s_col[buf][j];
-                s_col[buf][j] = 0.f;
-                if (val == 0.f || prev_c1 == 0 || j >= n || args.g1_row0 + prev_nu >= args.g1_rows) continue;
-                const int64_t gc = (int64_t)(abs(prev_c1) - 1) * n + j;
-                if (gc < args.g1_ld)
-                    atomicAdd(args.g1 + (args.g1_row0 + prev_nu) * args.g1_ld + gc,
-                              (prev_c1 > 0 ? prev_rs : -prev_rs) * s_f1[j] * val);
+        // Gamma1 row (q, nu) of the previous item += its column sums x f'/f at the q' block and its
+        // row sums x f''/f at the q'' block: 16-byte reductions of four adjacent entries when n is a
+        // multiple of 4 (rows are 128-entry aligned), single ones otherwise; the buffer is zeroed
+        const bool vec4 = (n & 3) == 0;
+        auto flush_sums = [&](int buf) {
+            const bool row_ok = prev_nu >= 0 && args.g1_row0 + prev_nu < args.g1_rows;
+            float* grow = args.g1 + (args.g1_row0 + prev_nu) * args.g1_ld;
+            const int per = vec4 ? 4 : 1, nb = (rb3 + per - 1) / per;
+            for (int t = et; t < 2 * nb; t += kChainEpiThreads) {
+                const bool rows = t >= nb;                   // 0: columns at q', 1: rows at q''
+                const int j0 = (rows ? t - nb : t) * per;
+                const int code = rows ? prev_c2 : prev_c1;
+                float* src = rows ? &s_row[buf][j0] : &s_col[buf][j0];
+                float v[4] = {0.f, 0.f, 0.f, 0.f}, fp[4] = {0.f, 0.f, 0.f, 0.f};
+                bool any = false;
+                for (int k = 0; k < per; ++k) {
+                    v[k] = src[k];
+                    src[k] = 0.f;
+                    fp[k] = rows ? s_f2[j0 + k] : s_tab[j0 + k].x;
+                    any |= v[k] != 0.f && j0 + k < n;
+                }
+                if (!any || code == 0 || !row_ok) continue;
+                const float r = code > 0 ? prev_rs : -prev_rs;
+                const int64_t gc = (int64_t)(abs(code) - 1) * n + j0;
+                if (gc + per - 1 >= args.g1_ld) { atomicExch(args.status, (int)PHX_ERR_INVALID); continue; }   // bounds self-check
+                if (vec4)
+                    atomicAdd(reinterpret_cast<float4*>(grow + gc),
+                              make_float4(r * fp[0] * v[0], r * fp[1] * v[1], r * fp[2] * v[2], r * fp[3] * v[3]));
                 else
-                    atomicExch(args.status, (int)PHX_ERR_INVALID);     // bounds self-check
+                    atomicAdd(grow + gc, r * fp[0] * v[0]);
             }
         };
         if (MODE == CHAIN_GS)
-            for (int j = et; j < 2 * kMaxNp; j += kChainEpiThreads) (&s_col[0][0])[j] = 0.f;
+            for (int j = et; j < 2 * kMaxNp; j += kChainEpiThreads) { (&s_col[0][0])[j] = 0.f; (&s_row[0][0])[j] = 0.f; }
         convert(0);
         for (int li = 0; li < L; ++li) {
             const int it = item_begin + li;
             const int p = it / nnu, nu = it % nnu;
             if (epi_barrier_any(kChainEpiThreads, abort_flag != 0)) break;   // one decision for all
-            if (MODE == CHAIN_GS && li > 0) flush_cols((li - 1) & 1);
+            if (MODE == CHAIN_GS && li > 0) flush_sums((li - 1) & 1);
             if (p != cur_p) {
                 // partner tables of this slot's q' (every thread has finished the previous item:
                 // barrier above) and this thread's row constants at q''
@@ -381,9 +415,10 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                 for (int j = et; j < rb3; j += kChainEpiThreads) {
                     const bool v = j < n;
                     const float f1 = v ? (float)args.freq[(int64_t)q1 * n + j] : 0.0f;
-                    s_f1[j] = f1;
-                    s_n1[j] = v ? (float)args.nB[(int64_t)q1 * n + j] : 0.0f;
-                    s_if1[j] = (v && f1 >= args.f_min) ? 1.0f / f1 : 0.0f;   // 0 masks padding and soft partners
+                    // 1/f' = 0 masks padding and soft partners
+                    s_tab[j] = make_float4(f1, v ? (float)args.nB[(int64_t)q1 * n + j] : 0.0f,
+                                           (v && f1 >= args.f_min) ? 1.0f / f1 : 0.0f, 0.0f);
+                    if (MODE == CHAIN_GS) s_f2[j] = v ? (float)args.freq[(int64_t)q2 * n + j] : 0.0f;
                     if (MODE == CHAIN_GT)
                         for (int t = 0; t < kMaxT; ++t)
                             s_n1t[t][j] = (v && t < args.n_t) ? (float)args.nB[t * args.nb_stride + (int64_t)q1 * n + j]
@@ -416,17 +451,18 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                 tc::tc_fence_after();
                 if (quarter_live) {
                     const uint32_t d3 = tmem_base + lane_off + d3_col0;
-                    for (int c0 = part * 16; c0 < rb3; c0 += 32) {
+                    for (int c0 = part * 16; c0 < rb3; c0 += 16 * kChainEpiParts) {
                         float v[16], vi[16], e[16];
                         tc::tmem_ld16(d3 + c0, v);
                         tc::tmem_ld16(d3 + rb3 + c0, vi);
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             const int jj = c0 + i;
-                            const float f1 = s_f1[jj], n1 = s_n1[jj], if1 = s_if1[jj];
+                            const float4 tb = s_tab[jj];
+                            const float f1 = tb.x, n1 = tb.y, if1 = tb.z;
                             const float x = d02 - f1, y = d02 + f1;
-                            const float gd = fabsf(x) < lim ? (gauss ? __expf(ga_a * x * x) : __frcp_rn(x * x + h2)) : 0.f;
-                            const float ga = fabsf(y) < lim ? (gauss ? __expf(ga_a * y * y) : __frcp_rn(y * y + h2)) : 0.f;
+                            const float gd = fabsf(x) < lim ? (gauss ? ex2_approx(ga2 * x * x) : __frcp_rn(x * x + h2)) : 0.f;
+                            const float ga = fabsf(y) < lim ? (gauss ? ex2_approx(ga2 * y * y) : __frcp_rn(y * y + h2)) : 0.f;
                             const float v2 = fmaf(v[i], v[i], vi[i] * vi[i]);
                             if (MODE == CHAIN_GT) {
 #pragma unroll
@@ -443,7 +479,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                                     gs += e[i];
                                 } else {
                                     gs = fmaf(v2, w, gs);
-                                    ws += w;
+                                    if (want_w) ws += w;
                                 }
                             }
                         }
@@ -496,23 +532,17 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                 }
             }
             if (MODE == CHAIN_GS) {
-                // column (q'', nu''): this lane's row sum (over this warp's partner columns)
-                const float rs = args.g1_scale / f0;
-                if (ok && live && c2 != 0 && gs != 0.f && args.g1_row0 + nu < args.g1_rows) {
-                    const int64_t gc = (int64_t)(abs(c2) - 1) * n + nu2;
-                    if (gc < args.g1_ld)
-                        atomicAdd(args.g1 + (args.g1_row0 + nu) * args.g1_ld + gc, (c2 > 0 ? rs : -rs) * f2 * gs);
-                    else
-                        atomicExch(args.status, (int)PHX_ERR_INVALID);
-                }
+                // column (q'', nu''): this lane's row sum over this warp's partner columns
+                if (ok && live && gs != 0.f) atomicAdd(&s_row[li & 1][nu2], gs);
                 prev_nu = nu;
                 prev_c1 = c1;
-                prev_rs = rs;
+                prev_c2 = c2;
+                prev_rs = args.g1_scale / f0;
             }
         }
         if (MODE == CHAIN_GS) {
             epi_barrier(kChainEpiThreads);
-            if (!abort_flag && prev_nu >= 0) flush_cols((L - 1) & 1);
+            if (!abort_flag && prev_nu >= 0) flush_sums((L - 1) & 1);
         }
     }
     __syncthreads();

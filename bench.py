@@ -603,24 +603,65 @@ def run_batched(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
-    # the same jobs as sequential single-job calls (no graph, default tiles)
+    # the same jobs as sequential single-job calls (no graph, default tiles), with the library's
+    # per-launch events on: device time per kernel class and per job
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile_enable(True)
+    per_job_ms = []
     e0.record(stream)
     for j in jobs:
+        j0, j1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        j0.record(stream)
         ctx.gamma(j["fc3"], j["freq"], j["evec"], j["irr_dev"], j["T"], j["shape"], j["sigma"], j["window"],
                   j["f_min"], precision=args.precision, gamma=torch.zeros_like(j["gamma"]))
+        j1.record(stream)
+        per_job_ms.append((j0, j1))
     e1.record(stream)
     torch.cuda.synchronize()
     ms_seq = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    seq_kernel_ms = {k: v[0] for k, v in prof.items() if k != "launches" and v[1] > 0}
+    per_job_ms = [a.elapsed_time(b) for a, b in per_job_ms]
     sizes = [(3 * w.crystal.n_atoms, w.mesh[0]) for w in sweep]
+    # the FP64 GPU path (same algorithm, FP64 operands) on one irreducible q-point of every job:
+    # its rate, and the error of the batched linewidths of that q-point against it
+    fp64 = None
+    if args.fp64_q > 0:
+        t64, trip64, errs = 0.0, 0, []
+        for j in jobs:
+            k = min(1, len(j["irr"]) - 1)
+            sub = j["irr_dev"][k:k + 1].contiguous()
+            g64 = torch.zeros((1, j["gamma"].shape[1]), dtype=torch.float64, device=dev)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            ctx.gamma(j["fc3"], j["freq"], j["evec"], sub, j["T"], j["shape"], j["sigma"], j["window"], j["f_min"],
+                      precision="fp64", gamma=g64)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            t64 += a0.elapsed_time(a1) / 1e3
+            fr = j["freq"].cpu().numpy()
+            nqj, nj = fr.shape
+            trip64 += int((fr[int(j["irr"][k])] >= j["f_min"]).sum()) * nqj * nj * nj
+            ref = g64.cpu().numpy()[0]
+            got = j["gamma"][k].cpu().numpy()
+            big = ref > 1e-3 * ref.max()
+            errs.append(float((np.abs(got - ref)[big] / ref[big]).max()) if big.any() else 0.0)
+        fp64 = {"value": trip64 / t64, "unit": UNIT, "sample": "one irreducible q-point per job",
+                "gamma_max_rel_err_vs_fp64": max(errs), "per_job_gamma_err": errs}
     line = {"metric": METRIC, "value": trip / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.precision, "data": "synthetic",
             "config": {"workload": f"batched sweep: first {n_take} of 64 seeded mass-disordered LJ fcc cells "
                                    "(seed 3), (modes, mesh edge) = " + json.dumps(sizes),
                        "triplets_per_step": trip, "jobs": n_take},
-            "sequential_single_job_calls": {"value": trip / (ms_seq / 1e3), "ms": ms_seq},
+            "sequential_single_job_calls": {"value": trip / (ms_seq / 1e3), "ms": ms_seq,
+                                            "kernel_ms": seq_kernel_ms, "per_job_ms": per_job_ms,
+                                            "note": "timed with per-launch events on"},
             "first_call_s_incl_autotune_and_capture": t_first, "setup_s": t_setup}
+    if fp64:
+        line["fp64_path"] = fp64
+        line["speedup_vs_fp64_path"] = line["value"] / fp64["value"]
     clocks = clk.summary()
     if clocks:
         line["clocks"] = clocks

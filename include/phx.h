@@ -255,9 +255,11 @@ phx_status phx_gamma_cell(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_t
  * conductivity (as phx_unfold + phx_kappa_rta) are enqueued as one CUDA graph, captured on the
  * first call and replayed by later calls with the same job list (same pointers and
  * parameters).  Job arrays are device memory except irr_q (host).  Precision PHX_BF16X3 or
- * PHX_TF32.  The q' tile of each job class (modes, mesh, lattice differences) is taken from
- * tune[j].q_tile when tune is given and > 0, else chosen by timing the candidates 8..128 on
- * one irreducible q-point of the first job of the class (cached per context).
+ * PHX_TF32.  The q' tile and the contraction kernel of each job class (modes, mesh, lattice
+ * differences) are taken from tune[j] when tune is given and tune[j].q_tile > 0, else chosen
+ * by timing every candidate (q' tiles 8..128, and where it fits for the class the chained
+ * kernel against the two GEMMs) twice on one irreducible q-point of the first job of the
+ * class and keeping the fastest (cached per context).
  * The call enqueues on `stream` (ordered after work already on it) and returns without
  * synchronising.  Errors: as phx_gamma; PHX_ERR_UNSUPPORTED for PHX_FP64. */
 typedef struct {
@@ -279,7 +281,9 @@ typedef struct {
 } phx_job;
 
 typedef struct {
-    int32_t q_tile;                /* q' per Fourier tile; 0 = autotune                   */
+    int32_t q_tile;                /* q' per Fourier tile; 0 = autotune (tile and kernel)  */
+    int32_t chain;                 /* with q_tile > 0: 1 chained kernel (if it fits), 0 the
+                                      two GEMMs, -1 as PHX_OPT_CHAIN                       */
 } phx_tune;
 
 phx_status phx_gamma_batched(phx_ctx* ctx, int32_t n_jobs, const phx_job* jobs, int32_t prec,

@@ -54,7 +54,7 @@ class Job(C.Structure):
 
 
 class Tune(C.Structure):
-    _fields_ = [("q_tile", C.c_int32)]
+    _fields_ = [("q_tile", C.c_int32), ("chain", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -387,11 +387,13 @@ class Context:
                                        PRECISIONS[precision], _ptr(gamma), mem, stream))
         return gamma
 
-    def gamma_batched(self, jobs, precision="bf16x3", q_tiles=None):
+    def gamma_batched(self, jobs, precision="bf16x3", q_tiles=None, chain=None):
         """phx_gamma_batched.  jobs: list of dicts with keys fc3 (FC3), freq, evec (CUDA tensors),
         irr (numpy int32), irr_dev (CUDA int32), T, shape, sigma, window, f_min, gamma (CUDA out),
         and optionally vv, full_to_irr, gamma_full, kappa (CUDA) and volume for the conductivity.
-        q_tiles: None (autotune) or a list of q' tiles per job."""
+        q_tiles: None (autotune the tile and the contraction kernel) or a list of q' tiles per
+        job; chain: with q_tiles, a list per job (1 chained kernel, 0 two GEMMs, -1 context
+        option) or None (-1 for all)."""
         import torch
         arr = (Job * len(jobs))()
         keep = []
@@ -419,6 +421,7 @@ class Context:
             tune = (Tune * len(jobs))()
             for k, q in enumerate(q_tiles):
                 tune[k].q_tile = int(q)
+                tune[k].chain = -1 if chain is None else int(chain[k])
         dev = jobs[0]["freq"].device if jobs else torch.device("cuda", self.device)
         stream = torch.cuda.current_stream(dev).cuda_stream
         self._check(lib.phx_gamma_batched(self.h, len(jobs), C.addressof(arr), PRECISIONS[precision],

@@ -49,7 +49,7 @@ struct phx_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<uint8_t> graph_key;
     int64_t graph_launches = 0;
-    std::map<std::vector<int>, int> tune_q;
+    std::map<std::vector<int>, std::pair<int, int>> tune_q;   // job class -> (q' tile, chained kernel)
     // options (phx_set_option)
     int opt_chain = 0;                            // 0 auto, 1 force the chained kernel, 2 never
     unsigned long long opt_wait_ns = 2000000000ull;   // bound of every device barrier wait

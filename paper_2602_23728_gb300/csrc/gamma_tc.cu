@@ -1072,7 +1072,8 @@ bool chain_shapes(TcPlan& P) {
     return true;
 }
 
-phx_status tc_plan(phx_ctx* ctx, const phx_fc3* f, int prec, int q_override, TcPlan* pl, bool allow_chain = true) {
+// chain_pref: -1 follows PHX_OPT_CHAIN, 0 never, 1 wherever the chained kernel fits
+phx_status tc_plan(phx_ctx* ctx, const phx_fc3* f, int prec, int q_override, TcPlan* pl, int chain_pref = -1) {
     TcPlan P;
     P.prec = prec;
     const int n = f->n, nq = f->nq;
@@ -1143,8 +1144,8 @@ phx_status tc_plan(phx_ctx* ctx, const phx_fc3* f, int prec, int q_override, TcP
     // Chained contractions: by default where they beat the three-GEMM chain (64 < n <= 96: the
     // MMA rows are modes, so small n would leave most of the 128 rows idle); PHX_OPT_CHAIN
     // forces them on (any n they fit) or off.
-    const int oc = ctx->opt_chain;
-    if (allow_chain && oc != 2 && (oc == 1 || (n > 64 && n <= 96))) P.chain = chain_shapes(P);
+    const int oc = chain_pref == 0 ? 2 : chain_pref == 1 ? 1 : ctx->opt_chain;
+    if (oc != 2 && (oc == 1 || (n > 64 && n <= 96))) P.chain = chain_shapes(P);
     if (P.chain) {
         P.bytes_t = (size_t)nq * n * P.kr * esz;
         P.bytes_e = 0;
@@ -1423,8 +1424,11 @@ phx_status phx_gamma_tc_multi_t(phx_ctx* ctx, const phx_fc3* f, const double* fr
 
 namespace {
 
+// Best (q' tile, contraction kernel) of a job class: every tile 8..128 with the two GEMMs and,
+// where it fits, with the chained kernel, each timed twice (the faster sample counts) on one
+// irreducible q-point of the job.
 template <int PREC>
-phx_status autotune_q(phx_ctx* ctx, const phx_job& job, cudaStream_t s, int* best_q) {
+phx_status autotune_q(phx_ctx* ctx, const phx_job& job, cudaStream_t s, int* best_q, int* best_chain) {
     const phx_fc3* f = job.fc3;
     const int iq = job.irr_q[job.n_irr > 1 ? 1 : 0];
     GammaParams gp{};
@@ -1435,25 +1439,31 @@ phx_status autotune_q(phx_ctx* ctx, const phx_job& job, cudaStream_t s, int* bes
     if (!nB || !gacc) return PHX_ERR_NOMEM;
     PHX_CUDA_CHECK(ctx, phx_launch_occupations(job.freq_thz, f->nq * f->n, job.temperature, 0, nB, nullptr, s));
     float best_ms = 1e30f;
-    int last_q = -1;
     *best_q = 0;
-    for (int cand : {8, 16, 32, 64, 128}) {
-        TcPlan P;
-        if (tc_plan(ctx, f, PREC, cand, &P) != PHX_OK) continue;
-        if (P.Q == last_q) continue;                 // clamped to the mesh size already tried
-        last_q = P.Q;
-        TcBuffers B;
-        PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.chain ? 0 : P.bytes_m, P.bytes_e, P.bytes_p, P.bytes_t, P.nq,
-                     f->nnz, (int64_t)P.n * P.n, &B));
-        float ms = 0.f;
-        for (int rep = 0; rep < 2; ++rep) {
-            PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_in, s));
-            PHX_TRY(tc_enqueue<PREC>(ctx, P, f, B, job.freq_thz, job.evec, nB, &iq, 1, gp, gacc, nullptr, s));
-            PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_out, s));
-            PHX_CUDA_CHECK(ctx, cudaEventSynchronize(ctx->ev_out));
-            PHX_CUDA_CHECK(ctx, cudaEventElapsedTime(&ms, ctx->ev_in, ctx->ev_out));
+    *best_chain = 0;
+    for (int chain = 0; chain < 2; ++chain) {
+        int last_q = -1;
+        for (int cand : {8, 16, 32, 64, 128}) {
+            TcPlan P;
+            if (tc_plan(ctx, f, PREC, cand, &P, chain) != PHX_OK) continue;
+            if (P.chain != (chain == 1)) break;          // the chained kernel does not fit this class
+            if (P.Q == last_q) continue;                 // clamped to the mesh size already tried
+            last_q = P.Q;
+            TcBuffers B;
+            PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.chain ? 0 : P.bytes_m, P.bytes_e, P.bytes_p, P.bytes_t,
+                             P.nq, f->nnz, (int64_t)P.n * P.n, &B));
+            float best_rep = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                float ms = 0.f;
+                PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_in, s));
+                PHX_TRY(tc_enqueue<PREC>(ctx, P, f, B, job.freq_thz, job.evec, nB, &iq, 1, gp, gacc, nullptr, s));
+                PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_out, s));
+                PHX_CUDA_CHECK(ctx, cudaEventSynchronize(ctx->ev_out));
+                PHX_CUDA_CHECK(ctx, cudaEventElapsedTime(&ms, ctx->ev_in, ctx->ev_out));
+                best_rep = std::min(best_rep, ms);
+            }
+            if (best_rep < best_ms) { best_ms = best_rep; *best_q = P.Q; *best_chain = chain; }
         }
-        if (ms < best_ms) { best_ms = ms; *best_q = P.Q; }
     }
     if (*best_q == 0) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "autotune: no q' tile fits");
     return PHX_OK;
@@ -1473,23 +1483,26 @@ phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, const phx_
 
     // plans (q' tile from the caller, the autotune table, or a fresh tuning run)
     std::vector<TcPlan> plans(n_jobs);
-    std::vector<int> qtiles(n_jobs, 0);
+    std::vector<int> qtiles(n_jobs, 0), chains(n_jobs, -1);
     for (int j = 0; j < n_jobs; ++j) {
         const phx_job& jb = jobs[j];
         PHX_TRY(tc_prepare_fc3(ctx, const_cast<phx_fc3*>(jb.fc3)));
         int q = (tune && tune[j].q_tile > 0) ? tune[j].q_tile : 0;
+        int ch = (tune && tune[j].q_tile > 0) ? tune[j].chain : -1;
         if (q == 0) {
             const std::vector<int> key = {PREC, jb.fc3->n, jb.fc3->mesh[0], jb.fc3->mesh[1], jb.fc3->mesh[2], jb.fc3->n_d};
             auto it = ctx->tune_q.find(key);
             if (it == ctx->tune_q.end()) {
-                PHX_TRY(autotune_q<PREC>(ctx, jb, cs, &q));
-                ctx->tune_q[key] = q;
+                PHX_TRY(autotune_q<PREC>(ctx, jb, cs, &q, &ch));
+                ctx->tune_q[key] = {q, ch};
             } else {
-                q = it->second;
+                q = it->second.first;
+                ch = it->second.second;
             }
         }
         qtiles[j] = q;
-        PHX_TRY(tc_plan(ctx, jb.fc3, PREC, q, &plans[j]));
+        chains[j] = ch;
+        PHX_TRY(tc_plan(ctx, jb.fc3, PREC, q, &plans[j], ch));
     }
     // workspace for the largest job, allocated before any capture
     size_t bw = 0, bm = 0, bx = 0, be = 0, bp = 0, bt = 0;
@@ -1512,11 +1525,12 @@ phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, const phx_
     if (!nB || !gacc || !acc9) return PHX_ERR_NOMEM;
 
     // graph key: the job list, the precision and the tiles
-    std::vector<uint8_t> key(sizeof(phx_job) * n_jobs + sizeof(int) * (n_jobs + 1));
+    std::vector<uint8_t> key(sizeof(phx_job) * n_jobs + sizeof(int) * (2 * n_jobs + 1));
     std::memcpy(key.data(), jobs, sizeof(phx_job) * n_jobs);
     std::memcpy(key.data() + sizeof(phx_job) * n_jobs, qtiles.data(), sizeof(int) * n_jobs);
+    std::memcpy(key.data() + sizeof(phx_job) * n_jobs + sizeof(int) * n_jobs, chains.data(), sizeof(int) * n_jobs);
     const int prec_v = PREC;
-    std::memcpy(key.data() + sizeof(phx_job) * n_jobs + sizeof(int) * n_jobs, &prec_v, sizeof(int));
+    std::memcpy(key.data() + sizeof(phx_job) * n_jobs + sizeof(int) * 2 * n_jobs, &prec_v, sizeof(int));
     // host irr lists are part of the key by content
     for (int j = 0; j < n_jobs; ++j) {
         const uint8_t* b = (const uint8_t*)jobs[j].irr_q;

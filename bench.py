@@ -963,6 +963,78 @@ def run_sc(args):
     return 0
 
 
+def run_sc64(args):
+    """Iterative BTE on a 64-atom cell (4x4x4 primitive LJ fcc, 50/50 masses 39.95/83.8 seed 11,
+    192 modes) on a 12x12x12 mesh at 50 K, Gaussian 0.1 THz: 868 time-reversal representatives,
+    Gamma1 of 166,656 x 166,656 in FP32 (111 GB) held on the device.  One step, as fcc32-sc."""
+    import torch
+    import paper_2602_23728_gb300 as phx
+    import phx_inputs as P
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctx = phx.Context(0)
+    c = P.random_masses(P.fcc_primitive_multiple(5.26, (4, 4, 4)), 39.95, 83.8, seed=11)
+    mesh = (12, 12, 12)
+    f2, f3 = P.ifc_lj_vectorised(c, P.LennardJones())
+    nq, n = int(np.prod(mesh)), c.n_modes
+    qh = np.array([(i // (mesh[1] * mesh[2]) / mesh[0], (i // mesh[2]) % mesh[1] / mesh[1], i % mesh[2] / mesh[2])
+                   for i in range(nq)])
+    q = torch.from_numpy(qh).to(dev)
+    freq = torch.zeros((nq, n), dtype=torch.float64, device=dev)
+    evec = torch.zeros((nq, n, n), dtype=torch.complex128, device=dev)
+    vel = torch.zeros((nq, n, 3), dtype=torch.float64, device=dev)
+    h = ctx.fc3(c.lattice, c.masses, f3.idx, f3.val, mesh)
+    n_tr = phx.time_reversal_count(mesh)
+    g0 = torch.zeros((n_tr, n), dtype=torch.float64, device=dev)
+    mfp = torch.zeros((n_tr, n, 3), dtype=torch.float64, device=dev)
+
+    def step():
+        ctx.harmonic(c.lattice, c.masses, f2.idx, f2.val.reshape(-1, 9), q, freq=freq, evec=evec, vel=vel,
+                     want_vv=False)
+        return ctx.kappa_sc(c.lattice, c.masses, h, freq, evec, vel, 50.0, shape="gauss", sigma=0.1, window=2.0,
+                            f_min=0.01, max_iter=args.sc_iter, tol=args.sc_tol, precision=args.precision,
+                            gamma0=g0, mfp=mfp)
+
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        r = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    fr = freq.cpu().numpy()
+    irr_tr = np.unique([min(i, int(O_neg)) for i, O_neg in enumerate(_neg_index(mesh))])
+    trip = int((fr[irr_tr] >= 0.01).sum()) * nq * n * n
+    R = n_tr * n
+    line = {"metric": METRIC, "value": trip / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "cell64-mesh12 iterative BTE: 64-atom LJ fcc (4x4x4 primitive, masses 39.95/83.8 "
+                                   "seed 11), 192 modes, 12x12x12, 50 K, Gauss 0.1 THz; Gamma1 over the %d "
+                                   "time-reversal representatives (R = %d rows, %.0f GB in FP32)"
+                                   % (n_tr, R, R * ((R + 127) // 128 * 128) * 4 / 1e9),
+                       "triplets_per_step": trip},
+            "kappa_rta_wmk": float(np.trace(r["kappa"][0]) / 3), "kappa_sc_wmk": float(np.trace(r["kappa"][-1]) / 3),
+            "iterations": r["n_iter"], "converged": r["converged"]}
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+    print(json.dumps(line, default=float), flush=True)
+    ctx.close()
+    return 0
+
+
+def _neg_index(mesh):
+    m1, m2, m3 = mesh
+    out = []
+    for i in range(m1 * m2 * m3):
+        a, b, c = i // (m2 * m3), (i // m3) % m2, i % m3
+        out.append((((m1 - a) % m1) * m2 + (m2 - b) % m2) * m3 + (m3 - c) % m3)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -979,7 +1051,7 @@ def main():
     ap.add_argument("--ref-qp", type=int, default=64, help="q' per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="fcc32",
-                    choices=["fcc32", "fcc32-sc", "batched16", "batched64", "surrogate24", "cell1000"],
+                    choices=["fcc32", "fcc32-sc", "sc64-mesh12", "batched16", "batched64", "surrogate24", "cell1000"],
                     help="fcc32: the headline workload; batched16/64: the many-crystal sweep; surrogate24: the "
                          "learned-linewidth pipeline; cell1000: the Gamma-only 1000-atom disordered cell "
                          "(each its own JSON line); fcc32-sc: the iterative BTE on the headline crystal")
@@ -1004,6 +1076,8 @@ def main():
         return run_cell(args)
     if args.workload == "fcc32-sc":
         return run_sc(args)
+    if args.workload == "sc64-mesh12":
+        return run_sc64(args)
     return run_phx(args)
 
 

@@ -380,8 +380,9 @@ phx_status phx_kappa_rta(phx_ctx* ctx, const phx_cell* cell, int32_t nq, int32_t
  *    linewidth sum, with weight w (decay + absorption term), adds w f'/f at column (q', nu')
  *    and w f''/f at column (q'' = -q-q', nu''); a column of a point listed through -q is
  *    added with sign -1.  Gamma1 stays on the device, R x R in FP64 (prec = PHX_FP64) or
- *    FP32 (tensor-core precisions); inputs whose Gamma1 exceeds 96 GB return
- *    PHX_ERR_UNSUPPORTED.  Its entries are accumulated with atomic adds (FP64 or FP32), so
+ *    FP32 (tensor-core precisions); inputs whose Gamma1 does not fit in the device memory
+ *    free at the call less 32 GB (kept for the contraction's workspace) return
+ *    PHX_ERR_UNSUPPORTED (R x R x 4 bytes: 111 GB for 192 modes on a 12^3 mesh).  Its entries are accumulated with atomic adds (FP64 or FP32), so
  *    two calls on the same inputs agree to rounding, not bit for bit.
  *  - Iteration (Eq. sc_iter) lambda^(k+1) = (v - Gamma1 lambda^(k)) / Gamma0 stops at the
  *    first k >= 1 with |Tr kappa^(k) - Tr kappa^(k-1)| < tol |Tr kappa^(k-1)| (*converged =

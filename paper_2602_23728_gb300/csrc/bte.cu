@@ -244,12 +244,19 @@ phx_status phx_kappa_sc(phx_ctx* ctx, const phx_cell* cell, const phx_fc3* fc3, 
     const int64_t ld = (R + kLdAlign - 1) / kLdAlign * kLdAlign;
     const size_t esz = prec == PHX_FP64 ? 8 : 4;
     const size_t mat_bytes = (size_t)R * ld * esz;
-    if (R > INT32_MAX / 4 || mat_bytes > ((size_t)96 << 30))
-        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED,
-                             "phx_kappa_sc: Gamma1 of %lld rows needs %.1f GB (limit 96 GB)", (long long)R,
-                             mat_bytes / 1e9);
-
     cudaSetDevice(ctx->device);
+    // Gamma1 is held densely: it must fit in the device memory still free, less room for the
+    // contraction's own workspace (operands of one q' tile, a few GB to ~25 GB at 192 modes)
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 0; }
+    const size_t reserve = (size_t)32 << 30;
+    const size_t have = ctx->ws.count("sc.G1") ? ctx->ws["sc.G1"].second : 0;   // reused in place
+    const size_t avail = free_b + have > reserve ? free_b + have - reserve : 0;
+    if (R > INT32_MAX / 4 || mat_bytes > avail)
+        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED,
+                             "phx_kappa_sc: Gamma1 of %lld rows needs %.1f GB (%.1f GB of device memory available)",
+                             (long long)R, mat_bytes / 1e9, avail / 1e9);
+
     cudaStream_t s = as_stream(stream);
     const int64_t n2 = (int64_t)n * n;
     const double *d_f = nullptr, *d_e = nullptr, *d_v = nullptr;

@@ -3,8 +3,8 @@ Gamma0, the folded Gamma1 matrix, every kappa iterate and the mean free paths.  
 rounding; BF16x3 within the linewidth bar on Gamma0 and on the l1 error of every Gamma1 row
 relative to its Gamma0, and within the kappa bar on every iterate; TF32 reported.  Cases: a
 two-atom cell (segmented column sums: n = 6), both broadenings, odd and even meshes (points with q = -q); the 32-atom cell (n = 96: whole-warp
-column sums) on a 3x1x1 mesh; and, marked slow, the 8x8x8 bench configuration on one sampled
-representative's rows."""
+column sums) on a 3x1x1 mesh; a 64-atom cell (192 modes) on a 3x1x1 mesh; and, marked slow, the
+8x8x8 bench configuration on one sampled representative's rows."""
 import numpy as np
 import pytest
 
@@ -62,6 +62,10 @@ def _case(c, mesh, T, shape, sigma, n_iter=8):
                 g1=g1, hist=hist, lam=lam, vol=vol, irr=irr, pos=pos, n_iter=n_iter)
 
 
+def _cell64():
+    return P.random_masses(P.fcc_primitive_multiple(5.26, (4, 4, 4)), 39.95, 83.8, seed=11)
+
+
 def _diatomic():
     return P.random_masses(P.fcc_primitive_multiple(5.26, (2, 1, 1)), 39.95, 83.8, seed=1)
 
@@ -70,6 +74,9 @@ CASES = {
     "diatomic-333-gauss": lambda: _case(_diatomic(), (3, 3, 3), 50.0, "gauss", 0.3),
     "diatomic-422-lorentz": lambda: _case(_diatomic(), (4, 2, 2), 40.0, "lorentz", 0.4),
     "fcc32-311-gauss": lambda: _case(P.fcc_massdisorder_32().crystal, (3, 1, 1), 50.0, "gauss", 0.1, n_iter=4),
+    # 64 atoms (192 modes: the two-GEMM path with streamed eigenvector operands in two column
+    # groups), the cell of the 12^3 iterative-BTE run, on a reduced mesh
+    "cell64-311-gauss": lambda: _case(_cell64(), (3, 1, 1), 50.0, "gauss", 0.2, n_iter=4),
 }
 
 

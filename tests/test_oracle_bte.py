@@ -6,7 +6,8 @@ substitution.  These tests rebuild the collision operator from the processes the
 the outgoing partners at their own mesh points and no time-reversal assumption), and check:
 the two operators agree on time-reversal-odd fields; the iteration on the full mesh with the
 process operator gives the oracle's kappa history; the RTA start is Eq. (rta); the converged
-iterate is the direct solution of Eq. (inverse); and the s^2 scaling of Phi3.
+iterate is the direct solution of Eq. (inverse); the s^2 scaling of Phi3; and detailed
+balance of the collision operator on shell, with planted mistakes that it rejects.
 """
 import numpy as np
 import pytest
@@ -186,3 +187,69 @@ def test_phi3_scaling(case):
     h4, _, _ = O.bte.iterate(s["mesh"], s["freq"], s["vel"], 4 * s["g0"], 4 * s["g1"], s["T"], s["vol"], n_iter=3,
                              tol=0)
     assert np.abs(4 * h4 - h1).max() <= 1e-12 * np.abs(h1).max()
+
+
+def _on_shell_rows(s, pair_weights=None, monkeypatch=None):
+    """Folded Gamma1 rows of the representatives, with the case's eigenvectors but whole-number
+    frequencies (1, 2 or 3 THz, equal at q and -q) and a window of 0.4 THz: every triplet that
+    survives the window is exactly resonant (f = f' + f'' or f + f' = f'')."""
+    mesh, n = s["mesh"], s["freq"].shape[1]
+    rng = np.random.default_rng(5)
+    freq = rng.integers(1, 4, size=(len(s["irr"]), n)).astype(np.float64)[s["pos"]]
+    if pair_weights is not None:
+        monkeypatch.setattr(O.anharmonic, "pair_weights", pair_weights)
+    _, g1f = O.bte.scattering_rows(s["fc3"], mesh, freq, s["evec"], s["irr"], s["T"], shape=s["kw"]["shape"],
+                                   sigma=0.2, window=2.0)
+    return freq, O.bte.reduce_columns(g1f, mesh, n)
+
+
+def _detailed_balance_asym(s, freq, g1):
+    """max |D - D^T| / max |D| for D = diag(n(n+1) f) Gamma1 diag(1/f) over the representatives
+    with -q != q (the others carry lambda = 0)."""
+    n = freq.shape[1]
+    f = freq[s["irr"]].ravel()
+    nb = O.occupation.bose(freq[s["irr"]], s["T"]).ravel()
+    live = np.repeat(s["sign"][s["irr"]] != 0, n)
+    d = (nb * (nb + 1) * f)[:, None] * g1 / f[None, :]
+    d = np.where(live[:, None] & live[None, :], d, 0.0)
+    assert np.abs(d).max() > 0
+    return float(np.abs(d - d.T).max() / np.abs(d).max())
+
+
+def test_gamma1_detailed_balance_on_shell(case):
+    """Detailed balance, a property of the linearised collision operator that the oracle's
+    assembly does not use: a process couples its partners through one equilibrium rate P,
+    which is n(n+1) times that process's linewidth term of every participant, so
+    diag(n(n+1) f) (Gamma0 + Gamma1) diag(1/f) is symmetric on time-reversal-odd fields
+    (the Boltzmann-equation symmetry behind the paper's variational and direct solvers).
+    The rate identity n (1 + n' + n'') = n' n'' behind it holds on shell only, so the pin uses
+    frequencies for which every triplet inside the window is exactly resonant.  With the
+    broadened, off-shell occupations of real spectra the symmetry holds only to O(sigma)."""
+    freq, g1 = _on_shell_rows(case)
+    assert _detailed_balance_asym(case, freq, g1) < 1e-12
+
+
+@pytest.mark.parametrize("mistake", ["absorption-sign", "decay-occupation"])
+def test_gamma1_detailed_balance_catches_planted_mistakes(case, mistake, monkeypatch):
+    """The on-shell pin rejects an oracle whose weights carry a plausible mistake."""
+    good = O.anharmonic.pair_weights
+
+    def planted(f0, f1, f2, n1, n2, shape, sigma, f_min, window):
+        if mistake == "absorption-sign":            # (n'' - n') in place of (n' - n'')
+            return _swap_abs(good, f0, f1, f2, n1, n2, shape, sigma, f_min, window)
+        # (n' + n'') in place of (1 + n' + n'') in the decay term; absorption unchanged
+        return good(f0, f1, f2, n1 - 0.5, n2 - 0.5, shape, sigma, f_min, window)
+
+    freq, g1 = _on_shell_rows(case, planted, monkeypatch)
+    assert _detailed_balance_asym(case, freq, g1) > 1e-3
+
+
+def _swap_abs(good, f0, f1, f2, n1, n2, shape, sigma, f_min, window):
+    """Weights with the absorption term's occupation difference negated."""
+    dec = good(f0, f1, f2, n1, n2, shape, sigma, f_min, window)
+    F0, F1, F2 = f0[:, None, None], f1[None, :, None], f2[None, None, :]
+    N1, N2 = n1[None, :, None], n2[None, None, :]
+    ok = (F0 >= f_min) & (F1 >= f_min) & (F2 >= f_min)
+    www = np.where(ok, (2 * np.pi) ** 4 * F0 * F1 * F2, 1.0)
+    absorb = 2.0 * (N1 - N2) * O.anharmonic.broadening(F0 + F1 - F2, shape, sigma, window)
+    return dec - np.where(ok, 2.0 * absorb / www, 0.0)

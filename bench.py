@@ -74,6 +74,26 @@ def tensor_peak(peaks, precision, sustained=True):
     return None, "FP64 CUDA-core path"
 
 
+def new_context(phx, device, args):
+    """Library context with the run's options."""
+    ctx = phx.Context(device)
+    ctx.set_option("pair", args.pair)
+    return ctx
+
+
+def pair_count(iq, mesh, pair=True):
+    """q' contracted for irreducible q: every mesh point, or with exchange pairs one per
+    unordered {q', q''} ((nq + n_self) / 2, n_self = the q' with 2 q' = -q mod G)."""
+    nq = int(np.prod(mesh))
+    if not pair:
+        return nq
+    k = (iq // (mesh[1] * mesh[2]), (iq // mesh[2]) % mesh[1], iq % mesh[2])
+    n_self = 1
+    for d in range(3):
+        n_self *= 1 if mesh[d] % 2 else (0 if k[d] % 2 else 2)
+    return (nq + n_self) // 2
+
+
 def roofline_of(prof, steps, ms_step, precision, peaks, src, workload):
     """Roofline of the kernel class with the most device time in a profiled pass of `steps`
     steps: tensor-bound classes against the tensor peak of the precision (algorithmic flops),
@@ -238,6 +258,12 @@ class Workload:
         valid = (f[self.irr] >= self.w.f_min_thz).sum()
         return int(valid) * self.nq * self.n * self.n
 
+    def triplets_evaluated(self, pair):
+        """Triplets the contractions evaluate: with exchange pairs about half of triplets()."""
+        f = self.freq.cpu().numpy()
+        return sum(int((f[iq] >= self.w.f_min_thz).sum()) * pair_count(int(iq), self.w.mesh, pair)
+                   for iq in self.irr) * self.n * self.n
+
     # ---- end to end through the public API with host (pinned) buffers
     def step_host(self, bufs):
         w, c, ctx = self.w, self.c, self.ctx
@@ -387,7 +413,7 @@ def run_phx(args):
     device = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=device)
-    ctx = phx.Context(local)
+    ctx = new_context(phx, local, args)
     wl = Workload(phx, ctx, args.precision, device)
     if args.irr_limit > 0:
         wl.limit_irreducible(args.irr_limit)
@@ -442,10 +468,11 @@ def run_phx(args):
     # roofline of the kernel class with the most device time (events of the profiled step)
     peaks, src = load_peaks()
     roof = roofline_of(prof, 1, ms_prof, args.precision, peaks, src, "fcc32")
-    # the whole step's contraction: 16 n flops per triplet (two complex contractions of n terms,
-    # 8 flops per complex multiply-add) over the step time, against the same tensor peak
+    # the whole step's contraction: 16 n flops per evaluated triplet (two complex contractions of
+    # n terms, 8 flops per complex multiply-add) over the step time, against the same tensor peak
     peak_t, _ = tensor_peak(peaks, args.precision)
-    step_fl = 16.0 * wl.n * trip
+    trip_eval = wl.triplets_evaluated(bool(args.pair))
+    step_fl = 16.0 * wl.n * trip_eval
     step_contraction = {"flops_per_step": step_fl, "achieved": step_fl / (ms / 1e3) / 1e12, "unit": "TFLOP/s",
                         "frac": (step_fl / (ms / 1e3) / 1e12 / peak_t) if peak_t else None}
     k_ref = golden_kappa(wl.w, wl.f2, wl.f3)
@@ -456,7 +483,13 @@ def run_phx(args):
             "config": {"workload": "fcc32-massdis-mesh8: 32-atom LJ fcc (2x2x2 conventional, masses 39.95/83.8 "
                                    "seed 2), 96 modes, 8x8x8 mesh, 260 irreducible q (time reversal), 50 K, "
                                    "Gaussian 0.1 THz",
-                       "triplets_per_step_per_gpu": trip, "l2": "working set > L2 (W operand 226 MB, "
+                       "triplets_per_step_per_gpu": trip,
+                       "exchange_pairs": bool(args.pair),
+                       "triplets_evaluated_per_step_per_gpu": trip_eval,
+                       "triplet_count_note": "value counts every term (irreducible mode, q', nu', nu'') of the "
+                                             "linewidth sums; with exchange pairs the kernels contract one q' "
+                                             "per unordered {q', q''} with both orderings' weights",
+                       "l2": "working set > L2 (W operand 226 MB, "
                        "eigenvector tables 75 MB per step)", "parallelism": f"replicas x{world}"},
             "e2e": {"value": trip_all / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
@@ -560,7 +593,7 @@ def run_batched(args):
     import phx_inputs as P
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    ctx = phx.Context(0)
+    ctx = new_context(phx, 0, args)
     n_take = 64 if args.workload == "batched64" else 16
     sweep = P.batched_sweep()[:n_take]
     jobs, trip = [], 0
@@ -680,7 +713,7 @@ def run_surrogate(args):
     import phx_inputs as P
     from paper_2602_23728_gb300 import surrogate
     torch.cuda.set_device(0)
-    ctx = phx.Context(0)
+    ctx = new_context(phx, 0, args)
     w = P.fcc_conventional_4(mesh=(24, 24, 24), temperature=40.0)
     c = w.crystal
     f2, f3 = w.ifc2(), w.ifc3()
@@ -723,7 +756,7 @@ def run_cell(args):
     import oracle as O
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    ctx = phx.Context(0)
+    ctx = new_context(phx, 0, args)
     t_setup = time.perf_counter()
     w = P.gamma_disordered_1000(reps=(args.cell_reps,) * 3)
     c = w.crystal
@@ -846,7 +879,7 @@ def run_sc(args):
     import oracle as O
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    ctx = phx.Context(0)
+    ctx = new_context(phx, 0, args)
     wl = Workload(phx, ctx, args.precision, dev, mesh=(args.sc_mesh,) * 3)
     w, c = wl.w, wl.c
     n, nq = wl.n, wl.nq
@@ -972,7 +1005,7 @@ def run_sc64(args):
     import phx_inputs as P
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    ctx = phx.Context(0)
+    ctx = new_context(phx, 0, args)
     c = P.random_masses(P.fcc_primitive_multiple(5.26, (4, 4, 4)), 39.95, 83.8, seed=11)
     mesh = (12, 12, 12)
     f2, f3 = P.ifc_lj_vectorised(c, P.LennardJones())
@@ -1063,6 +1096,9 @@ def main():
     ap.add_argument("--cell-reps", type=int, default=10,
                     help="cell1000: primitive cells per edge of the disordered cell (10 = the 1000-atom "
                          "workload; 6 = a 216-atom cell of the same kind for profiler captures)")
+    ap.add_argument("--pair", type=int, default=1, choices=[0, 1],
+                    help="1: the tensor-core passes evaluate each exchange pair {q', q''} once (default); "
+                         "0: every q' of the mesh")
     ap.add_argument("--irr-limit", type=int, default=0,
                     help="profiling aid: process only the first N irreducible q per step (0: all)")
     args = ap.parse_args()

@@ -106,8 +106,13 @@ const char* phx_version(void);
  *   PHX_OPT_CHAIN: which kernel runs the two eigenvector contractions of the tensor-core
  *     linewidth path (Eq. (phi3_proj)): 0 = automatic (the chained kernel, which keeps the
  *     intermediate X in tensor memory, for 64 < n <= 96 modes; otherwise two GEMMs with X
- *     in device memory), 1 = the chained kernel wherever it fits (n <= 96), 2 = never.  The
- *     multi-temperature and scattering-row passes always use the two GEMMs.
+ *     in device memory), 1 = the chained kernel wherever it fits (n <= 96), 2 = never.  It
+ *     applies to the linewidth, multi-temperature and scattering-row passes alike.
+ *   PHX_OPT_PAIR: 1 (default) = the tensor-core passes evaluate each unordered partner pair
+ *     {q', q'' = -(q + q')} of the q' sum of Eq. (gamma) once, with the weights of both
+ *     orderings (|V3|^2 is the same for both: Eq. (phi3_proj) is symmetric in the modes), so
+ *     about half of the q' are contracted; 0 = every q' of the mesh.  Results agree to
+ *     rounding.  The FP64 path always sums every q'.
  *   PHX_OPT_WAIT_LIMIT_NS: bound of every device barrier wait of the tensor-core kernels
  *     (default 2e9 ns); a wait that runs out makes the kernel retire and the call return
  *     PHX_ERR_TIMEOUT (host-memory calls; device-memory calls leave the status to the next
@@ -115,7 +120,7 @@ const char* phx_version(void);
  *   PHX_OPT_STARVE: test hook; nonzero makes the tensor-core kernels' load producers issue
  *     nothing, so the first barrier wait runs out with no copy or MMA in flight.
  * Errors: PHX_ERR_INVALID for an unknown option or a value out of range. */
-typedef enum { PHX_OPT_CHAIN = 0, PHX_OPT_WAIT_LIMIT_NS = 1, PHX_OPT_STARVE = 2 } phx_option;
+typedef enum { PHX_OPT_CHAIN = 0, PHX_OPT_WAIT_LIMIT_NS = 1, PHX_OPT_STARVE = 2, PHX_OPT_PAIR = 3 } phx_option;
 phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value);
 
 /* ---------------------------------------------------------------- grid (host only)

@@ -200,6 +200,10 @@ phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value) {
         case PHX_OPT_STARVE:
             ctx->opt_starve = value != 0;
             return PHX_OK;
+        case PHX_OPT_PAIR:
+            if (value < 0 || value > 1) return phx_set_error(ctx, PHX_ERR_INVALID, "PHX_OPT_PAIR %lld", (long long)value);
+            ctx->opt_pair = (int)value;
+            return PHX_OK;
         default:
             return phx_set_error(ctx, PHX_ERR_INVALID, "unknown option %d", option);
     }

@@ -45,8 +45,9 @@ struct ChainArgs {
     int n_items;                // q' slots x bands of this launch (slot-major)
     int nnu;                    // bands nu per slot
     int rows_per_slot;          // rows of M per q' slot
+    const int32_t* qp;          // per slot: mesh index of q'
     const int32_t* qpp;         // per slot: mesh index of q''
-    int t0;                     // first q' of the tile (slot p is q' = t0 + p)
+    int pair;                   // nonzero: each q' stands for its exchange pair (q', q'')
     int nu0;                    // first band of the chunk
     int iq;
     const double* freq;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                 if (new_p) {
                     // stage-3 table of q' once the previous slot's stage-3 MMAs are done
                     if (n_b3 > 0 && !tc::mbar_wait(&b3_empty, (n_b3 - 1) & 1, &abort_flag, wl)) { fail(); break; }
-                    const int row = (args.t0 + p) * n;
+                    const int row = args.qp[p] * n;
                     tc::mbar_expect_tx(&b3_full, kPlanes * nkc * blk_b);
                     for (int pl = 0; pl < kPlanes; ++pl)
                         for (int c = 0; c < nkc; ++c)
@@ -362,6 +363,11 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
 #pragma unroll
         for (int t = 0; t < kMaxT; ++t) nn2t[t] = 0.f;
         int c1 = 0, c2 = 0;                              // CHAIN_GS: time-reversal codes of q', q''
+        // element weight cA (1+n'+n'') g(f-f'-f'') + cB (n'-n'') (g(f+f'-f'') - [pk] g(f+f''-f')):
+        // (1, 2, no) for one ordered q' term; with exchange pairs (2, 2, yes) for q' != q'' (both
+        // orderings) and (1, 1, yes) for q' = q'' (its (nu', nu'') sum already holds both)
+        float cA = 1.f, cB = 2.f;
+        bool pk = false;
         // CHAIN_GS: the column sums of item li are complete once every epilogue thread has passed
         // the barrier at the start of item li + 1; they are flushed to Gamma1 there (before the
         // partner tables change) from a buffer the next item does not use
@@ -411,7 +417,10 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                 // partner tables of this slot's q' (every thread has finished the previous item:
                 // barrier above) and this thread's row constants at q''
                 if (MODE == CHAIN_GS) epi_barrier(kChainEpiThreads);    // flush read the old tables
-                const int q1 = args.t0 + p, q2 = args.qpp[p];
+                const int q1 = args.qp[p], q2 = args.qpp[p];
+                pk = args.pair != 0;
+                cA = pk && q1 != q2 ? 2.f : 1.f;
+                cB = pk && q1 == q2 ? 1.f : 2.f;
                 for (int j = et; j < rb3; j += kChainEpiThreads) {
                     const bool v = j < n;
                     const float f1 = v ? (float)args.freq[(int64_t)q1 * n + j] : 0.0f;
@@ -440,7 +449,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
             // w = [...] / (2 pi)^4 / (f0 f1 f2): delta(w) = g(f)/(2 pi) and 1/(w0 w1 w2)
             const float inv_f02 = live ? 1.0f / (1558.5454565440389f * f0 * f2) : 0.0f;
             const float rowfac = norm * inv_f02;
-            const float d02 = f0 - f2, one_n2 = 1.f + nn2;
+            const float d02 = f0 - f2, s02 = f0 + f2, one_n2 = 1.f + nn2;
             float gs = 0.f, ws = 0.f;
             float gst[kMaxT];
 #pragma unroll
@@ -460,18 +469,20 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                             const int jj = c0 + i;
                             const float4 tb = s_tab[jj];
                             const float f1 = tb.x, n1 = tb.y, if1 = tb.z;
-                            const float x = d02 - f1, y = d02 + f1;
+                            const float x = d02 - f1, y = d02 + f1, z = s02 - f1;
                             const float gd = fabsf(x) < lim ? (gauss ? ex2_approx(ga2 * x * x) : __frcp_rn(x * x + h2)) : 0.f;
                             const float ga = fabsf(y) < lim ? (gauss ? ex2_approx(ga2 * y * y) : __frcp_rn(y * y + h2)) : 0.f;
+                            const float gb = pk && fabsf(z) < lim ? (gauss ? ex2_approx(ga2 * z * z) : __frcp_rn(z * z + h2)) : 0.f;
                             const float v2 = fmaf(v[i], v[i], vi[i] * vi[i]);
                             if (MODE == CHAIN_GT) {
+                                const float gdd = cA * gd, gad = cB * (ga - gb);
 #pragma unroll
                                 for (int t = 0; t < kMaxT; ++t) {
                                     const float n1t = s_n1t[t][jj];
-                                    gst[t] = fmaf(v2 * if1, (1.f + nn2t[t] + n1t) * gd + 2.f * (n1t - nn2t[t]) * ga, gst[t]);
+                                    gst[t] = fmaf(v2 * if1, (1.f + nn2t[t] + n1t) * gdd + (n1t - nn2t[t]) * gad, gst[t]);
                                 }
                             } else {
-                                const float w = ((one_n2 + n1) * gd + 2.f * (n1 - nn2) * ga) * if1;
+                                const float w = (cA * (one_n2 + n1) * gd + cB * (n1 - nn2) * (ga - gb)) * if1;
                                 if (MODE == CHAIN_GS) {
                                     // full element weight; rows without a live mode add nothing (select,
                                     // not product: such lanes of D3 may hold anything)

@@ -52,6 +52,7 @@ struct phx_ctx {
     std::map<std::vector<int>, std::pair<int, int>> tune_q;   // job class -> (q' tile, chained kernel)
     // options (phx_set_option)
     int opt_chain = 0;                            // 0 auto, 1 force the chained kernel, 2 never
+    int opt_pair = 1;                             // evaluate each exchange pair {q', q''} once
     unsigned long long opt_wait_ns = 2000000000ull;   // bound of every device barrier wait
     int opt_starve = 0;                           // test hook: tensor-core producers issue nothing
 };

@@ -81,7 +81,9 @@ struct TcArgs {
     // EPI_G
     const double* freq;
     const double* nB;
-    int iq, t0, nu0, m1, m2, m3;
+    int iq, nu0, m1, m2, m3;
+    const int32_t* qp1;         // per problem: mesh index of q'
+    int pair;                   // nonzero: each q' stands for its exchange pair (q', q'')
     float sigma, window, f_min;
     int shape;
     double* gacc;               // [n] for this irreducible q (offset applied)
@@ -337,6 +339,11 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
         const int half = (warp - 2) >> 2;                 // part index (0 .. kEpiParts - 1)
         constexpr int kStride = 16 * kEpiParts;
         int q1 = 0, q2 = 0, cur_p = -1;
+        // element weight cA (1+n'+n'') g(f-f'-f'') + cB (n'-n'') (g(f+f'-f'') - [pk] g(f+f''-f')):
+        // (1, 2, no) for one ordered q' term; with exchange pairs (2, 2, yes) for q' != q'' (both
+        // orderings) and (1, 1, yes) for q' = q'' (its (nu', nu'') sum already holds both)
+        float cA = 1.f, cB = 2.f;
+        bool pk = false;
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int it = item_begin; it < item_end; ++it) {
@@ -350,8 +357,11 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
             if (epi_barrier_any(kEpiThreads, !ok || abort_flag != 0)) break;   // one decision for all
             if ((EPI == EPI_G || EPI == EPI_GT || EPI == EPI_GS) && p != cur_p) {
                 // partner tables of this problem's q' (the previous tile is done: barrier above)
-                q1 = args.t0 + p;
+                q1 = args.qp1[p];
                 q2 = phx_third_index(args.iq, q1, args.m1, args.m2, args.m3);
+                pk = args.pair != 0;
+                cA = pk && q1 != q2 ? 2.f : 1.f;
+                cB = pk && q1 == q2 ? 1.f : 2.f;
                 for (int j = et; j < np; j += kEpiThreads) {
                     const bool v = j < args.n;
                     const float f1 = v ? (float)args.freq[(int64_t)q1 * args.n + j] : 0.0f;
@@ -484,7 +494,7 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                 }
                 const bool live = valid && f0 >= args.f_min && f2 >= args.f_min;
                 const float inv_f02 = live ? 1.0f / (1558.5454565440389f * f0 * f2) : 0.0f;
-                const float d02 = f0 - f2, lim = args.window * args.sigma;
+                const float d02 = f0 - f2, s02 = f0 + f2, lim = args.window * args.sigma;
                 const bool gauss = args.shape == PHX_GAUSS;
                 const float a = -1.f / (args.sigma * args.sigma), h2 = 0.25f * args.sigma * args.sigma;
                 const float norm = gauss ? 0.56418958354775628f / args.sigma : 0.5f * args.sigma / 3.14159265358979f;
@@ -499,14 +509,16 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                     for (int i = 0; i < 16; ++i) {
                         const int j = m0 + j0 + i;
                         const float if1 = s_if1[j], f1 = s_f1[j];
-                        const float x = d02 - f1, y = d02 + f1;
+                        const float x = d02 - f1, y = d02 + f1, z = s02 - f1;
                         const float gd = fabsf(x) < lim ? (gauss ? __expf(a * x * x) : __frcp_rn(x * x + h2)) : 0.f;
                         const float ga = fabsf(y) < lim ? (gauss ? __expf(a * y * y) : __frcp_rn(y * y + h2)) : 0.f;
+                        const float gb = pk && fabsf(z) < lim ? (gauss ? __expf(a * z * z) : __frcp_rn(z * z + h2)) : 0.f;
                         const float v2 = fmaf(v[i], v[i], vi[i] * vi[i]) * if1;
+                        const float gad = cB * (ga - gb), gdd = cA * gd;
 #pragma unroll
                         for (int t = 0; t < kMaxT; ++t) {
                             const float n1 = s_n1t[t * kMaxNp + j];
-                            gs[t] = fmaf(v2, (1.f + nn2[t] + n1) * gd + 2.f * (n1 - nn2[t]) * ga, gs[t]);
+                            gs[t] = fmaf(v2, (1.f + nn2[t] + n1) * gdd + (n1 - nn2[t]) * gad, gs[t]);
                         }
                     }
                 }
@@ -547,7 +559,7 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                 const float a = -1.f / (args.sigma * args.sigma), h2 = 0.25f * args.sigma * args.sigma;
                 const float norm = gauss ? 0.56418958354775628f / args.sigma : 0.5f * args.sigma / 3.14159265358979f;
                 const float rowfac = live ? norm / (1558.5454565440389f * f0 * f2) : 0.0f;
-                const float d02 = f0 - f2, lim = args.window * args.sigma;
+                const float d02 = f0 - f2, s02 = f0 + f2, lim = args.window * args.sigma;
                 const float one_n2 = 1.f + nn2;
                 const int key = valid ? nu : -1 - lane;
                 const bool vec4 = (args.n & 3) == 0;       // groups of four adjacent entries stay in one row
@@ -576,10 +588,11 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                     for (int i = 0; i < 16; ++i) {
                         const int j = m0 + j0 + i;
                         const float f1 = s_f1[j], n1 = s_n1[j], if1 = s_if1[j];
-                        const float x = d02 - f1, y = d02 + f1;
+                        const float x = d02 - f1, y = d02 + f1, z = s02 - f1;
                         const float gd = fabsf(x) < lim ? (gauss ? __expf(a * x * x) : __frcp_rn(x * x + h2)) : 0.f;
                         const float ga = fabsf(y) < lim ? (gauss ? __expf(a * y * y) : __frcp_rn(y * y + h2)) : 0.f;
-                        const float w = ((one_n2 + n1) * gd + 2.f * (n1 - nn2) * ga) * (if1 * rowfac);
+                        const float gb = pk && fabsf(z) < lim ? (gauss ? __expf(a * z * z) : __frcp_rn(z * z + h2)) : 0.f;
+                        const float w = (cA * (one_n2 + n1) * gd + cB * (n1 - nn2) * (ga - gb)) * (if1 * rowfac);
                         e[i] = fmaf(v[i], v[i], vi[i] * vi[i]) * w;
                         gs += e[i];
                     }
@@ -694,7 +707,7 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                 const bool live = valid && f0 >= args.f_min && f2 >= args.f_min;
                 // w = [...] / (2 pi)^4 / (f0 f1 f2): delta(w) = g(f)/(2 pi) and 1/(w0 w1 w2)
                 const float inv_f02 = live ? 1.0f / (1558.5454565440389f * f0 * f2) : 0.0f;
-                const float d02 = f0 - f2, lim = args.window * args.sigma;
+                const float d02 = f0 - f2, s02 = f0 + f2, lim = args.window * args.sigma;
                 const float one_n2 = 1.f + nn2;
                 float gs = 0.f, ws = 0.f;
                 float vi[16];
@@ -707,10 +720,11 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                         for (int i = 0; i < 16; ++i) {
                             const int j = m0 + j0 + i;
                             const float f1 = s_f1[j], n1 = s_n1[j], if1 = s_if1[j];
-                            const float x = d02 - f1, y = d02 + f1;
+                            const float x = d02 - f1, y = d02 + f1, z = s02 - f1;
                             const float gd = fabsf(x) < lim ? __expf(a * x * x) : 0.f;
                             const float ga = fabsf(y) < lim ? __expf(a * y * y) : 0.f;
-                            const float w = ((one_n2 + n1) * gd + 2.f * (n1 - nn2) * ga) * if1;
+                            const float gb = pk && fabsf(z) < lim ? __expf(a * z * z) : 0.f;
+                            const float w = (cA * (one_n2 + n1) * gd + cB * (n1 - nn2) * (ga - gb)) * if1;
                             gs = fmaf(fmaf(v[i], v[i], vi[i] * vi[i]), w, gs);
                             ws += w;
                         }
@@ -726,10 +740,11 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                         for (int i = 0; i < 16; ++i) {
                             const int j = m0 + j0 + i;
                             const float f1 = s_f1[j], n1 = s_n1[j], if1 = s_if1[j];
-                            const float x = d02 - f1, y = d02 + f1;
+                            const float x = d02 - f1, y = d02 + f1, z = s02 - f1;
                             const float gd = fabsf(x) < lim ? __frcp_rn(x * x + h2) : 0.f;
                             const float ga = fabsf(y) < lim ? __frcp_rn(y * y + h2) : 0.f;
-                            const float w = ((one_n2 + n1) * gd + 2.f * (n1 - nn2) * ga) * if1;
+                            const float gb = pk && fabsf(z) < lim ? __frcp_rn(z * z + h2) : 0.f;
+                            const float w = (cA * (one_n2 + n1) * gd + cB * (n1 - nn2) * (ga - gb)) * if1;
                             gs = fmaf(fmaf(v[i], v[i], vi[i] * vi[i]), w, gs);
                             ws += w;
                         }
@@ -816,12 +831,57 @@ __global__ void prep_evec_tables(const double2* __restrict__ evec, int nq, int n
     }
 }
 
-// B tables of the Fourier phases exp(-i q'.d) for every tile of Q q' (slot = q' - tile*Q).
+// The q' of one irreducible q in increasing mesh order with their q'' = -(q + q') mod G.  With
+// `pair`, only the q' with q' <= q'' are listed: V3 is symmetric under the exchange of the two
+// partners (Eq. (phi3_proj) sums over all three modes alike), so one evaluation of an
+// unordered pair {q', q''} serves both terms of the q' sum; there are (nq + n_self) / 2 of
+// them, n_self counting the q' = q''.  One block.
+__global__ void pair_list_kernel(int iq, int m1, int m2, int m3, int pair, int32_t* __restrict__ qp,
+                                 int32_t* __restrict__ qpp) {
+    __shared__ int s_warp[32];
+    __shared__ int s_base;
+    const int nq = m1 * m2 * m3, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nq; c0 += blockDim.x) {
+        const int q1 = c0 + threadIdx.x;
+        const int q2 = q1 < nq ? phx_third_index(iq, q1, m1, m2, m3) : 0;
+        const bool take = q1 < nq && (!pair || q1 <= q2);
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        if (lane == 0) s_warp[warp] = __popc(bal);
+        __syncthreads();
+        int before = s_base;
+        for (int w = 0; w < warp; ++w) before += s_warp[w];
+        if (take) {
+            const int pos = before + __popc(bal & ((1u << lane) - 1u));
+            qp[pos] = q1;
+            qpp[pos] = q2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) for (int w = 0; w < nw; ++w) s_base += s_warp[w];
+        __syncthreads();
+    }
+}
+
+// Length of pair_list_kernel's list (host side).
+int pair_count(int iq, const int* mesh, bool pair) {
+    const int nq = mesh[0] * mesh[1] * mesh[2];
+    if (!pair) return nq;
+    const int k[3] = {iq / (mesh[1] * mesh[2]), (iq / mesh[2]) % mesh[1], iq % mesh[2]};
+    int n_self = 1;
+    for (int d = 0; d < 3; ++d)     // solutions of 2 k' = -k (mod m): one for odd m, two or none for even m
+        n_self *= (mesh[d] & 1) ? 1 : ((k[d] & 1) ? 0 : 2);
+    return (nq + n_self) / 2;
+}
+
+// B tables of the Fourier phases exp(-i q'.d) for the listed q', tiles of Qb list entries
+// (tile t, slot s: entry t * Qb + s; slots past the list or past Qb are zero).
 template <int PREC>
-__global__ void prep_phase_tables(const int32_t* __restrict__ d_int, int n_d, int m1, int m2, int m3, int Q,
-                                  int n_tiles, int qp_np, int kcp, void* hi, void* lo) {
+__global__ void prep_phase_tables(const int32_t* __restrict__ d_int, int n_d, int m1, int m2, int m3,
+                                  const int32_t* __restrict__ qlist, int count, int Qb, int n_tiles, int qp_np,
+                                  int kcp, void* hi, void* lo) {
     const int N = 2 * qp_np, kr = 2 * kcp;
-    const int nq = m1 * m2 * m3;
     const int64_t total = (int64_t)n_tiles * N * kr;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int kk = (int)(t % kr);
@@ -829,9 +889,10 @@ __global__ void prep_phase_tables(const int32_t* __restrict__ d_int, int n_d, in
         const int tile = (int)(t / ((int64_t)kr * N));
         const int slot = j < qp_np ? j : j - qp_np;
         const int d = kk < kcp ? kk : kk - kcp;
-        const int qp = tile * Q + slot;
+        const int pos = tile * Qb + slot;
         float val = 0.f;
-        if (slot < Q && qp < nq && d < n_d) {
+        if (slot < Qb && pos < count && d < n_d) {
+            const int qp = qlist[pos];
             const int k1 = qp / (m2 * m3), k2 = (qp / m3) % m2, k3 = qp % m3;
             const int a1 = (k1 * d_int[3 * d]) % m1, a2 = (k2 * d_int[3 * d + 1]) % m2, a3 = (k3 * d_int[3 * d + 2]) % m3;
             double s, c;
@@ -1183,7 +1244,8 @@ phx_status tc_prepare_fc3(phx_ctx* ctx, phx_fc3* f) {
 
 struct TcBuffers {
     Operand W, M, X, E, P, T;
-    int32_t* qpp = nullptr;
+    int32_t* qp = nullptr;      // q' list of the current irreducible q (pair_list_kernel)
+    int32_t* qpp = nullptr;     // and their q''
     float2* wph = nullptr;
     float2* eqf = nullptr;
 };
@@ -1201,10 +1263,11 @@ phx_status tc_alloc(phx_ctx* ctx, int prec, size_t bw, size_t bm, size_t bx, siz
     if (!get("tc.W", bw, &b->W) || !get("tc.M", bm, &b->M) || !get("tc.X", bx, &b->X) || !get("tc.E", be, &b->E) ||
         !get("tc.P", bp, &b->P) || !get("tc.T", bt, &b->T))
         return PHX_ERR_NOMEM;
+    b->qp = (int32_t*)phx_ws(ctx, "tc.qp", (size_t)max_nq * 4);
     b->qpp = (int32_t*)phx_ws(ctx, "tc.qpp", (size_t)max_nq * 4);
     b->wph = (float2*)phx_ws(ctx, "tc.wph", (size_t)std::max<int64_t>(max_nnz, 1) * sizeof(float2));
     b->eqf = (float2*)phx_ws(ctx, "tc.eqf", (size_t)max_n2 * sizeof(float2));
-    if (!b->qpp || !b->wph || !b->eqf) return PHX_ERR_NOMEM;
+    if (!b->qp || !b->qpp || !b->wph || !b->eqf) return PHX_ERR_NOMEM;
     return PHX_OK;
 }
 
@@ -1234,10 +1297,8 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
     else
         prep_evec_tables<PREC><<<2048, 256, 0, s>>>((const double2*)evec, nq, n, np, kcp, B.E.hi, B.E.lo);
     PHX_CUDA_CHECK(ctx, cudaGetLastError());
-    prep_phase_tables<PREC><<<256, 256, 0, s>>>(f->d_int, f->n_d, f->mesh[0], f->mesh[1], f->mesh[2], Q,
-                                                P.n_tiles_q, qp_np, kcp_d, B.P.hi, B.P.lo);
-    PHX_CUDA_CHECK(ctx, cudaGetLastError());
-    ctx->launches += 2;
+    ctx->launches += 1;
+    const bool pair = ctx->opt_pair != 0;
 
     TcArgs aD{}, aA{}, aB{};
     ChainArgs aC{};
@@ -1308,7 +1369,14 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
     for (int si = 0; si < n_irr; ++si) {
         const int iq = irr_host[si];
         const int k1 = iq / (f->mesh[1] * f->mesh[2]), k2 = (iq / f->mesh[2]) % f->mesh[1], k3 = iq % f->mesh[2];
-        PHX_CUDA_CHECK(ctx, phx_launch_third_index(iq, f->mesh, B.qpp, s));
+        // this q's q' list (exchange pairs) in tiles of at most Q, balanced, and their phase tables
+        pair_list_kernel<<<1, 1024, 0, s>>>(iq, f->mesh[0], f->mesh[1], f->mesh[2], pair ? 1 : 0, B.qp, B.qpp);
+        const int count = pair_count(iq, f->mesh, pair);
+        const int n_tq = (count + Q - 1) / Q, Qb = (count + n_tq - 1) / n_tq;
+        prep_phase_tables<PREC><<<64, 256, 0, s>>>(f->d_int, f->n_d, f->mesh[0], f->mesh[1], f->mesh[2], B.qp, count,
+                                                   Qb, n_tq, qp_np, kcp_d, B.P.hi, B.P.lo);
+        PHX_CUDA_CHECK(ctx, cudaGetLastError());
+        ctx->launches += 2;
         const int pblocks = (int)std::min<int64_t>((f->nnz + n2 + 255) / 256, 4096);
         fold_phase_kernel<<<pblocks, 256, 0, s>>>(f->ent_r2, f->ent_w, f->nnz, (double)k1 / f->mesh[0],
                                                   (double)k2 / f->mesh[1], (double)k3 / f->mesh[2], B.wph,
@@ -1338,8 +1406,8 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
             aB.rows = (int)ra; aB.tiles = aA.tiles; aB.a_rows_per_problem = (int)ra;
             aB.nu0 = nu0;
             aB.g1_row0 = (int64_t)si * n + nu0;
-            for (int tq = 0; tq < P.n_tiles_q; ++tq) {
-                const int t0 = tq * Q, Qt = std::min(Q, nq - t0);
+            for (int tq = 0; tq < n_tq; ++tq) {
+                const int t0 = tq * Qb, Qt = std::min(Qb, count - t0);
                 aD.b_base = tq;
                 aD.nq_slots = Qt;
                 // algorithmic work: complex MACs x 8 flops; bytes: operands read + results written once
@@ -1351,7 +1419,7 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
                 phx_prof_end(ctx, pp, s, PHX_K_DFT, fl_d, op_bytes * ((double)rw * f->n_d + (double)Qt * ra * n));
                 if (P.chain) {
                     aC.n_items = Qt * nnu; aC.nnu = nnu; aC.rows_per_slot = (int)ra;
-                    aC.qpp = B.qpp + t0; aC.t0 = t0; aC.nu0 = nu0;
+                    aC.qp = B.qp + t0; aC.qpp = B.qpp + t0; aC.pair = pair ? 1 : 0; aC.nu0 = nu0;
                     aC.g1_row0 = (int64_t)si * n + nu0;
                     pp = phx_prof_begin(ctx, s);
                     PHX_CUDA_CHECK(ctx, launch_chain_mode<PREC>(aC, chain_mode, P.c_smem, sms, s));
@@ -1364,8 +1432,9 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
                 pp = phx_prof_begin(ctx, s);
                 PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_X>(ctx, aA, P.stream_b, Qt, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_GEMM_E2, fl_e, op_bytes * 2.0 * Qt * ra * n);
-                aB.b_idx = f->tc_ident + t0;
-                aB.t0 = t0;
+                aB.b_idx = B.qp + t0;
+                aB.qp1 = B.qp + t0;
+                aB.pair = pair ? 1 : 0;
                 pp = phx_prof_begin(ctx, s);
                 if (n_t > 0)
                     PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_GT>(ctx, aB, P.stream_b, Qt, sms, s)));
@@ -1524,12 +1593,12 @@ phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, const phx_
     double* acc9 = (double*)phx_ws(ctx, "b.acc9", (size_t)n_jobs * 9 * 8);
     if (!nB || !gacc || !acc9) return PHX_ERR_NOMEM;
 
-    // graph key: the job list, the precision and the tiles
+    // graph key: the job list, the precision, the pair option and the tiles
     std::vector<uint8_t> key(sizeof(phx_job) * n_jobs + sizeof(int) * (2 * n_jobs + 1));
     std::memcpy(key.data(), jobs, sizeof(phx_job) * n_jobs);
     std::memcpy(key.data() + sizeof(phx_job) * n_jobs, qtiles.data(), sizeof(int) * n_jobs);
     std::memcpy(key.data() + sizeof(phx_job) * n_jobs + sizeof(int) * n_jobs, chains.data(), sizeof(int) * n_jobs);
-    const int prec_v = PREC;
+    const int prec_v = PREC + 16 * ctx->opt_pair;      // the exchange-pair option changes the launches
     std::memcpy(key.data() + sizeof(phx_job) * n_jobs + sizeof(int) * 2 * n_jobs, &prec_v, sizeof(int));
     // host irr lists are part of the key by content
     for (int j = 0; j < n_jobs; ++j) {

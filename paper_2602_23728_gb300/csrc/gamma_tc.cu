@@ -924,43 +924,92 @@ __global__ void fold_phase_kernel(const int32_t* __restrict__ ent_r2, const doub
     }
 }
 
-// S3, part 2: the DFT's A operand, row (nu, b, c), K = [Re W(d) | Im W(d)].  Half a warp per
-// row, each lane two adjacent d (looping when n_d > 32), stored as pairs, so every store
-// instruction writes one contiguous run of the row.  seg_of[(b*n + c)*n_d + d] is the COO
-// segment of (d, b, c) or -1; rows without any segment are written as zeros, so no clearing
-// is needed.
+// Eight consecutive elements (idx a multiple of 8): one 16-byte store per plane (bf16 planes)
+// or two (tf32).
 template <int PREC>
-__global__ void fold_tc_kernel(const int32_t* __restrict__ seg_of, const int64_t* __restrict__ seg_start,
-                               const int32_t* __restrict__ ent_a, const float2* __restrict__ wph, int n_d,
-                               const float2* __restrict__ eqf, int n, int nu0, int rows, int kcp, void* hi,
-                               void* lo) {
-    // half a warp per row: lane h of the half computes d = 2h + 32 t and 2h + 1 + 32 t (two
-    // independent segment walks) and stores both as one pair per plane
-    const int nn = n * n;
-    const int kr = 2 * kcp;
-    const int h = threadIdx.x & 15;
-    const int halves = gridDim.x * (blockDim.x >> 4);
-    for (int row = blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4); row < rows; row += halves) {
-        const int nu = nu0 + row / nn;
-        const int bc = row % nn;
-        for (int d0 = 2 * h; d0 < kcp; d0 += 32) {
-            float ar[2] = {0.f, 0.f}, ai[2] = {0.f, 0.f};
+__device__ __forceinline__ void store_operand8(void* hi, void* lo, int64_t idx, const float* v) {
+    if (PREC == P_BF16X3) {
+        uint32_t h[4], l[4];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int d = d0 + u;
-                if (d >= n_d) continue;
-                const int s = seg_of[bc * n_d + d];
-                if (s < 0) continue;
-                const int64_t k1 = seg_start[s + 1];
-                for (int64_t k = seg_start[s]; k < k1; ++k) {
-                    const float2 w = wph[k];
-                    const float2 e = eqf[ent_a[k] * n + nu];
-                    ar[u] += w.x * e.x - w.y * e.y;
-                    ai[u] += w.x * e.y + w.y * e.x;
+        for (int j = 0; j < 4; ++j) tc::split_bf16x2(v[2 * j], v[2 * j + 1], &h[j], &l[j]);
+        *reinterpret_cast<uint4*>((__nv_bfloat16*)hi + idx) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>((__nv_bfloat16*)lo + idx) = make_uint4(l[0], l[1], l[2], l[3]);
+    } else {
+        float4* o = reinterpret_cast<float4*>((float*)hi + idx);
+        o[0] = make_float4(tc::round_tf32(v[0]), tc::round_tf32(v[1]), tc::round_tf32(v[2]), tc::round_tf32(v[3]));
+        o[1] = make_float4(tc::round_tf32(v[4]), tc::round_tf32(v[5]), tc::round_tf32(v[6]), tc::round_tf32(v[7]));
+    }
+}
+
+// S3, part 2: the DFT's A operand for one q, row (nu, b, c) with K = [Re W(d) | Im W(d)],
+// W_nu(b, c; d) = sum over the COO entries (a, b, c) of lattice difference d of w_k e_q(a, nu).
+// One warp per (b, c) pair and block of 32 bands (lane = band nu): for each chunk of 32 d the
+// lanes read the 32 segment bounds at once (seg_of[(b*n + c)*n_d + d], then broadcast), every
+// entry of the chunk adds w_k e_q(a_k, nu) to the register accumulator of its d (a coalesced
+// read of e_q's row a_k; a segment's entries are read 32 at a time and broadcast), and each
+// lane stores its row's chunk as 16-byte vectors.  Half
+// chunks (16 d) without any entry are skipped: they are zero for every q, and the operand is
+// cleared once per job.
+template <int PREC>
+__global__ void __launch_bounds__(256, 3) fold_tc_kernel(const int32_t* __restrict__ seg_of,
+                                                      const int64_t* __restrict__ seg_start,
+                                                      const int32_t* __restrict__ ent_a,
+                                                      const float2* __restrict__ wph, int n_d,
+                                                      const float2* __restrict__ eqf, int n, int nu0, int nnu,
+                                                      int kcp, void* hi, void* lo) {
+    const int lane = threadIdx.x & 31;
+    const int nn = n * n, kr = 2 * kcp;
+    const int64_t items = (int64_t)nn * ((nnu + 31) / 32);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t it = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += warps) {
+        const int bc = (int)(it % nn);                 // adjacent warps: adjacent (b, c), adjacent table rows
+        const int nl = (int)(it / nn) * 32 + lane;     // band within the chunk of bands
+        const bool live = nl < nnu;
+        const float2* erow = eqf + (nu0 + (live ? nl : 0));
+        for (int dc = 0; dc < kcp; dc += 32) {
+            const int dl = dc + lane;
+            const int sg = dl < n_d ? seg_of[(int64_t)bc * n_d + dl] : -1;
+            int64_t k0 = 0, k1 = 0;
+            if (sg >= 0) { k0 = seg_start[sg]; k1 = seg_start[sg + 1]; }
+            const unsigned has = __ballot_sync(0xffffffffu, sg >= 0);
+            if (has == 0) continue;
+            // two halves of 16 d (keeps the accumulators at 32 registers)
+#pragma unroll
+            for (int h = 0; h < 32; h += 16) {
+                if (((has >> h) & 0xffffu) == 0) continue;
+                float ar[16], ai[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    ar[i] = 0.f;
+                    ai[i] = 0.f;
+                    if (!((has >> (h + i)) & 1u)) continue;
+                    const int64_t s0 = __shfl_sync(0xffffffffu, k0, h + i), s1 = __shfl_sync(0xffffffffu, k1, h + i);
+                    // up to 32 entries at a time: one coalesced read of (a_k, w_k), then broadcasts,
+                    // so the e_q reads of successive entries are independent
+                    for (int64_t kb = s0; kb < s1; kb += 32) {
+                        const int cnt = s1 - kb < 32 ? (int)(s1 - kb) : 32;
+                        int a_l = 0;
+                        float2 w_l = make_float2(0.f, 0.f);
+                        if (lane < cnt) { a_l = ent_a[kb + lane]; w_l = wph[kb + lane]; }
+#pragma unroll 4
+                        for (int j = 0; j < cnt; ++j) {
+                            const int a = __shfl_sync(0xffffffffu, a_l, j);
+                            const float wx = __shfl_sync(0xffffffffu, w_l.x, j), wy = __shfl_sync(0xffffffffu, w_l.y, j);
+                            const float2 e = erow[(int64_t)a * n];
+                            ar[i] += wx * e.x - wy * e.y;
+                            ai[i] += wx * e.y + wy * e.x;
+                        }
+                    }
+                }
+                if (live) {
+                    const int64_t base = ((int64_t)nl * nn + bc) * kr + dc + h;
+#pragma unroll
+                    for (int j = 0; j < 16; j += 8) {
+                        store_operand8<PREC>(hi, lo, base + j, ar + j);
+                        store_operand8<PREC>(hi, lo, base + kcp + j, ai + j);
+                    }
                 }
             }
-            store_operand2<PREC>(hi, lo, (int64_t)row * kr + d0, ar[0], ar[1]);
-            store_operand2<PREC>(hi, lo, (int64_t)row * kr + kcp + d0, ai[0], ai[1]);
         }
     }
 }
@@ -1392,9 +1441,10 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
             const int64_t rw = (int64_t)nnu * n2, ra = (int64_t)nnu * n;
             {
                 const int pf = phx_prof_begin(ctx, s);
-                const int blocks = (int)std::min<int64_t>((rw + 15) / 16, (int64_t)sms * 32);
+                const int64_t items = n2 * ((nnu + 31) / 32);
+                const int blocks = (int)std::min<int64_t>((items + 7) / 8, (int64_t)sms * 3);   // 3 CTAs per SM fit
                 fold_tc_kernel<PREC><<<blocks, 256, 0, s>>>(f->tc_seg_of, f->seg_start, f->ent_a, B.wph, f->n_d, B.eqf,
-                                                            n, nu0, (int)rw, kcp_d, B.W.hi, B.W.lo);
+                                                            n, nu0, nnu, kcp_d, B.W.hi, B.W.lo);
                 PHX_CUDA_CHECK(ctx, cudaGetLastError());
                 phx_prof_end(ctx, pf, s, PHX_K_FOLD, 8.0 * (double)f->nnz * nnu, (double)rw * kr_d * esz * planes);
                 ctx->launches += 1;

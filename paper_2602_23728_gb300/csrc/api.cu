@@ -549,7 +549,7 @@ void phx_fc3_destroy(phx_fc3* h) {
     if (!h) return;
     cudaFree(h->d_int); cudaFree(h->seg_key); cudaFree(h->seg_start);
     cudaFree(h->ent_a); cudaFree(h->ent_r2); cudaFree(h->ent_w);
-    cudaFree(h->tc_seg_of); cudaFree(h->tc_ident);
+    cudaFree(h->tc_bc_start); cudaFree(h->tc_ent_ad); cudaFree(h->tc_ent_src);
     cudaFree(h->g0_nbr_start); cudaFree(h->g0_nbr_atom); cudaFree(h->g0_seg_start);
     cudaFree(h->g0_ent_i); cudaFree(h->g0_ent_w);
     delete h;

@@ -77,8 +77,12 @@ struct phx_fc3 {
     int32_t* ent_r2 = nullptr;      // [nnz][3] R'' of each entry
     double* ent_w = nullptr;        // [nnz] Phi3 / sqrt(m_a m_b m_c)
     // tensor-core path tables, built on first use (before any capture)
-    int32_t* tc_seg_of = nullptr;   // [n][n][n_d] segment of (d, b, c) or -1
-    int32_t* tc_ident = nullptr;    // [nq] 0..nq-1
+    // the entries again, grouped by (b, c), then by d, then a: entry j of pair bc = b*n + c is
+    // j in [tc_bc_start[bc], tc_bc_start[bc + 1]), with (a, d) = tc_ent_ad[j] and its position in
+    // the arrays above tc_ent_src[j]
+    int64_t* tc_bc_start = nullptr; // [n*n + 1]
+    int2* tc_ent_ad = nullptr;      // [nnz]
+    int32_t* tc_ent_src = nullptr;  // [nnz]
     // Gamma-only large-cell path (mesh 1x1x1): permutation-symmetrised F = Phi3/sqrt(mmm) with
     // images summed, grouped by (row atom J, neighbour slot of atom K, gamma, beta) for
     // W_a[3J+beta][3K+gamma] = sum_i F[i][3J+beta][3K+gamma] e_a[i]

@@ -908,15 +908,17 @@ __global__ void prep_phase_tables(const int32_t* __restrict__ d_int, int n_d, in
 
 // S3, part 1: per COO entry the q-dependent factor phi/sqrt(mmm) * exp(+2 pi i q.R'') and the
 // eigenvectors of q, both rounded to FP32 once per q (FP64 is the narrowest pipe on GB300).
-__global__ void fold_phase_kernel(const int32_t* __restrict__ ent_r2, const double* __restrict__ ent_w, int64_t nnz,
-                                  double qa, double qb, double qc, float2* __restrict__ wph,
-                                  const double2* __restrict__ eq, int nn, float2* __restrict__ eqf) {
+__global__ void fold_phase_kernel(const int32_t* __restrict__ ent_src, const int32_t* __restrict__ ent_r2,
+                                  const double* __restrict__ ent_w, int64_t nnz, double qa, double qb, double qc,
+                                  float2* __restrict__ wph, const double2* __restrict__ eq, int nn,
+                                  float2* __restrict__ eqf) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz + nn; k += (int64_t)gridDim.x * blockDim.x) {
         if (k < nnz) {
-            const double x = 2.0 * (qa * ent_r2[3 * k] + qb * ent_r2[3 * k + 1] + qc * ent_r2[3 * k + 2]);
+            const int64_t o = ent_src[k];              // wph in the (b, c)-grouped order of the entries
+            const double x = 2.0 * (qa * ent_r2[3 * o] + qb * ent_r2[3 * o + 1] + qc * ent_r2[3 * o + 2]);
             double sn, cs;
             sincospi(x, &sn, &cs);
-            wph[k] = make_float2((float)(ent_w[k] * cs), (float)(ent_w[k] * sn));
+            wph[k] = make_float2((float)(ent_w[o] * cs), (float)(ent_w[o] * sn));
         } else {
             const double2 e = eq[k - nnz];
             eqf[k - nnz] = make_float2((float)e.x, (float)e.y);
@@ -943,74 +945,117 @@ __device__ __forceinline__ void store_operand8(void* hi, void* lo, int64_t idx, 
 
 // S3, part 2: the DFT's A operand for one q, row (nu, b, c) with K = [Re W(d) | Im W(d)],
 // W_nu(b, c; d) = sum over the COO entries (a, b, c) of lattice difference d of w_k e_q(a, nu).
-// One warp per (b, c) pair and block of 32 bands (lane = band nu): for each chunk of 32 d the
-// lanes read the 32 segment bounds at once (seg_of[(b*n + c)*n_d + d], then broadcast), every
-// entry of the chunk adds w_k e_q(a_k, nu) to the register accumulator of its d (a coalesced
-// read of e_q's row a_k; a segment's entries are read 32 at a time and broadcast), and each
-// lane stores its row's chunk as 16-byte vectors.  Half
-// chunks (16 d) without any entry are skipped: they are zero for every q, and the operand is
-// cleared once per job.
+// One warp per (b, c) pair and block of 32 bands (lane = band nu).  The pair's entries are
+// contiguous and ordered by d: the lanes read them 32 at a time, (a, d, w) are broadcast by
+// shuffles, and each run of equal d sums w e_q(a, nu) (a coalesced read of e_q's row a) in
+// registers and writes it once into the warp's shared-memory tile (rows padded to 65 words:
+// conflict-free row writes).  A chunk of 32 d is then stored transposed, eight lanes per row,
+// so that every store instruction writes whole 128-byte lines, with the d that no run wrote
+// selected as zero.  The next pair's bounds and
+// first batch are read while the current one is summed.  Chunks without any entry are
+// skipped: they are zero for every q, and the operand is cleared once per job.  When e_q fits
+// beside the tiles (n <= 96: 16 warps, one CTA per SM) the CTA first copies it to shared
+// memory; otherwise (8 warps, three CTAs per SM) it is read through the caches.
+constexpr int kFoldPitch = 65;
+constexpr size_t kFoldTile = 32 * kFoldPitch * sizeof(float);      // per warp
+constexpr size_t kFoldSmemMax = 220 * 1024;
+
 template <int PREC>
-__global__ void __launch_bounds__(256, 3) fold_tc_kernel(const int32_t* __restrict__ seg_of,
-                                                      const int64_t* __restrict__ seg_start,
-                                                      const int32_t* __restrict__ ent_a,
-                                                      const float2* __restrict__ wph, int n_d,
-                                                      const float2* __restrict__ eqf, int n, int nu0, int nnu,
-                                                      int kcp, void* hi, void* lo) {
+__global__ void __launch_bounds__(512) fold_tc_kernel(const int64_t* __restrict__ bc_start,
+                                                      const int2* __restrict__ ent_ad,
+                                                      const float2* __restrict__ wph,
+                                                      const float2* __restrict__ eqf_g, int n, int nu0,
+                                                      int nnu, int kcp, int eq_smem, void* hi, void* lo) {
+    extern __shared__ float s_fold[];
     const int lane = threadIdx.x & 31;
+    float* tile = s_fold + (threadIdx.x >> 5) * 32 * kFoldPitch;
+    const float2* eqf = eqf_g;
+    if (eq_smem) {
+        float2* s_eq = reinterpret_cast<float2*>(s_fold + (blockDim.x >> 5) * 32 * kFoldPitch);
+        for (int i = threadIdx.x; i < n * n; i += blockDim.x) s_eq[i] = eqf_g[i];
+        __syncthreads();
+        eqf = s_eq;
+    }
     const int nn = n * n, kr = 2 * kcp;
     const int64_t items = (int64_t)nn * ((nnu + 31) / 32);
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t it = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += warps) {
-        const int bc = (int)(it % nn);                 // adjacent warps: adjacent (b, c), adjacent table rows
-        const int nl = (int)(it / nn) * 32 + lane;     // band within the chunk of bands
-        const bool live = nl < nnu;
-        const float2* erow = eqf + (nu0 + (live ? nl : 0));
-        for (int dc = 0; dc < kcp; dc += 32) {
-            const int dl = dc + lane;
-            const int sg = dl < n_d ? seg_of[(int64_t)bc * n_d + dl] : -1;
-            int64_t k0 = 0, k1 = 0;
-            if (sg >= 0) { k0 = seg_start[sg]; k1 = seg_start[sg + 1]; }
-            const unsigned has = __ballot_sync(0xffffffffu, sg >= 0);
-            if (has == 0) continue;
-            // two halves of 16 d (keeps the accumulators at 32 registers)
-#pragma unroll
-            for (int h = 0; h < 32; h += 16) {
-                if (((has >> h) & 0xffffu) == 0) continue;
-                float ar[16], ai[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    ar[i] = 0.f;
-                    ai[i] = 0.f;
-                    if (!((has >> (h + i)) & 1u)) continue;
-                    const int64_t s0 = __shfl_sync(0xffffffffu, k0, h + i), s1 = __shfl_sync(0xffffffffu, k1, h + i);
-                    // up to 32 entries at a time: one coalesced read of (a_k, w_k), then broadcasts,
-                    // so the e_q reads of successive entries are independent
-                    for (int64_t kb = s0; kb < s1; kb += 32) {
-                        const int cnt = s1 - kb < 32 ? (int)(s1 - kb) : 32;
-                        int a_l = 0;
-                        float2 w_l = make_float2(0.f, 0.f);
-                        if (lane < cnt) { a_l = ent_a[kb + lane]; w_l = wph[kb + lane]; }
-#pragma unroll 4
-                        for (int j = 0; j < cnt; ++j) {
-                            const int a = __shfl_sync(0xffffffffu, a_l, j);
-                            const float wx = __shfl_sync(0xffffffffu, w_l.x, j), wy = __shfl_sync(0xffffffffu, w_l.y, j);
-                            const float2 e = erow[(int64_t)a * n];
-                            ar[i] += wx * e.x - wy * e.y;
-                            ai[i] += wx * e.y + wy * e.x;
+    const int2 none = make_int2(0, -1);
+    // store lanes: row group lane >> 3, part (lane >> 2) & 1 (Re, Im), 8-element chunk lane & 3
+    const int st_row = lane >> 3, st_part = (lane >> 2) & 1, st_chunk = (lane & 3) * 8;
+    int64_t it = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    // bounds of item it (a) and it + warps (b); first batch of item it
+    int64_t a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+    int2 ad = none;
+    float2 w = make_float2(0.f, 0.f);
+    if (it < items) {
+        const int bc = (int)(it % nn);
+        a0 = bc_start[bc]; a1 = bc_start[bc + 1];
+        if (lane < a1 - a0) { ad = ent_ad[a0 + lane]; w = wph[a0 + lane]; }
+    }
+    if (it + warps < items) {
+        const int bc = (int)((it + warps) % nn);
+        b0 = bc_start[bc]; b1 = bc_start[bc + 1];
+    }
+    for (; it < items; it += warps) {
+        // in flight while this item is summed: the next item's first batch, the bounds after it
+        int2 nad = none;
+        float2 nw = make_float2(0.f, 0.f);
+        if (it + warps < items && lane < b1 - b0) { nad = ent_ad[b0 + lane]; nw = wph[b0 + lane]; }
+        int64_t c0 = 0, c1 = 0;
+        if (it + 2 * warps < items) {
+            const int bc = (int)((it + 2 * warps) % nn);
+            c0 = bc_start[bc]; c1 = bc_start[bc + 1];
+        }
+        if (a1 > a0) {
+            const int bc = (int)(it % nn);
+            const int band0 = (int)(it / nn) * 32;         // first band of the block
+            const int nl = band0 + lane;
+            const float2* erow = eqf + (nu0 + (nl < nnu ? nl : 0));
+            int64_t jb = a0, j = a0;                       // first entry of the batch, next entry
+            for (int dc = 0; dc < kcp && j < a1; dc += 32) {
+                // runs of equal d (entries are ordered by d): each run's sum goes to the tile once,
+                // and the mask of written d zero-selects the rest when the chunk is stored
+                uint32_t mask = 0;
+                while (j < a1) {
+                    int t = (int)(j - jb);
+                    const int d = __shfl_sync(0xffffffffu, ad.y, t);
+                    if (d >= dc + 32) break;
+                    float sr = 0.f, si = 0.f;
+                    do {
+                        const int a = __shfl_sync(0xffffffffu, ad.x, t);
+                        const float wx = __shfl_sync(0xffffffffu, w.x, t), wy = __shfl_sync(0xffffffffu, w.y, t);
+                        const float2 e = erow[(int64_t)a * n];
+                        sr += wx * e.x - wy * e.y;
+                        si += wx * e.y + wy * e.x;
+                        if (++j - jb == 32 && j < a1) {
+                            jb = j;
+                            ad = lane < a1 - jb ? ent_ad[jb + lane] : none;
+                            w = lane < a1 - jb ? wph[jb + lane] : make_float2(0.f, 0.f);
                         }
-                    }
+                        t = (int)(j - jb);
+                    } while (j < a1 && __shfl_sync(0xffffffffu, ad.y, t) == d);
+                    tile[lane * kFoldPitch + (d - dc)] = sr;
+                    tile[lane * kFoldPitch + 32 + (d - dc)] = si;
+                    mask |= 1u << (d - dc);
                 }
-                if (live) {
-                    const int64_t base = ((int64_t)nl * nn + bc) * kr + dc + h;
+                if (mask == 0) continue;
+                __syncwarp();
+#pragma unroll 2
+                for (int g = 0; g < 32; g += 4) {
+                    const int r = g + st_row;
+                    if (band0 + r < nnu) {
+                        const float* src = tile + r * kFoldPitch + st_part * 32 + st_chunk;
+                        float v[8];
 #pragma unroll
-                    for (int j = 0; j < 16; j += 8) {
-                        store_operand8<PREC>(hi, lo, base + j, ar + j);
-                        store_operand8<PREC>(hi, lo, base + kcp + j, ai + j);
+                        for (int k = 0; k < 8; ++k) v[k] = ((mask >> (st_chunk + k)) & 1u) ? src[k] : 0.f;
+                        store_operand8<PREC>(hi, lo, ((int64_t)(band0 + r) * nn + bc) * kr + st_part * kcp + dc + st_chunk, v);
                     }
                 }
+                __syncwarp();
             }
         }
+        a0 = b0; a1 = b1; b0 = c0; b1 = c1;
+        ad = nad; w = nw;
     }
 }
 
@@ -1264,30 +1309,54 @@ phx_status tc_plan(phx_ctx* ctx, const phx_fc3* f, int prec, int q_override, TcP
     return PHX_OK;
 }
 
-// Per-crystal device tables (kept with the Phi3 handle): dense segment map [b][c][d] and the
-// identity index list of the mesh.  Host work; must run before any stream capture.
+// Per-crystal device tables (kept with the Phi3 handle): the entries grouped by (b, c), then
+// d, then a, with their source positions.  Host work; must run before any stream capture.
 phx_status tc_prepare_fc3(phx_ctx* ctx, phx_fc3* f) {
-    if (f->tc_seg_of) return PHX_OK;
-    const int n = f->n, nq = f->nq;
-    const int64_t n2 = (int64_t)n * n;
-    std::vector<int32_t> id(nq);
-    for (int i = 0; i < nq; ++i) id[i] = i;
-    std::vector<int32_t> so((size_t)f->n_d * n2, -1);
-    std::vector<int32_t> keys((size_t)f->n_seg * 3);
-    PHX_CUDA_CHECK(ctx, cudaMemcpy(keys.data(), f->seg_key, keys.size() * 4, cudaMemcpyDeviceToHost));
-    for (int64_t sgi = 0; sgi < f->n_seg; ++sgi)
-        so[((size_t)keys[3 * sgi + 1] * n + keys[3 * sgi + 2]) * f->n_d + keys[3 * sgi]] = (int32_t)sgi;
-    int32_t *dso = nullptr, *did = nullptr;
-    if (cudaMalloc(&dso, std::max<size_t>(so.size() * 4, 16)) != cudaSuccess ||
-        cudaMalloc(&did, std::max<size_t>(id.size() * 4, 16)) != cudaSuccess) {
+    if (f->tc_bc_start) return PHX_OK;
+    const int n = f->n;
+    const int64_t n2 = (int64_t)n * n, nnz = f->nnz, ns = f->n_seg;
+    std::vector<int32_t> keys((size_t)ns * 3), ea((size_t)nnz);
+    std::vector<int64_t> ss((size_t)ns + 1, 0);
+    if (ns > 0) {
+        PHX_CUDA_CHECK(ctx, cudaMemcpy(keys.data(), f->seg_key, keys.size() * 4, cudaMemcpyDeviceToHost));
+        PHX_CUDA_CHECK(ctx, cudaMemcpy(ss.data(), f->seg_start, ss.size() * 8, cudaMemcpyDeviceToHost));
+        PHX_CUDA_CHECK(ctx, cudaMemcpy(ea.data(), f->ent_a, ea.size() * 4, cudaMemcpyDeviceToHost));
+    }
+    std::vector<int64_t> start((size_t)n2 + 1, 0);
+    for (int64_t sg = 0; sg < ns; ++sg) start[(int64_t)keys[3 * sg + 1] * n + keys[3 * sg + 2] + 1] += ss[sg + 1] - ss[sg];
+    for (int64_t b = 0; b < n2; ++b) start[b + 1] += start[b];
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    std::vector<int2> ad((size_t)nnz);
+    std::vector<int32_t> src((size_t)nnz);
+    // segments are stored in (d, b, c) order and their entries in a order, so each pair's
+    // entries come out in (d, a) order
+    for (int64_t sg = 0; sg < ns; ++sg) {
+        const int64_t bc = (int64_t)keys[3 * sg + 1] * n + keys[3 * sg + 2];
+        for (int64_t k = ss[sg]; k < ss[sg + 1]; ++k) {
+            const int64_t j = fill[bc]++;
+            ad[j] = make_int2(ea[k], keys[3 * sg]);
+            src[j] = (int32_t)k;
+        }
+    }
+    int64_t* dstart = nullptr;
+    int2* dad = nullptr;
+    int32_t* dsrc = nullptr;
+    if (cudaMalloc(&dstart, start.size() * 8) != cudaSuccess ||
+        cudaMalloc(&dad, std::max<size_t>(ad.size() * sizeof(int2), 16)) != cudaSuccess ||
+        cudaMalloc(&dsrc, std::max<size_t>(src.size() * 4, 16)) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(dso);
+        cudaFree(dstart);
+        cudaFree(dad);
         return phx_set_error(ctx, PHX_ERR_NOMEM, "tensor-core tables: allocation failed");
     }
-    PHX_CUDA_CHECK(ctx, cudaMemcpy(dso, so.data(), so.size() * 4, cudaMemcpyHostToDevice));
-    PHX_CUDA_CHECK(ctx, cudaMemcpy(did, id.data(), id.size() * 4, cudaMemcpyHostToDevice));
-    f->tc_seg_of = dso;
-    f->tc_ident = did;
+    PHX_CUDA_CHECK(ctx, cudaMemcpy(dstart, start.data(), start.size() * 8, cudaMemcpyHostToDevice));
+    if (nnz > 0) {
+        PHX_CUDA_CHECK(ctx, cudaMemcpy(dad, ad.data(), ad.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        PHX_CUDA_CHECK(ctx, cudaMemcpy(dsrc, src.data(), src.size() * 4, cudaMemcpyHostToDevice));
+    }
+    f->tc_bc_start = dstart;
+    f->tc_ent_ad = dad;
+    f->tc_ent_src = dsrc;
     return PHX_OK;
 }
 
@@ -1427,7 +1496,7 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
         PHX_CUDA_CHECK(ctx, cudaGetLastError());
         ctx->launches += 2;
         const int pblocks = (int)std::min<int64_t>((f->nnz + n2 + 255) / 256, 4096);
-        fold_phase_kernel<<<pblocks, 256, 0, s>>>(f->ent_r2, f->ent_w, f->nnz, (double)k1 / f->mesh[0],
+        fold_phase_kernel<<<pblocks, 256, 0, s>>>(f->tc_ent_src, f->ent_r2, f->ent_w, f->nnz, (double)k1 / f->mesh[0],
                                                   (double)k2 / f->mesh[1], (double)k3 / f->mesh[2], B.wph,
                                                   (const double2*)evec + (int64_t)iq * n2, (int)n2, B.eqf);
         PHX_CUDA_CHECK(ctx, cudaGetLastError());
@@ -1442,9 +1511,20 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
             {
                 const int pf = phx_prof_begin(ctx, s);
                 const int64_t items = n2 * ((nnu + 31) / 32);
-                const int blocks = (int)std::min<int64_t>((items + 7) / 8, (int64_t)sms * 3);   // 3 CTAs per SM fit
-                fold_tc_kernel<PREC><<<blocks, 256, 0, s>>>(f->tc_seg_of, f->seg_start, f->ent_a, B.wph, f->n_d, B.eqf,
-                                                            n, nu0, nnu, kcp_d, B.W.hi, B.W.lo);
+                // e_q in shared memory beside 16 warps' tiles when it fits (one CTA per SM), else
+                // 8 warps per CTA and three CTAs per SM
+                const bool eq_smem = 16 * kFoldTile + (size_t)n2 * sizeof(float2) <= kFoldSmemMax;
+                const int fw = eq_smem ? 16 : 8, per_sm = eq_smem ? 1 : 3;
+                const size_t fsmem = fw * kFoldTile + (eq_smem ? (size_t)n2 * sizeof(float2) : 0);
+                const int blocks = (int)std::min<int64_t>((items + fw - 1) / fw, (int64_t)sms * per_sm);
+                static bool fold_attr = false;
+                if (!fold_attr) {
+                    PHX_CUDA_CHECK(ctx, cudaFuncSetAttribute(fold_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                             (int)kFoldSmemMax));
+                    fold_attr = true;
+                }
+                fold_tc_kernel<PREC><<<blocks, 32 * fw, fsmem, s>>>(f->tc_bc_start, f->tc_ent_ad, B.wph, B.eqf, n, nu0, nnu,
+                                                                   kcp_d, eq_smem ? 1 : 0, B.W.hi, B.W.lo);
                 PHX_CUDA_CHECK(ctx, cudaGetLastError());
                 phx_prof_end(ctx, pf, s, PHX_K_FOLD, 8.0 * (double)f->nnz * nnu, (double)rw * kr_d * esz * planes);
                 ctx->launches += 1;

@@ -113,6 +113,9 @@ const char* phx_version(void);
  *     orderings (|V3|^2 is the same for both: Eq. (phi3_proj) is symmetric in the modes), so
  *     about half of the q' are contracted; 0 = every q' of the mesh.  Results agree to
  *     rounding.  The FP64 path always sums every q'.
+ *   PHX_OPT_SIDE_SMS: with the chained kernel, the fold and Fourier stages (S3, S4) of the next
+ *     q' tile run on a second stream over this many SMs while the chained kernel runs on the
+ *     others (M double-buffered); -1 (default) = the library's choice, 0 = one stream; at most 76.
  *   PHX_OPT_WAIT_LIMIT_NS: bound of every device barrier wait of the tensor-core kernels
  *     (default 2e9 ns); a wait that runs out makes the kernel retire and the call return
  *     PHX_ERR_TIMEOUT (host-memory calls; device-memory calls leave the status to the next
@@ -120,7 +123,13 @@ const char* phx_version(void);
  *   PHX_OPT_STARVE: test hook; nonzero makes the tensor-core kernels' load producers issue
  *     nothing, so the first barrier wait runs out with no copy or MMA in flight.
  * Errors: PHX_ERR_INVALID for an unknown option or a value out of range. */
-typedef enum { PHX_OPT_CHAIN = 0, PHX_OPT_WAIT_LIMIT_NS = 1, PHX_OPT_STARVE = 2, PHX_OPT_PAIR = 3 } phx_option;
+typedef enum {
+    PHX_OPT_CHAIN = 0,
+    PHX_OPT_WAIT_LIMIT_NS = 1,
+    PHX_OPT_STARVE = 2,
+    PHX_OPT_PAIR = 3,
+    PHX_OPT_SIDE_SMS = 4
+} phx_option;
 phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value);
 
 /* ---------------------------------------------------------------- grid (host only)

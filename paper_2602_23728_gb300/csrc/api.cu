@@ -160,6 +160,9 @@ void phx_destroy(phx_ctx* ctx) {
     cudaFree(ctx->status_word);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+    for (cudaEvent_t e : ctx->side_ev)
+        if (e) cudaEventDestroy(e);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -199,6 +202,10 @@ phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value) {
             return PHX_OK;
         case PHX_OPT_STARVE:
             ctx->opt_starve = value != 0;
+            return PHX_OK;
+        case PHX_OPT_SIDE_SMS:
+            if (value < -1 || value > 76) return phx_set_error(ctx, PHX_ERR_INVALID, "PHX_OPT_SIDE_SMS %lld", (long long)value);
+            ctx->opt_side_sms = (int)value;
             return PHX_OK;
         case PHX_OPT_PAIR:
             if (value < 0 || value > 1) return phx_set_error(ctx, PHX_ERR_INVALID, "PHX_OPT_PAIR %lld", (long long)value);

@@ -46,6 +46,10 @@ struct phx_ctx {
     // batched path: capture stream, cached graph of the last job list, q'-tile autotune table
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // chained linewidth path: side stream of the fold and Fourier GEMM, with its fork, join and
+    // buffer events (created outside any capture)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t side_ev[8] = {};
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<uint8_t> graph_key;
     int64_t graph_launches = 0;
@@ -53,6 +57,7 @@ struct phx_ctx {
     // options (phx_set_option)
     int opt_chain = 0;                            // 0 auto, 1 force the chained kernel, 2 never
     int opt_pair = 1;                             // evaluate each exchange pair {q', q''} once
+    int opt_side_sms = -1;                        // SMs of the side stream (-1: default, 0: one stream)
     unsigned long long opt_wait_ns = 2000000000ull;   // bound of every device barrier wait
     int opt_starve = 0;                           // test hook: tensor-core producers issue nothing
 };

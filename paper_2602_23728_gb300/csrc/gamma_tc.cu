@@ -1362,6 +1362,7 @@ phx_status tc_prepare_fc3(phx_ctx* ctx, phx_fc3* f) {
 
 struct TcBuffers {
     Operand W, M, X, E, P, T;
+    size_t x_bytes = 0;         // bytes of each X plane (X, or the chained kernel's second M buffer)
     int32_t* qp = nullptr;      // q' list of the current irreducible q (pair_list_kernel)
     int32_t* qpp = nullptr;     // and their q''
     float2* wph = nullptr;
@@ -1378,15 +1379,37 @@ phx_status tc_alloc(phx_ctx* ctx, int prec, size_t bw, size_t bm, size_t bx, siz
         o->lo = planes == 2 ? phx_ws(ctx, nl.c_str(), bytes) : nullptr;
         return o->hi && (planes == 1 || o->lo);
     };
+    b->x_bytes = bx;
     if (!get("tc.W", bw, &b->W) || !get("tc.M", bm, &b->M) || !get("tc.X", bx, &b->X) || !get("tc.E", be, &b->E) ||
         !get("tc.P", bp, &b->P) || !get("tc.T", bt, &b->T))
         return PHX_ERR_NOMEM;
-    b->qp = (int32_t*)phx_ws(ctx, "tc.qp", (size_t)max_nq * 4);
-    b->qpp = (int32_t*)phx_ws(ctx, "tc.qpp", (size_t)max_nq * 4);
+    b->qp = (int32_t*)phx_ws(ctx, "tc.qp", (size_t)max_nq * 8);      // two lists (by q parity)
+    b->qpp = (int32_t*)phx_ws(ctx, "tc.qpp", (size_t)max_nq * 8);
     b->wph = (float2*)phx_ws(ctx, "tc.wph", (size_t)std::max<int64_t>(max_nnz, 1) * sizeof(float2));
     b->eqf = (float2*)phx_ws(ctx, "tc.eqf", (size_t)max_n2 * sizeof(float2));
     if (!b->qp || !b->qpp || !b->wph || !b->eqf) return PHX_ERR_NOMEM;
     return PHX_OK;
+}
+
+// Side stream and events of the chained path (created once per context, outside any capture).
+phx_status ensure_side(phx_ctx* ctx) {
+    if (ctx->side_stream) return PHX_OK;
+    PHX_CUDA_CHECK(ctx, cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : ctx->side_ev) PHX_CUDA_CHECK(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return PHX_OK;
+}
+
+// SMs given to the side stream: the option, else PHX_SIDE_SMS, else 48 of 152 (measured at
+// fcc32 8^3: 24 / 32 / 40 / 48 side SMs give 713 / 556 / 464 / 412 ms per step against 441 ms
+// on one stream; the fold and Fourier GEMM of a tile then take about as long on 48 SMs as
+// the chained kernel on the other 104).
+int side_sms(const phx_ctx* ctx, int sms) {
+    int v = ctx->opt_side_sms;
+    if (v < 0) {
+        v = 48 * sms / 152;
+        if (const char* env = getenv("PHX_SIDE_SMS")) v = atoi(env);
+    }
+    return std::max(0, std::min(v, sms / 2));
 }
 
 // Enqueue the whole linewidth computation of one job on `s` (kernel launches and memsets
@@ -1407,7 +1430,8 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
     // padding columns of M, X and W must read as zero for this job's layout
     for (int pl = 0; pl < planes; ++pl) {
         PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.M.lo : B.M.hi, 0, P.bytes_m, s));
-        if (!P.chain) PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.X.lo : B.X.hi, 0, P.bytes_m, s));
+        if (B.x_bytes >= P.bytes_m)   // X, or the chained kernel's second M buffer
+            PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.X.lo : B.X.hi, 0, P.bytes_m, s));
         PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.W.lo : B.W.hi, 0, P.bytes_w, s));
     }
     if (P.chain)
@@ -1420,6 +1444,7 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
 
     TcArgs aD{}, aA{}, aB{};
     ChainArgs aC{};
+    CUtensorMap m_map2[2];          // chained kernel: M maps of the second buffer
     const int64_t m_rows = (int64_t)Q * P.rows_a;
     for (int pl = 0; pl < planes; ++pl) {
         const void* w = pl ? B.W.lo : B.W.hi;
@@ -1432,6 +1457,7 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
             ok = ok && make_map(&aC.ta_map[pl], t, PREC, (int64_t)nq * n, kr, P.c_ra) &&
                  make_map(&aC.tb_map[pl], t, PREC, (int64_t)nq * n, kr, P.c_rb3) &&
                  make_map(&aC.m_map[pl], m, PREC, m_rows, kr, kcp);
+            if (B.x_bytes >= P.bytes_m) ok = ok && make_map(&m_map2[pl], pl ? B.X.lo : B.X.hi, PREC, m_rows, kr, kcp);
         } else {
             const void* x = pl ? B.X.lo : B.X.hi;
             const void* e = pl ? B.E.lo : B.E.hi;
@@ -1484,21 +1510,39 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
         aB.g1_rows = (int64_t)n_irr * n;
     }
 
+    // Chained path with a side stream: the per-q lists, the fold and the Fourier GEMM run on s2
+    // over `side` SMs, the chained kernel on s over the others.  M alternates between two
+    // buffers by tile (the second is the X workspace, which the chained kernel does not use) and
+    // the q' lists between two by q; events order every producer before its consumer and every
+    // consumer before the producer that overwrites its buffer.
+    const int side = (P.chain && ctx->side_stream && B.x_bytes >= P.bytes_m) ? side_sms(ctx, sms) : 0;
+    cudaStream_t s2 = side > 0 ? ctx->side_stream : s;
+    cudaEvent_t* ev = ctx->side_ev;       // [0] fork, [1] join, [2..3] M ready, [4..5] M free, [6..7] lists free
+    const int main_ctas = sms - side, side_ctas = side > 0 ? side : sms;
+    if (side > 0) {
+        PHX_CUDA_CHECK(ctx, cudaEventRecord(ev[0], s));
+        PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(s2, ev[0], 0));
+    }
+    int64_t g = 0;                        // tiles enqueued so far
     for (int si = 0; si < n_irr; ++si) {
         const int iq = irr_host[si];
         const int k1 = iq / (f->mesh[1] * f->mesh[2]), k2 = (iq / f->mesh[2]) % f->mesh[1], k3 = iq % f->mesh[2];
+        const int qb = side > 0 ? (si & 1) : 0;
+        int32_t* qp_l = B.qp + (int64_t)qb * nq;
+        int32_t* qpp_l = B.qpp + (int64_t)qb * nq;
+        if (side > 0 && si >= 2) PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(s2, ev[6 + qb], 0));
         // this q's q' list (exchange pairs) in tiles of at most Q, balanced, and their phase tables
-        pair_list_kernel<<<1, 1024, 0, s>>>(iq, f->mesh[0], f->mesh[1], f->mesh[2], pair ? 1 : 0, B.qp, B.qpp);
+        pair_list_kernel<<<1, 1024, 0, s2>>>(iq, f->mesh[0], f->mesh[1], f->mesh[2], pair ? 1 : 0, qp_l, qpp_l);
         const int count = pair_count(iq, f->mesh, pair);
         const int n_tq = (count + Q - 1) / Q, Qb = (count + n_tq - 1) / n_tq;
-        prep_phase_tables<PREC><<<64, 256, 0, s>>>(f->d_int, f->n_d, f->mesh[0], f->mesh[1], f->mesh[2], B.qp, count,
-                                                   Qb, n_tq, qp_np, kcp_d, B.P.hi, B.P.lo);
+        prep_phase_tables<PREC><<<64, 256, 0, s2>>>(f->d_int, f->n_d, f->mesh[0], f->mesh[1], f->mesh[2], qp_l, count,
+                                                    Qb, n_tq, qp_np, kcp_d, B.P.hi, B.P.lo);
         PHX_CUDA_CHECK(ctx, cudaGetLastError());
         ctx->launches += 2;
         const int pblocks = (int)std::min<int64_t>((f->nnz + n2 + 255) / 256, 4096);
-        fold_phase_kernel<<<pblocks, 256, 0, s>>>(f->tc_ent_src, f->ent_r2, f->ent_w, f->nnz, (double)k1 / f->mesh[0],
-                                                  (double)k2 / f->mesh[1], (double)k3 / f->mesh[2], B.wph,
-                                                  (const double2*)evec + (int64_t)iq * n2, (int)n2, B.eqf);
+        fold_phase_kernel<<<pblocks, 256, 0, s2>>>(f->tc_ent_src, f->ent_r2, f->ent_w, f->nnz, (double)k1 / f->mesh[0],
+                                                   (double)k2 / f->mesh[1], (double)k3 / f->mesh[2], B.wph,
+                                                   (const double2*)evec + (int64_t)iq * n2, (int)n2, B.eqf);
         PHX_CUDA_CHECK(ctx, cudaGetLastError());
         ctx->launches += 2;
         aB.iq = iq;
@@ -1509,24 +1553,24 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
             const int nnu = std::min(n_nu, n - nu0);
             const int64_t rw = (int64_t)nnu * n2, ra = (int64_t)nnu * n;
             {
-                const int pf = phx_prof_begin(ctx, s);
+                const int pf = phx_prof_begin(ctx, s2);
                 const int64_t items = n2 * ((nnu + 31) / 32);
                 // e_q in shared memory beside 16 warps' tiles when it fits (one CTA per SM), else
                 // 8 warps per CTA and three CTAs per SM
                 const bool eq_smem = 16 * kFoldTile + (size_t)n2 * sizeof(float2) <= kFoldSmemMax;
                 const int fw = eq_smem ? 16 : 8, per_sm = eq_smem ? 1 : 3;
                 const size_t fsmem = fw * kFoldTile + (eq_smem ? (size_t)n2 * sizeof(float2) : 0);
-                const int blocks = (int)std::min<int64_t>((items + fw - 1) / fw, (int64_t)sms * per_sm);
+                const int blocks = (int)std::min<int64_t>((items + fw - 1) / fw, (int64_t)side_ctas * per_sm);
                 static bool fold_attr = false;
                 if (!fold_attr) {
                     PHX_CUDA_CHECK(ctx, cudaFuncSetAttribute(fold_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                              (int)kFoldSmemMax));
                     fold_attr = true;
                 }
-                fold_tc_kernel<PREC><<<blocks, 32 * fw, fsmem, s>>>(f->tc_bc_start, f->tc_ent_ad, B.wph, B.eqf, n, nu0, nnu,
-                                                                   kcp_d, eq_smem ? 1 : 0, B.W.hi, B.W.lo);
+                fold_tc_kernel<PREC><<<blocks, 32 * fw, fsmem, s2>>>(f->tc_bc_start, f->tc_ent_ad, B.wph, B.eqf, n, nu0,
+                                                                    nnu, kcp_d, eq_smem ? 1 : 0, B.W.hi, B.W.lo);
                 PHX_CUDA_CHECK(ctx, cudaGetLastError());
-                phx_prof_end(ctx, pf, s, PHX_K_FOLD, 8.0 * (double)f->nnz * nnu, (double)rw * kr_d * esz * planes);
+                phx_prof_end(ctx, pf, s2, PHX_K_FOLD, 8.0 * (double)f->nnz * nnu, (double)rw * kr_d * esz * planes);
                 ctx->launches += 1;
             }
             aD.rows = (int)rw; aD.tiles = (int)((rw + kBoxRows - 1) / kBoxRows);
@@ -1536,34 +1580,45 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
             aB.rows = (int)ra; aB.tiles = aA.tiles; aB.a_rows_per_problem = (int)ra;
             aB.nu0 = nu0;
             aB.g1_row0 = (int64_t)si * n + nu0;
-            for (int tq = 0; tq < n_tq; ++tq) {
+            for (int tq = 0; tq < n_tq; ++tq, ++g) {
                 const int t0 = tq * Qb, Qt = std::min(Qb, count - t0);
+                const int mb = side > 0 ? (int)(g & 1) : 0;
                 aD.b_base = tq;
                 aD.nq_slots = Qt;
+                aD.out_hi = mb ? B.X.hi : B.M.hi;
+                aD.out_lo = mb ? B.X.lo : B.M.lo;
                 // algorithmic work: complex MACs x 8 flops; bytes: operands read + results written once
                 const double fl_d = 8.0 * (double)rw * Qt * f->n_d;
                 const double fl_e = 8.0 * (double)Qt * ra * n * n;
                 const double op_bytes = (double)planes * esz * 2.0;   // one complex value of an operand
-                int pp = phx_prof_begin(ctx, s);
-                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_M, false>(ctx, aD, 1, sms, s)));
-                phx_prof_end(ctx, pp, s, PHX_K_DFT, fl_d, op_bytes * ((double)rw * f->n_d + (double)Qt * ra * n));
+                if (side > 0 && g >= 2) PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(s2, ev[4 + mb], 0));
+                int pp = phx_prof_begin(ctx, s2);
+                PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_M, false>(ctx, aD, 1, side_ctas, s2)));
+                phx_prof_end(ctx, pp, s2, PHX_K_DFT, fl_d, op_bytes * ((double)rw * f->n_d + (double)Qt * ra * n));
                 if (P.chain) {
+                    if (side > 0) {
+                        PHX_CUDA_CHECK(ctx, cudaEventRecord(ev[2 + mb], s2));
+                        PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(s, ev[2 + mb], 0));
+                    }
                     aC.n_items = Qt * nnu; aC.nnu = nnu; aC.rows_per_slot = (int)ra;
-                    aC.qp = B.qp + t0; aC.qpp = B.qpp + t0; aC.pair = pair ? 1 : 0; aC.nu0 = nu0;
+                    aC.qp = qp_l + t0; aC.qpp = qpp_l + t0; aC.pair = pair ? 1 : 0; aC.nu0 = nu0;
                     aC.g1_row0 = (int64_t)si * n + nu0;
+                    ChainArgs ac = aC;
+                    if (mb) { ac.m_map[0] = m_map2[0]; ac.m_map[1] = m_map2[1]; }
                     pp = phx_prof_begin(ctx, s);
-                    PHX_CUDA_CHECK(ctx, launch_chain_mode<PREC>(aC, chain_mode, P.c_smem, sms, s));
+                    PHX_CUDA_CHECK(ctx, launch_chain_mode<PREC>(ac, chain_mode, P.c_smem, main_ctas, s));
                     // two contractions; bytes: the M operand read once
                     phx_prof_end(ctx, pp, s, PHX_K_CHAIN, 2.0 * fl_e, op_bytes * (double)Qt * ra * n);
+                    if (side > 0) PHX_CUDA_CHECK(ctx, cudaEventRecord(ev[4 + mb], s));
                     ctx->launches += 2;
                     continue;
                 }
-                aA.b_idx = B.qpp + t0;
+                aA.b_idx = qpp_l + t0;
                 pp = phx_prof_begin(ctx, s);
                 PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_X>(ctx, aA, P.stream_b, Qt, sms, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_GEMM_E2, fl_e, op_bytes * 2.0 * Qt * ra * n);
-                aB.b_idx = B.qp + t0;
-                aB.qp1 = B.qp + t0;
+                aB.b_idx = qp_l + t0;
+                aB.qp1 = qp_l + t0;
                 aB.pair = pair ? 1 : 0;
                 pp = phx_prof_begin(ctx, s);
                 if (n_t > 0)
@@ -1576,6 +1631,11 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
                 ctx->launches += 3;
             }
         }
+        if (side > 0) PHX_CUDA_CHECK(ctx, cudaEventRecord(ev[6 + qb], s));
+    }
+    if (side > 0) {
+        PHX_CUDA_CHECK(ctx, cudaEventRecord(ev[1], s2));
+        PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(s, ev[1], 0));
     }
     return PHX_OK;
 }
@@ -1589,8 +1649,10 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
     PHX_TRY(tc_plan(ctx, f, PREC, 0, &P));
     PHX_TRY(tc_prepare_fc3(ctx, const_cast<phx_fc3*>(f)));
     TcBuffers B;
-    PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.chain ? 0 : P.bytes_m, P.bytes_e, P.bytes_p, P.bytes_t, P.nq,
-                     f->nnz, (int64_t)P.n * P.n, &B));
+    const bool two_m = P.chain && side_sms(ctx, ctx->sm_count > 0 ? ctx->sm_count : 148) > 0;
+    if (two_m) PHX_TRY(ensure_side(ctx));
+    PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, (!P.chain || two_m) ? P.bytes_m : 0, P.bytes_e, P.bytes_p,
+                     P.bytes_t, P.nq, f->nnz, (int64_t)P.n * P.n, &B));
     return tc_enqueue<PREC>(ctx, P, f, B, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s, n_t, nb_stride,
                             t_stride, g1);
 }
@@ -1649,8 +1711,10 @@ phx_status autotune_q(phx_ctx* ctx, const phx_job& job, cudaStream_t s, int* bes
             if (P.Q == last_q) continue;                 // clamped to the mesh size already tried
             last_q = P.Q;
             TcBuffers B;
-            PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.chain ? 0 : P.bytes_m, P.bytes_e, P.bytes_p, P.bytes_t,
-                             P.nq, f->nnz, (int64_t)P.n * P.n, &B));
+            const bool two_m = P.chain && side_sms(ctx, ctx->sm_count > 0 ? ctx->sm_count : 148) > 0;
+            if (two_m) PHX_TRY(ensure_side(ctx));
+            PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, (!P.chain || two_m) ? P.bytes_m : 0, P.bytes_e, P.bytes_p,
+                             P.bytes_t, P.nq, f->nnz, (int64_t)P.n * P.n, &B));
             float best_rep = 1e30f;
             for (int rep = 0; rep < 2; ++rep) {
                 float ms = 0.f;
@@ -1703,14 +1767,17 @@ phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, const phx_
         chains[j] = ch;
         PHX_TRY(tc_plan(ctx, jb.fc3, PREC, q, &plans[j], ch));
     }
-    // workspace for the largest job, allocated before any capture
+    // workspace for the largest job, allocated before any capture (as are the side stream and its
+    // events: chained jobs then keep a second M buffer in the X workspace)
+    const int side = side_sms(ctx, ctx->sm_count > 0 ? ctx->sm_count : 148);
+    if (side > 0) PHX_TRY(ensure_side(ctx));
     size_t bw = 0, bm = 0, bx = 0, be = 0, bp = 0, bt = 0;
     int64_t mnq = 1, mnnz = 1, mn2 = 1, mnb = 1, mg = 1;
     for (int j = 0; j < n_jobs; ++j) {
         const TcPlan& P = plans[j];
         bw = std::max(bw, P.bytes_w); bm = std::max(bm, P.bytes_m); be = std::max(be, P.bytes_e);
         bp = std::max(bp, P.bytes_p); bt = std::max(bt, P.bytes_t);
-        if (!P.chain) bx = std::max(bx, P.bytes_m);
+        if (!P.chain || side > 0) bx = std::max(bx, P.bytes_m);
         mnq = std::max<int64_t>(mnq, P.nq); mnnz = std::max<int64_t>(mnnz, jobs[j].fc3->nnz);
         mn2 = std::max<int64_t>(mn2, (int64_t)P.n * P.n);
         mnb = std::max<int64_t>(mnb, (int64_t)P.nq * P.n);
@@ -1728,7 +1795,7 @@ phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, const phx_
     std::memcpy(key.data(), jobs, sizeof(phx_job) * n_jobs);
     std::memcpy(key.data() + sizeof(phx_job) * n_jobs, qtiles.data(), sizeof(int) * n_jobs);
     std::memcpy(key.data() + sizeof(phx_job) * n_jobs + sizeof(int) * n_jobs, chains.data(), sizeof(int) * n_jobs);
-    const int prec_v = PREC + 16 * ctx->opt_pair;      // the exchange-pair option changes the launches
+    const int prec_v = PREC + 16 * ctx->opt_pair + 32 * side;   // the pair and side-stream options change the launches
     std::memcpy(key.data() + sizeof(phx_job) * n_jobs + sizeof(int) * 2 * n_jobs, &prec_v, sizeof(int));
     // host irr lists are part of the key by content
     for (int j = 0; j < n_jobs; ++j) {

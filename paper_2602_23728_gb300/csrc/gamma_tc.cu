@@ -389,20 +389,49 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                 // destination advances by a fixed stride per column pair.
                 const int nb = row / args.n, ce = (row % args.n) & ~1;
                 const bool odd = lane & 1;
-                const int64_t slot_stride = (int64_t)args.out_rows_per_slot * args.out_kr;
-                const int64_t row_off = (int64_t)nb * args.out_kr + ce;
+                // 32-bit offsets (a tile of M is far below 2^31 elements per plane); a pair is one
+                // 32-bit word of each bf16 plane, split in one packed conversion
+                const uint32_t slot_stride = (uint32_t)args.out_rows_per_slot * (uint32_t)args.out_kr;
+                const uint32_t row_off = (uint32_t)nb * (uint32_t)args.out_kr + (uint32_t)ce;
                 for (int j0 = half * 16; j0 < NA; j0 += kStride) {
                     tc::tmem_ld16(taddr + j0, v);
                     const bool re = j0 < mg;
                     const int s0 = m0 + (re ? j0 : j0 - mg) + (odd ? 1 : 0);   // slot of this lane's first pair
                     const int n_ok = valid ? args.nq_slots - s0 : 0;            // pairs with slot < nq_slots
-                    int64_t idx = (int64_t)s0 * slot_stride + row_off + (re ? 0 : args.out_kcp);
+                    uint32_t idx = (uint32_t)s0 * slot_stride + row_off + (re ? 0u : (uint32_t)args.out_kcp);
+                    if (PREC == P_BF16X3) {
+                        uint32_t* hw = reinterpret_cast<uint32_t*>(args.out_hi);
+                        uint32_t* lw = reinterpret_cast<uint32_t*>(args.out_lo);
+                        uint32_t w = idx >> 1;                                   // idx is even
+                        // warp-uniform choice: both branches shuffle with the full mask
+                        if (__all_sync(0xffffffffu, n_ok >= 16)) {
 #pragma unroll
-                    for (int i = 0; i < 16; i += 2) {
-                        const float recv = __shfl_xor_sync(0xffffffffu, odd ? v[i] : v[i + 1], 1);
-                        const float a0 = odd ? recv : v[i], a1 = odd ? v[i + 1] : recv;
-                        if (i < n_ok) store_operand2<PREC>(args.out_hi, args.out_lo, idx, a0, a1);
-                        idx += 2 * slot_stride;
+                            for (int i = 0; i < 16; i += 2) {
+                                const float recv = __shfl_xor_sync(0xffffffffu, odd ? v[i] : v[i + 1], 1);
+                                uint32_t h, l;
+                                tc::split_bf16x2(odd ? recv : v[i], odd ? v[i + 1] : recv, &h, &l);
+                                hw[w] = h;
+                                lw[w] = l;
+                                w += slot_stride;                                // two slots = slot_stride words
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; i += 2) {
+                                const float recv = __shfl_xor_sync(0xffffffffu, odd ? v[i] : v[i + 1], 1);
+                                uint32_t h, l;
+                                tc::split_bf16x2(odd ? recv : v[i], odd ? v[i + 1] : recv, &h, &l);
+                                if (i < n_ok) { hw[w] = h; lw[w] = l; }
+                                w += slot_stride;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; i += 2) {
+                            const float recv = __shfl_xor_sync(0xffffffffu, odd ? v[i] : v[i + 1], 1);
+                            const float a0 = odd ? recv : v[i], a1 = odd ? v[i + 1] : recv;
+                            if (i < n_ok) store_operand2<PREC>(args.out_hi, args.out_lo, idx, a0, a1);
+                            idx += 2 * slot_stride;
+                        }
                     }
                 }
             } else if (EPI == EPI_M && (args.n & 1) == 0) {
@@ -1294,6 +1323,8 @@ phx_status tc_plan(phx_ctx* ctx, const phx_fc3* f, int prec, int q_override, TcP
     if (P.rows_w > INT32_MAX / 2) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: W chunk too large");
     P.bytes_w = (size_t)P.rows_w * P.kr_d * esz;
     P.bytes_m = (size_t)Q * P.rows_a * P.kr * esz;
+    if ((int64_t)Q * P.rows_a * P.kr >= ((int64_t)1 << 31))   // the Fourier epilogue indexes M in 32 bits
+        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "tensor-core path: q' tile of M too large");
     P.bytes_e = (size_t)nq * 2 * P.np * P.kr * esz;
     P.bytes_p = (size_t)P.n_tiles_q * 2 * P.qp_np * P.kr_d * esz;
     // Chained contractions: by default where they beat the three-GEMM chain (64 < n <= 96: the

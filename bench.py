@@ -94,10 +94,13 @@ def pair_count(iq, mesh, pair=True):
     return (nq + n_self) // 2
 
 
-def roofline_of(prof, steps, ms_step, precision, peaks, src, workload):
+def roofline_of(prof, steps, ms_step, precision, peaks, src, workload, sm_share=None):
     """Roofline of the kernel class with the most device time in a profiled pass of `steps`
     steps: tensor-bound classes against the tensor peak of the precision (algorithmic flops),
-    with the HBM figure (algorithmic bytes over the copy bandwidth) as a second field."""
+    with the HBM figure (algorithmic bytes over the copy bandwidth) as a second field.
+    sm_share: {class: (SMs the class runs on, SMs of the GPU)} for classes confined to part of
+    the GPU (the chained kernel next to the side stream); their line adds the fraction of the
+    peak of those SMs."""
     per = {k: v for k, v in prof.items() if k != "launches" and v[1] > 0}
     if not per:
         return None
@@ -119,6 +122,11 @@ def roofline_of(prof, steps, ms_step, precision, peaks, src, workload):
     roof.update({"algorithmic_flops_per_launch": fl / nl, "algorithmic_bytes_per_launch": by / nl,
                  "launches_per_step": nl / steps, "avg_launch_ms": tot_ms / nl,
                  "share_of_step": tot_ms / steps / ms_step})
+    if sm_share and name in sm_share and sm_share[name][0] < sm_share[name][1]:
+        used, total = sm_share[name]
+        roof.update({"sms": used, "sms_total": total, "frac_of_its_sms_peak": roof["frac"] * total / used,
+                     "sms_note": f"runs on {used} of {total} SMs while the fold and Fourier GEMM of the next q' "
+                                 f"tile run on the other {total - used} (frac is against the whole GPU's peak)"})
     return roof
 
 
@@ -467,7 +475,10 @@ def run_phx(args):
 
     # roofline of the kernel class with the most device time (events of the profiled step)
     peaks, src = load_peaks()
-    roof = roofline_of(prof, 1, ms_prof, args.precision, peaks, src, "fcc32")
+    sms_total = torch.cuda.get_device_properties(device).multi_processor_count
+    side = ctx.get_option("side_sms")
+    roof = roofline_of(prof, 1, ms_prof, args.precision, peaks, src, "fcc32",
+                       sm_share={"chain": (sms_total - side, sms_total)})
     # the whole step's contraction: 16 n flops per evaluated triplet (two complex contractions of
     # n terms, 8 flops per complex multiply-add) over the step time, against the same tensor peak
     peak_t, _ = tensor_peak(peaks, args.precision)
@@ -485,6 +496,7 @@ def run_phx(args):
                                    "Gaussian 0.1 THz",
                        "triplets_per_step_per_gpu": trip,
                        "exchange_pairs": bool(args.pair),
+                       "side_stream_sms": side,
                        "triplets_evaluated_per_step_per_gpu": trip_eval,
                        "triplet_count_note": "value counts every term (irreducible mode, q', nu', nu'') of the "
                                              "linewidth sums; with exchange pairs the kernels contract one q' "

@@ -131,6 +131,10 @@ typedef enum {
     PHX_OPT_SIDE_SMS = 4
 } phx_option;
 phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value);
+/* The value an option has in effect: for PHX_OPT_SIDE_SMS the SM count the chained path
+ * uses (the default resolved), for the others the value set.  Errors: PHX_ERR_INVALID for an
+ * unknown option or a null `value`. */
+phx_status phx_get_option(phx_ctx* ctx, int32_t option, int64_t* value);
 
 /* ---------------------------------------------------------------- grid (host only)
  * Irreducible set of a Gamma-centred mesh n1 x n2 x n3 (flat index (k1*n2+k2)*n3+k3)

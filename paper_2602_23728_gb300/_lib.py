@@ -97,6 +97,8 @@ lib.phx_kappa_sc.restype = C.c_int
 
 lib.phx_set_option.argtypes = [_P, _I, C.c_int64]
 lib.phx_set_option.restype = C.c_int
+lib.phx_get_option.argtypes = [_P, _I, C.c_void_p]
+lib.phx_get_option.restype = C.c_int
 lib.phx_profile_enable.argtypes = [_P, _I]
 lib.phx_profile_enable.restype = C.c_int
 lib.phx_profile_read.argtypes = [_P, _I, _P, _P, _P, _P]
@@ -137,7 +139,7 @@ KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4
 
 OPTIONS = {"chain": 0, "wait_limit_ns": 1, "starve": 2, "pair": 3, "side_sms": 4}
 
-EXPORTED = ["phx_set_option", "phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
+EXPORTED = ["phx_set_option", "phx_get_option", "phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
             "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_isotope", "phx_kappa_qhgk", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta", "phx_kappa_sc",
             "phx_kappa_rta_noalloc", "phx_gamma_batched", "phx_features", "phx_mlp_create", "phx_mlp_destroy",
             "phx_mlp_num_params", "phx_mlp_get_params", "phx_mlp_set_params", "phx_mlp_loss_grad", "phx_mlp_train",
@@ -281,6 +283,12 @@ class Context:
         'side_sms' (SMs of the fold/Fourier side stream next to the chained kernel; -1 default, 0 off),
         'wait_limit_ns' (bound of every device barrier wait), 'starve' (test hook)."""
         self._check(lib.phx_set_option(self.h, OPTIONS[name], int(value)))
+
+    def get_option(self, name):
+        """The option's value in effect ('side_sms': the SM count the chained path uses)."""
+        v = C.c_int64(0)
+        self._check(lib.phx_get_option(self.h, OPTIONS[name], C.addressof(v)))
+        return int(v.value)
 
     def profile_enable(self, on=True):
         self._check(lib.phx_profile_enable(self.h, 1 if on else 0))

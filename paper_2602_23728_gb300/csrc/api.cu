@@ -216,6 +216,19 @@ phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value) {
     }
 }
 
+phx_status phx_get_option(phx_ctx* ctx, int32_t option, int64_t* value) {
+    if (!ctx) return PHX_ERR_INVALID;
+    if (!value) return phx_set_error(ctx, PHX_ERR_INVALID, "phx_get_option: null value");
+    switch (option) {
+        case PHX_OPT_CHAIN: *value = ctx->opt_chain; return PHX_OK;
+        case PHX_OPT_WAIT_LIMIT_NS: *value = (int64_t)ctx->opt_wait_ns; return PHX_OK;
+        case PHX_OPT_STARVE: *value = ctx->opt_starve; return PHX_OK;
+        case PHX_OPT_PAIR: *value = ctx->opt_pair; return PHX_OK;
+        case PHX_OPT_SIDE_SMS: *value = phx_side_sms(ctx); return PHX_OK;
+        default: return phx_set_error(ctx, PHX_ERR_INVALID, "unknown option %d", option);
+    }
+}
+
 phx_status phx_profile_enable(phx_ctx* ctx, int32_t on) {
     if (!ctx) return PHX_ERR_INVALID;
     cudaSetDevice(ctx->device);

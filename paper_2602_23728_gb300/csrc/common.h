@@ -62,6 +62,9 @@ struct phx_ctx {
     int opt_starve = 0;                           // test hook: tensor-core producers issue nothing
 };
 
+// SMs the chained linewidth path gives to its side stream (gamma_tc.cu)
+int phx_side_sms(const phx_ctx* ctx);
+
 // Profiling helpers: begin returns a record slot (or -1 when profiling is off).
 int phx_prof_begin(phx_ctx* ctx, cudaStream_t s);
 void phx_prof_end(phx_ctx* ctx, int slot, cudaStream_t s, int kernel, double flops, double bytes);

@@ -1690,6 +1690,8 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
 
 }  // namespace
 
+int phx_side_sms(const phx_ctx* ctx) { return side_sms(ctx, ctx->sm_count > 0 ? ctx->sm_count : 148); }
+
 phx_status phx_gamma_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const double* evec, const double* nB,
                         const int32_t* irr_host, int n_irr, const GammaParams& gp, int prec, double* gacc,
                         double* wacc, cudaStream_t s, const G1Target* g1) {

@@ -131,3 +131,27 @@ def test_pair_scattering_rows(ctx, chain, mesh, shape, sigma):
 def test_pair_option_range(ctx, phx):
     with pytest.raises(phx.PhxError):
         ctx.set_option("pair", 2)
+
+
+@pytest.mark.parametrize("kind", ["fcc32-222", "cell72-333"])
+def test_side_stream_equals_one_stream(ctx, phx, kind):
+    """The fold and Fourier GEMM on a side stream next to the chained kernel (two M buffers,
+    event-ordered) give the one-stream result; only the CTA split of the items and so the
+    order of the FP64 accumulation changes."""
+    s = _setup(ctx, phx, kind)
+    ctx.set_option("chain", 1)
+    out = {}
+    for side in (0, -1, 16):
+        ctx.set_option("side_sms", side)
+        if side == 0:
+            assert ctx.get_option("side_sms") == 0
+        elif side == 16:
+            assert ctx.get_option("side_sms") == 16
+        else:
+            assert ctx.get_option("side_sms") > 0       # the library's default on a full GB300
+        out[side] = ctx.gamma(s["h"], s["freq"], s["evec"], s["irr"], s["T"], "gauss", s["sig"],
+                              precision="bf16x3")
+    for side in (-1, 16):
+        d = _rel(out[side], out[0])
+        print(f"{kind}: side {side} vs one stream {d:.2e}")
+        assert d < 1e-12

@@ -16,6 +16,7 @@
 
 #include "common.h"
 #include "gamma_common.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -158,6 +159,163 @@ gemm_f32_kernel(int M, int N, int K, const float* __restrict__ A, int lda, int64
             if (Z) Z[(int64_t)gm * ldc + gn] = z;
             C[(int64_t)gm * ldc + gn] = act ? z / (1.f + __expf(-z)) : z;
         }
+    }
+}
+
+// The same product on the tensor cores (tcgen05, kind::f16 in BF16x3: hi.hi + hi.lo + lo.hi,
+// FP32 accumulation in tensor memory), for the layers of width >= 16.  One CTA of 128
+// threads per 128-row tile of C (and per 128 columns, blockIdx.x) and member: K runs in chunks
+// of 64; for each chunk the threads read op(A) and op(B) from global memory (any
+// transposition; coalesced along whichever index is contiguous), split every value into bf16
+// hi and lo and write the 128-byte-swizzled K-major layout the MMA reads (within a 1024-byte
+// group of eight 128-byte rows, the 16-byte unit u of row r sits at unit u ^ (r % 8)); thread 0
+// issues the chunk's 4 K steps x 3 MMAs and commits, and the next chunk's writes wait for that
+// commit.  The epilogue reads the accumulator lane by lane (row = lane) and applies bias,
+// SiLU and the pre-activation output as gemm_f32_kernel does.  Every wait is bounded.
+constexpr int kMlpTcK = 64;                                   // K elements per chunk (128 bytes of bf16)
+constexpr uint32_t kMlpTcTile = 128 * 128;                    // bytes of one 128-row operand plane
+constexpr size_t kMlpTcSmem = 4 * (size_t)kMlpTcTile + 1024;  // A hi/lo, B hi/lo, alignment
+
+__device__ __forceinline__ uint32_t sw128_off(int r, int u) { return (uint32_t)(r * 128 + ((u ^ (r & 7)) << 4)); }
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128)
+gemm_tc_kernel(int M, int N, int K, const float* __restrict__ A, int lda, int64_t sA, const float* __restrict__ B,
+               int ldb, int64_t sB, float* __restrict__ C, int ldc, int64_t sC, const float* __restrict__ bias,
+               int64_t sBias, int act, float* __restrict__ Z, int accumulate, int ksplit, int32_t* status,
+               unsigned long long wait_ns) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t mma_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sAh = smem;
+    uint8_t* sAl = sAh + kMlpTcTile;
+    uint8_t* sBh = sAl + kMlpTcTile;
+    uint8_t* sBl = sBh + kMlpTcTile;
+    const int e = blockIdx.z, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
+    A += e * sA;
+    B += e * sB;
+    C += e * sC;
+    if (Z) Z += e * sC;
+    if (bias) bias += e * sBias;
+    const int n_ntiles = (N + 127) / 128;
+    const int m0 = blockIdx.y * 128, n0 = (blockIdx.x % n_ntiles) * 128, split = blockIdx.x / n_ntiles;
+    const int nt = min(128, N - n0), nmma = (nt + 15) & ~15;   // columns of this tile, MMA width
+    // K range of this split (whole chunks)
+    const int n_chunks_all = (K + kMlpTcK - 1) / kMlpTcK;
+    const int per = (n_chunks_all + ksplit - 1) / ksplit;
+    const int c_begin = split * per, c_end = min(n_chunks_all, c_begin + per);
+    const int n_chunks = max(0, c_end - c_begin);
+    if (t == 0) {
+        tc::mbar_init(&mma_bar, 1);
+        abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 128);
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t id = tc::idesc(128, nmma, 1u);
+    // This thread's share of a chunk: 8 units (8 K elements each) of A and of B.  Row-major
+    // operands: 8 threads per row read its 64 contiguous k; transposed ones: thread t takes
+    // row t (the contiguous index runs across the warp) and all 8 units.
+    auto a_row = [&](int i) { return TA ? t : i * 16 + (t >> 3); };
+    auto a_unit = [&](int i) { return TA ? i : (t & 7); };
+    auto b_row = [&](int i) { return TB ? i * 16 + (t >> 3) : t; };
+    auto b_unit = [&](int i) { return TB ? (t & 7) : i; };
+    float va[8][8], vb[8][8];
+    auto load = [&](int ch) {          // global -> registers, every load issued before any use
+        const int k0 = ch * kMlpTcK;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = a_row(i), kb = k0 + 8 * a_unit(i);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = kb + j;
+                va[i][j] = (m0 + r < M && k < K) ? (TA ? A[(int64_t)k * lda + m0 + r] : A[(int64_t)(m0 + r) * lda + k]) : 0.f;
+            }
+            const int rb = b_row(i), kc = k0 + 8 * b_unit(i);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = kc + j;
+                vb[i][j] = (rb < nt && k < K) ? (TB ? B[(int64_t)(n0 + rb) * ldb + k] : B[(int64_t)k * ldb + n0 + rb]) : 0.f;
+            }
+        }
+    };
+    auto put = [&](uint8_t* hi, uint8_t* lo, int r, int u, const float* v) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tc::split_bf16x2(v[2 * j], v[2 * j + 1], &h[j], &l[j]);
+        *reinterpret_cast<uint4*>(hi + sw128_off(r, u)) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(lo + sw128_off(r, u)) = make_uint4(l[0], l[1], l[2], l[3]);
+    };
+    bool ok = true;
+    if (n_chunks > 0) load(c_begin);
+    for (int q = 0; q < n_chunks; ++q) {
+        if (q > 0) {    // the previous chunk's MMAs have read the operands
+            ok = tc::mbar_wait(&mma_bar, (q - 1) & 1, &abort_flag, wait_ns);
+            if (!ok) { abort_flag = 1; atomicExch(status, (int)PHX_ERR_TIMEOUT); }
+            if (__syncthreads_or(!ok)) break;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            put(sAh, sAl, a_row(i), a_unit(i), va[i]);
+            if (b_row(i) < nmma) put(sBh, sBl, b_row(i), b_unit(i), vb[i]);
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (t == 0) {
+            tc::tc_fence_after();
+            const uint64_t ah = tc::sdesc_sw128(tc::smem_u32(sAh)), al = tc::sdesc_sw128(tc::smem_u32(sAl));
+            const uint64_t bh = tc::sdesc_sw128(tc::smem_u32(sBh)), bl = tc::sdesc_sw128(tc::smem_u32(sBl));
+#pragma unroll
+            for (int kk = 0; kk < kMlpTcK / 16; ++kk) {
+                const uint32_t acc = (q > 0 || kk > 0) ? 1u : 0u;
+                const uint64_t o = (uint64_t)(2 * kk);          // 32 bytes per K step, in 16-byte units
+                tc::mma_f16(tmem, ah + o, bh + o, id, acc);
+                tc::mma_f16(tmem, ah + o, bl + o, id, 1u);
+                tc::mma_f16(tmem, al + o, bh + o, id, 1u);
+            }
+            tc::mma_commit(&mma_bar);
+        }
+        if (q + 1 < n_chunks) load(c_begin + q + 1);   // in flight while the MMAs run
+    }
+    if (ok && n_chunks > 0) {
+        ok = tc::mbar_wait(&mma_bar, (n_chunks - 1) & 1, &abort_flag, wait_ns);
+        if (!ok) { abort_flag = 1; atomicExch(status, (int)PHX_ERR_TIMEOUT); }
+    }
+    ok = __syncthreads_and(ok) != 0;
+    tc::tc_fence_after();
+    if (ok && n_chunks > 0) {
+        // epilogue: warp w holds rows 32w .. 32w + 31 of the tile in its tensor-memory lanes;
+        // K splits add their partial products (the caller zeroed C; no bias, activation or Z)
+        const int gm = m0 + warp * 32 + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < nmma; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c0, v);
+            if (gm >= M) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int gn = n0 + c0 + j;
+                if (c0 + j >= nt) break;
+                if (ksplit > 1) {
+                    atomicAdd(&C[(int64_t)gm * ldc + gn], v[j]);
+                    continue;
+                }
+                float z = v[j] + (bias ? bias[gn] : 0.f);
+                if (accumulate) z += C[(int64_t)gm * ldc + gn];
+                if (Z) Z[(int64_t)gm * ldc + gn] = z;
+                C[(int64_t)gm * ldc + gn] = act ? z / (1.f + __expf(-z)) : z;
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 128);
     }
 }
 
@@ -378,9 +536,43 @@ phx_status mlp_reserve(phx_mlp* m, int64_t rows) {
     return PHX_OK;
 }
 
-cudaError_t gemm(int M, int N, int K, const float* A, int lda, int64_t sA, int tA, const float* B, int ldb,
-                 int64_t sB, int tB, float* C, int ldc, int64_t sC, const float* bias, int64_t sBias, int act, float* Z,
-                 int E, int accumulate, cudaStream_t s) {
+template <bool TA, bool TB>
+cudaError_t launch_gemm_tc(dim3 grid, int M, int N, int K, const float* A, int lda, int64_t sA, const float* B,
+                           int ldb, int64_t sB, float* C, int ldc, int64_t sC, const float* bias, int64_t sBias,
+                           int act, float* Z, int accumulate, int ksplit, const phx_ctx* ctx, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(gemm_tc_kernel<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpTcSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    gemm_tc_kernel<TA, TB><<<grid, 128, kMlpTcSmem, s>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, bias, sBias, act,
+                                                        Z, accumulate, ksplit, (int32_t*)ctx->status_word,
+                                                        ctx->opt_wait_ns);
+    return cudaGetLastError();
+}
+
+// C = op(A) op(B) (+ bias, SiLU): on the tensor cores when both the output width and K are at
+// least 16 on a Blackwell device (the hidden layers and their gradients), else FP32 SIMT tiles
+// (the input layer of n_in features, the one-column output layer).  `zeroed`: C holds zeros
+// and no bias, activation or accumulation is asked for, so K may be split over CTAs whose
+// partial products are added atomically (the weight gradients, whose K is the batch).
+cudaError_t gemm(const phx_ctx* ctx, int M, int N, int K, const float* A, int lda, int64_t sA, int tA, const float* B,
+                 int ldb, int64_t sB, int tB, float* C, int ldc, int64_t sC, const float* bias, int64_t sBias, int act,
+                 float* Z, int E, int accumulate, cudaStream_t s, bool zeroed = false) {
+    if (ctx->cc_major == 10 && N >= 16 && K >= 16 && M >= 16) {
+        const int tiles = ((N + 127) / 128) * ((M + 127) / 128) * E;
+        const int chunks = (K + kMlpTcK - 1) / kMlpTcK;
+        const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
+        int ksplit = zeroed && !bias && !act && !Z && !accumulate ? std::min(chunks, std::max(1, sms / tiles)) : 1;
+        ksplit = (chunks + ((chunks + ksplit - 1) / ksplit) - 1) / ((chunks + ksplit - 1) / ksplit);   // no empty split
+        dim3 grid(((N + 127) / 128) * ksplit, (M + 127) / 128, E);
+        if (tA && tB) return launch_gemm_tc<true, true>(grid, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, bias, sBias, act, Z, accumulate, ksplit, ctx, s);
+        if (tA) return launch_gemm_tc<true, false>(grid, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, bias, sBias, act, Z, accumulate, ksplit, ctx, s);
+        if (tB) return launch_gemm_tc<false, true>(grid, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, bias, sBias, act, Z, accumulate, ksplit, ctx, s);
+        return launch_gemm_tc<false, false>(grid, M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, bias, sBias, act, Z, accumulate, ksplit, ctx, s);
+    }
     dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, E);
     gemm_f32_kernel<<<grid, 256, 0, s>>>(M, N, K, A, lda, sA, tA, B, ldb, sB, tB, C, ldc, sC, bias, sBias, act, Z,
                                          accumulate);
@@ -404,7 +596,7 @@ static phx_status mlp_forward(phx_mlp* m, int rows, cudaStream_t s) {
         float* out = m->act + (int64_t)(l + 1) * layer;
         float* z = m->pre + (int64_t)(l + 1) * layer;
         const int ow = out_w(m, l);
-        PHX_CUDA_CHECK(m->ctx, gemm(rows, ow, in_w(m, l), in, in_w(m, l), s_in, 0, m->par + m->w_off[l], ow, m->n_par,
+        PHX_CUDA_CHECK(m->ctx, gemm(m->ctx, rows, ow, in_w(m, l), in, in_w(m, l), s_in, 0, m->par + m->w_off[l], ow, m->n_par,
                                     0, out, ow, L, m->par + m->b_off[l], m->n_par, l < m->depth ? 1 : 0, z, m->E, 0,
                                     s));
     }
@@ -417,6 +609,8 @@ static phx_status mlp_backward(phx_mlp* m, int rows, cudaStream_t s) {
     const int64_t layer = (int64_t)m->E * L;
     float* d = m->dbuf0;    // gradient w.r.t. the output of layer l (post-activation)
     float* dn = m->dbuf1;
+    // the weight gradients of the hidden layers are summed over K splits into a zeroed buffer
+    PHX_CUDA_CHECK(m->ctx, cudaMemsetAsync(m->grad, 0, sizeof(float) * m->n_par * m->E, s));
     for (int l = m->depth; l >= 0; --l) {
         const int iw = in_w(m, l), ow = out_w(m, l);
         if (l < m->depth) {
@@ -429,13 +623,13 @@ static phx_status mlp_backward(phx_mlp* m, int rows, cudaStream_t s) {
         const float* in = l == 0 ? m->xin : m->act + (int64_t)l * layer;
         const int64_t s_in = l == 0 ? 0 : L;
         // dW = in^T d : [iw x ow]
-        PHX_CUDA_CHECK(m->ctx, gemm(iw, ow, rows, in, iw, s_in, 1, d, ow, L, 0, m->grad + m->w_off[l], ow, m->n_par,
-                                    nullptr, 0, 0, nullptr, m->E, 0, s));
+        PHX_CUDA_CHECK(m->ctx, gemm(m->ctx, iw, ow, rows, in, iw, s_in, 1, d, ow, L, 0, m->grad + m->w_off[l], ow, m->n_par,
+                                    nullptr, 0, 0, nullptr, m->E, 0, s, true));
         bias_grad_kernel<<<dim3((ow + 127) / 128, m->E), 128, 0, s>>>(d, rows, ow, L, m->grad + m->b_off[l], m->n_par);
         PHX_CUDA_CHECK(m->ctx, cudaGetLastError());
         if (l > 0) {
             // d_in = d W^T : [rows x iw]
-            PHX_CUDA_CHECK(m->ctx, gemm(rows, iw, ow, d, ow, L, 0, m->par + m->w_off[l], ow, m->n_par, 1, dn, iw, L,
+            PHX_CUDA_CHECK(m->ctx, gemm(m->ctx, rows, iw, ow, d, ow, L, 0, m->par + m->w_off[l], ow, m->n_par, 1, dn, iw, L,
                                         nullptr, 0, 0, nullptr, m->E, 0, s));
             std::swap(d, dn);
         }

@@ -78,6 +78,7 @@ def new_context(phx, device, args):
     """Library context with the run's options."""
     ctx = phx.Context(device)
     ctx.set_option("pair", args.pair)
+    ctx.set_option("vel_fp32", args.vel_fp32)
     return ctx
 
 
@@ -497,6 +498,7 @@ def run_phx(args):
                        "triplets_per_step_per_gpu": trip,
                        "exchange_pairs": bool(args.pair),
                        "side_stream_sms": side,
+                       "velocity_products": "fp32" if args.vel_fp32 else "fp64",
                        "triplets_evaluated_per_step_per_gpu": trip_eval,
                        "triplet_count_note": "value counts every term (irreducible mode, q', nu', nu'') of the "
                                              "linewidth sums; with exchange pairs the kernels contract one q' "
@@ -1111,6 +1113,9 @@ def main():
     ap.add_argument("--pair", type=int, default=1, choices=[0, 1],
                     help="1: the tensor-core passes evaluate each exchange pair {q', q''} once (default); "
                          "0: every q' of the mesh")
+    ap.add_argument("--vel-fp32", type=int, default=1, choices=[0, 1],
+                    help="1: velocity products of the harmonic step with FP32 products and sums (default; the "
+                         "eigensolve, occupations and the kappa sum stay FP64); 0: FP64")
     ap.add_argument("--irr-limit", type=int, default=0,
                     help="profiling aid: process only the first N irreducible q per step (0: all)")
     args = ap.parse_args()

@@ -113,9 +113,13 @@ const char* phx_version(void);
  *     orderings (|V3|^2 is the same for both: Eq. (phi3_proj) is symmetric in the modes), so
  *     about half of the q' are contracted; 0 = every q' of the mesh.  Results agree to
  *     rounding.  The FP64 path always sums every q'.
- *   PHX_OPT_SIDE_SMS: with the chained kernel, the fold and Fourier stages (S3, S4) of the next
- *     q' tile run on a second stream over this many SMs while the chained kernel runs on the
- *     others (M double-buffered); -1 (default) = the library's choice, 0 = one stream; at most 76.
+ *   PHX_OPT_SIDE_SMS: the fold and Fourier stages (S3, S4) of the next q' tile run on a second
+ *     stream over this many SMs while the eigenvector contractions of the current tile (the
+ *     chained kernel or the two GEMMs) run on the others (M double-buffered); -1 (default) =
+ *     the library's choice, 0 = one stream; at most 76.
+ *   PHX_OPT_VEL_FP32: 1 = phx_harmonic forms the velocity products dD/dq E (Eq. (groupvel))
+ *     with FP32 products and sums (FP64 inputs and outputs: relative error ~1e-7, far below
+ *     the 1e-5 bar on kappa); 0 (default) = FP64.  The eigensolve stays FP64 either way.
  *   PHX_OPT_WAIT_LIMIT_NS: bound of every device barrier wait of the tensor-core kernels
  *     (default 2e9 ns); a wait that runs out makes the kernel retire and the call return
  *     PHX_ERR_TIMEOUT (host-memory calls; device-memory calls leave the status to the next
@@ -128,10 +132,11 @@ typedef enum {
     PHX_OPT_WAIT_LIMIT_NS = 1,
     PHX_OPT_STARVE = 2,
     PHX_OPT_PAIR = 3,
-    PHX_OPT_SIDE_SMS = 4
+    PHX_OPT_SIDE_SMS = 4,
+    PHX_OPT_VEL_FP32 = 5
 } phx_option;
 phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value);
-/* The value an option has in effect: for PHX_OPT_SIDE_SMS the SM count the chained path
+/* The value an option has in effect: for PHX_OPT_SIDE_SMS the SM count the tensor-core path
  * uses (the default resolved), for the others the value set.  Errors: PHX_ERR_INVALID for an
  * unknown option or a null `value`. */
 phx_status phx_get_option(phx_ctx* ctx, int32_t option, int64_t* value);

@@ -137,7 +137,7 @@ KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4
            "eigensolver": 6, "cell_sparse": 7, "cell_transpose": 8, "cell_gemm": 9, "eig_tridiag": 10,
            "eig_vectors": 11, "eig_back": 12, "eig_bisect": 13, "sc_step": 14, "chain": 15}
 
-OPTIONS = {"chain": 0, "wait_limit_ns": 1, "starve": 2, "pair": 3, "side_sms": 4}
+OPTIONS = {"chain": 0, "wait_limit_ns": 1, "starve": 2, "pair": 3, "side_sms": 4, "vel_fp32": 5}
 
 EXPORTED = ["phx_set_option", "phx_get_option", "phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
             "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_isotope", "phx_kappa_qhgk", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta", "phx_kappa_sc",
@@ -280,12 +280,13 @@ class Context:
     def set_option(self, name, value):
         """Context option: 'chain' (0 auto, 1 chained kernel wherever it fits, 2 never),
         'pair' (1: one evaluation per exchange pair {q', q''}, 0: every q'),
-        'side_sms' (SMs of the fold/Fourier side stream next to the chained kernel; -1 default, 0 off),
+        'side_sms' (SMs of the fold/Fourier side stream next to the contractions; -1 default, 0 off),
+        'vel_fp32' (1: velocity products of harmonic() with FP32 products and sums),
         'wait_limit_ns' (bound of every device barrier wait), 'starve' (test hook)."""
         self._check(lib.phx_set_option(self.h, OPTIONS[name], int(value)))
 
     def get_option(self, name):
-        """The option's value in effect ('side_sms': the SM count the chained path uses)."""
+        """The option's value in effect ('side_sms': the SM count the tensor-core path gives its side stream)."""
         v = C.c_int64(0)
         self._check(lib.phx_get_option(self.h, OPTIONS[name], C.addressof(v)))
         return int(v.value)

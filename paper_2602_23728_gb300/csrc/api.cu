@@ -207,6 +207,10 @@ phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value) {
             if (value < -1 || value > 76) return phx_set_error(ctx, PHX_ERR_INVALID, "PHX_OPT_SIDE_SMS %lld", (long long)value);
             ctx->opt_side_sms = (int)value;
             return PHX_OK;
+        case PHX_OPT_VEL_FP32:
+            if (value < 0 || value > 1) return phx_set_error(ctx, PHX_ERR_INVALID, "PHX_OPT_VEL_FP32 %lld", (long long)value);
+            ctx->opt_vel_fp32 = (int)value;
+            return PHX_OK;
         case PHX_OPT_PAIR:
             if (value < 0 || value > 1) return phx_set_error(ctx, PHX_ERR_INVALID, "PHX_OPT_PAIR %lld", (long long)value);
             ctx->opt_pair = (int)value;
@@ -225,6 +229,7 @@ phx_status phx_get_option(phx_ctx* ctx, int32_t option, int64_t* value) {
         case PHX_OPT_STARVE: *value = ctx->opt_starve; return PHX_OK;
         case PHX_OPT_PAIR: *value = ctx->opt_pair; return PHX_OK;
         case PHX_OPT_SIDE_SMS: *value = phx_side_sms(ctx); return PHX_OK;
+        case PHX_OPT_VEL_FP32: *value = ctx->opt_vel_fp32; return PHX_OK;
         default: return phx_set_error(ctx, PHX_ERR_INVALID, "unknown option %d", option);
     }
 }
@@ -444,6 +449,7 @@ phx_status phx_harmonic(phx_ctx* ctx, const phx_cell* cell, const phx_ifc2* fc2,
             p.B = o_e + (int64_t)q0 * n2 * 2; p.strideB = n2; p.divB = 3;
             p.C = Y; p.strideC = n2;
             p.lda = n; p.ldb = n; p.ldc = n;
+            p.fp32 = ctx->opt_vel_fp32;
             PHX_CUDA_CHECK(ctx, phx_launch_zgemm(n, n, n, 3 * c, p, s));
             PHX_CUDA_CHECK(ctx, phx_launch_velocity(o_e + (int64_t)q0 * n2 * 2, Y, o_f + (int64_t)q0 * n, n, c,
                                                     o_v ? o_v + (int64_t)q0 * n * 3 : nullptr,

@@ -46,7 +46,7 @@ struct phx_ctx {
     // batched path: capture stream, cached graph of the last job list, q'-tile autotune table
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    // chained linewidth path: side stream of the fold and Fourier GEMM, with its fork, join and
+    // tensor-core linewidth path: side stream of the fold and Fourier GEMM, with its fork, join and
     // buffer events (created outside any capture)
     cudaStream_t side_stream = nullptr;
     cudaEvent_t side_ev[8] = {};
@@ -58,11 +58,12 @@ struct phx_ctx {
     int opt_chain = 0;                            // 0 auto, 1 force the chained kernel, 2 never
     int opt_pair = 1;                             // evaluate each exchange pair {q', q''} once
     int opt_side_sms = -1;                        // SMs of the side stream (-1: default, 0: one stream)
+    int opt_vel_fp32 = 0;                         // velocity products of phx_harmonic in FP32
     unsigned long long opt_wait_ns = 2000000000ull;   // bound of every device barrier wait
     int opt_starve = 0;                           // test hook: tensor-core producers issue nothing
 };
 
-// SMs the chained linewidth path gives to its side stream (gamma_tc.cu)
+// SMs the tensor-core linewidth path gives to its side stream (gamma_tc.cu)
 int phx_side_sms(const phx_ctx* ctx);
 
 // Profiling helpers: begin returns a record slot (or -1 when profiling is off).
@@ -185,6 +186,7 @@ struct ZgemmBatch {
     int64_t strideB_inner;               // added per (b % divB) when idxB given
     int lda, ldb, ldc;
     int transA;                          // 1: A stored [K][M] (plain transpose, no conjugate)
+    int fp32;                            // 1: products and sums in FP32 (FP64 inputs and output)
 };
 cudaError_t phx_launch_zgemm(int M, int N, int K, int batch, const ZgemmBatch& p, cudaStream_t s);
 

@@ -1392,8 +1392,8 @@ phx_status tc_prepare_fc3(phx_ctx* ctx, phx_fc3* f) {
 }
 
 struct TcBuffers {
-    Operand W, M, X, E, P, T;
-    size_t x_bytes = 0;         // bytes of each X plane (X, or the chained kernel's second M buffer)
+    Operand W, M, M2, X, E, P, T;
+    size_t m2_bytes = 0;        // bytes of each plane of M's second buffer (side stream), 0 without
     int32_t* qp = nullptr;      // q' list of the current irreducible q (pair_list_kernel)
     int32_t* qpp = nullptr;     // and their q''
     float2* wph = nullptr;
@@ -1402,7 +1402,7 @@ struct TcBuffers {
 
 // Workspace large enough for the given byte counts (per plane) and element counts.
 phx_status tc_alloc(phx_ctx* ctx, int prec, size_t bw, size_t bm, size_t bx, size_t be, size_t bp, size_t bt,
-                    int64_t max_nq, int64_t max_nnz, int64_t max_n2, TcBuffers* b) {
+                    int64_t max_nq, int64_t max_nnz, int64_t max_n2, TcBuffers* b, size_t bm2 = 0) {
     const int planes = prec == P_BF16X3 ? 2 : 1;
     auto get = [&](const char* name, size_t bytes, Operand* o) -> bool {
         std::string nh = std::string(name) + ".hi", nl = std::string(name) + ".lo";
@@ -1410,9 +1410,9 @@ phx_status tc_alloc(phx_ctx* ctx, int prec, size_t bw, size_t bm, size_t bx, siz
         o->lo = planes == 2 ? phx_ws(ctx, nl.c_str(), bytes) : nullptr;
         return o->hi && (planes == 1 || o->lo);
     };
-    b->x_bytes = bx;
+    b->m2_bytes = bm2;
     if (!get("tc.W", bw, &b->W) || !get("tc.M", bm, &b->M) || !get("tc.X", bx, &b->X) || !get("tc.E", be, &b->E) ||
-        !get("tc.P", bp, &b->P) || !get("tc.T", bt, &b->T))
+        !get("tc.P", bp, &b->P) || !get("tc.T", bt, &b->T) || (bm2 > 0 && !get("tc.M2", bm2, &b->M2)))
         return PHX_ERR_NOMEM;
     b->qp = (int32_t*)phx_ws(ctx, "tc.qp", (size_t)max_nq * 8);      // two lists (by q parity)
     b->qpp = (int32_t*)phx_ws(ctx, "tc.qpp", (size_t)max_nq * 8);
@@ -1422,7 +1422,7 @@ phx_status tc_alloc(phx_ctx* ctx, int prec, size_t bw, size_t bm, size_t bx, siz
     return PHX_OK;
 }
 
-// Side stream and events of the chained path (created once per context, outside any capture).
+// Side stream and events of the tensor-core path (created once per context, outside any capture).
 phx_status ensure_side(phx_ctx* ctx) {
     if (ctx->side_stream) return PHX_OK;
     PHX_CUDA_CHECK(ctx, cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking));
@@ -1461,8 +1461,8 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
     // padding columns of M, X and W must read as zero for this job's layout
     for (int pl = 0; pl < planes; ++pl) {
         PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.M.lo : B.M.hi, 0, P.bytes_m, s));
-        if (B.x_bytes >= P.bytes_m)   // X, or the chained kernel's second M buffer
-            PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.X.lo : B.X.hi, 0, P.bytes_m, s));
+        if (!P.chain) PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.X.lo : B.X.hi, 0, P.bytes_m, s));
+        if (B.m2_bytes >= P.bytes_m) PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.M2.lo : B.M2.hi, 0, P.bytes_m, s));
         PHX_CUDA_CHECK(ctx, cudaMemsetAsync(pl ? B.W.lo : B.W.hi, 0, P.bytes_w, s));
     }
     if (P.chain)
@@ -1475,7 +1475,7 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
 
     TcArgs aD{}, aA{}, aB{};
     ChainArgs aC{};
-    CUtensorMap m_map2[2];          // chained kernel: M maps of the second buffer
+    CUtensorMap m_map2[2];          // M maps of the second buffer (chained kernel / EPI_X operand A)
     const int64_t m_rows = (int64_t)Q * P.rows_a;
     for (int pl = 0; pl < planes; ++pl) {
         const void* w = pl ? B.W.lo : B.W.hi;
@@ -1488,12 +1488,13 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
             ok = ok && make_map(&aC.ta_map[pl], t, PREC, (int64_t)nq * n, kr, P.c_ra) &&
                  make_map(&aC.tb_map[pl], t, PREC, (int64_t)nq * n, kr, P.c_rb3) &&
                  make_map(&aC.m_map[pl], m, PREC, m_rows, kr, kcp);
-            if (B.x_bytes >= P.bytes_m) ok = ok && make_map(&m_map2[pl], pl ? B.X.lo : B.X.hi, PREC, m_rows, kr, kcp);
+            if (B.m2_bytes >= P.bytes_m) ok = ok && make_map(&m_map2[pl], pl ? B.M2.lo : B.M2.hi, PREC, m_rows, kr, kcp);
         } else {
             const void* x = pl ? B.X.lo : B.X.hi;
             const void* e = pl ? B.E.lo : B.E.hi;
             ok = ok && make_map(&aA.a_map[pl], m, PREC, m_rows, kr, kBoxRows) &&
                  make_map(&aA.b_map[pl], e, PREC, (int64_t)nq * 2 * np, kr, mg) &&
+                 (B.m2_bytes < P.bytes_m || make_map(&m_map2[pl], pl ? B.M2.lo : B.M2.hi, PREC, m_rows, kr, kBoxRows)) &&
                  make_map(&aB.a_map[pl], x, PREC, m_rows, kr, kBoxRows) &&
                  make_map(&aB.b_map[pl], e, PREC, (int64_t)nq * 2 * np, kr, mg);
         }
@@ -1541,12 +1542,12 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
         aB.g1_rows = (int64_t)n_irr * n;
     }
 
-    // Chained path with a side stream: the per-q lists, the fold and the Fourier GEMM run on s2
-    // over `side` SMs, the chained kernel on s over the others.  M alternates between two
-    // buffers by tile (the second is the X workspace, which the chained kernel does not use) and
-    // the q' lists between two by q; events order every producer before its consumer and every
-    // consumer before the producer that overwrites its buffer.
-    const int side = (P.chain && ctx->side_stream && B.x_bytes >= P.bytes_m) ? side_sms(ctx, sms) : 0;
+    // With a side stream: the per-q lists, the fold and the Fourier GEMM run on s2 over `side`
+    // SMs, the contractions (chained kernel, or the e_q'' and e_q' GEMMs) on s over the others.
+    // M alternates between two buffers by tile and the q' lists between two by q; events order
+    // every producer before its consumer and every consumer before the producer that
+    // overwrites its buffer.
+    const int side = (ctx->side_stream && B.m2_bytes >= P.bytes_m) ? side_sms(ctx, sms) : 0;
     cudaStream_t s2 = side > 0 ? ctx->side_stream : s;
     cudaEvent_t* ev = ctx->side_ev;       // [0] fork, [1] join, [2..3] M ready, [4..5] M free, [6..7] lists free
     const int main_ctas = sms - side, side_ctas = side > 0 ? side : sms;
@@ -1616,8 +1617,8 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
                 const int mb = side > 0 ? (int)(g & 1) : 0;
                 aD.b_base = tq;
                 aD.nq_slots = Qt;
-                aD.out_hi = mb ? B.X.hi : B.M.hi;
-                aD.out_lo = mb ? B.X.lo : B.M.lo;
+                aD.out_hi = mb ? B.M2.hi : B.M.hi;
+                aD.out_lo = mb ? B.M2.lo : B.M.lo;
                 // algorithmic work: complex MACs x 8 flops; bytes: operands read + results written once
                 const double fl_d = 8.0 * (double)rw * Qt * f->n_d;
                 const double fl_e = 8.0 * (double)Qt * ra * n * n;
@@ -1626,11 +1627,11 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
                 int pp = phx_prof_begin(ctx, s2);
                 PHX_CUDA_CHECK(ctx, (launch_gemm<PREC, EPI_M, false>(ctx, aD, 1, side_ctas, s2)));
                 phx_prof_end(ctx, pp, s2, PHX_K_DFT, fl_d, op_bytes * ((double)rw * f->n_d + (double)Qt * ra * n));
+                if (side > 0) {
+                    PHX_CUDA_CHECK(ctx, cudaEventRecord(ev[2 + mb], s2));
+                    PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(s, ev[2 + mb], 0));
+                }
                 if (P.chain) {
-                    if (side > 0) {
-                        PHX_CUDA_CHECK(ctx, cudaEventRecord(ev[2 + mb], s2));
-                        PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(s, ev[2 + mb], 0));
-                    }
                     aC.n_items = Qt * nnu; aC.nnu = nnu; aC.rows_per_slot = (int)ra;
                     aC.qp = qp_l + t0; aC.qpp = qpp_l + t0; aC.pair = pair ? 1 : 0; aC.nu0 = nu0;
                     aC.g1_row0 = (int64_t)si * n + nu0;
@@ -1645,19 +1646,22 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
                     continue;
                 }
                 aA.b_idx = qpp_l + t0;
+                TcArgs aa = aA;
+                if (mb) { aa.a_map[0] = m_map2[0]; aa.a_map[1] = m_map2[1]; }
                 pp = phx_prof_begin(ctx, s);
-                PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_X>(ctx, aA, P.stream_b, Qt, sms, s)));
+                PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_X>(ctx, aa, P.stream_b, Qt, main_ctas, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_GEMM_E2, fl_e, op_bytes * 2.0 * Qt * ra * n);
+                if (side > 0) PHX_CUDA_CHECK(ctx, cudaEventRecord(ev[4 + mb], s));   // M[mb] read
                 aB.b_idx = qp_l + t0;
                 aB.qp1 = qp_l + t0;
                 aB.pair = pair ? 1 : 0;
                 pp = phx_prof_begin(ctx, s);
                 if (n_t > 0)
-                    PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_GT>(ctx, aB, P.stream_b, Qt, sms, s)));
+                    PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_GT>(ctx, aB, P.stream_b, Qt, main_ctas, s)));
                 else if (g1)
-                    PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_GS>(ctx, aB, P.stream_b, Qt, sms, s)));
+                    PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_GS>(ctx, aB, P.stream_b, Qt, main_ctas, s)));
                 else
-                    PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_G>(ctx, aB, P.stream_b, Qt, sms, s)));
+                    PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_G>(ctx, aB, P.stream_b, Qt, main_ctas, s)));
                 phx_prof_end(ctx, pp, s, PHX_K_GEMM_E1, fl_e, op_bytes * (double)Qt * ra * n);
                 ctx->launches += 3;
             }
@@ -1680,10 +1684,10 @@ phx_status run_tc(phx_ctx* ctx, const phx_fc3* f, const double* freq, const doub
     PHX_TRY(tc_plan(ctx, f, PREC, 0, &P));
     PHX_TRY(tc_prepare_fc3(ctx, const_cast<phx_fc3*>(f)));
     TcBuffers B;
-    const bool two_m = P.chain && side_sms(ctx, ctx->sm_count > 0 ? ctx->sm_count : 148) > 0;
+    const bool two_m = side_sms(ctx, ctx->sm_count > 0 ? ctx->sm_count : 148) > 0;
     if (two_m) PHX_TRY(ensure_side(ctx));
-    PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, (!P.chain || two_m) ? P.bytes_m : 0, P.bytes_e, P.bytes_p,
-                     P.bytes_t, P.nq, f->nnz, (int64_t)P.n * P.n, &B));
+    PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.chain ? 0 : P.bytes_m, P.bytes_e, P.bytes_p, P.bytes_t, P.nq,
+                     f->nnz, (int64_t)P.n * P.n, &B, two_m ? P.bytes_m : 0));
     return tc_enqueue<PREC>(ctx, P, f, B, freq, evec, nB, irr_host, n_irr, gp, gacc, wacc, s, n_t, nb_stride,
                             t_stride, g1);
 }
@@ -1744,10 +1748,10 @@ phx_status autotune_q(phx_ctx* ctx, const phx_job& job, cudaStream_t s, int* bes
             if (P.Q == last_q) continue;                 // clamped to the mesh size already tried
             last_q = P.Q;
             TcBuffers B;
-            const bool two_m = P.chain && side_sms(ctx, ctx->sm_count > 0 ? ctx->sm_count : 148) > 0;
+            const bool two_m = side_sms(ctx, ctx->sm_count > 0 ? ctx->sm_count : 148) > 0;
             if (two_m) PHX_TRY(ensure_side(ctx));
-            PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, (!P.chain || two_m) ? P.bytes_m : 0, P.bytes_e, P.bytes_p,
-                             P.bytes_t, P.nq, f->nnz, (int64_t)P.n * P.n, &B));
+            PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.chain ? 0 : P.bytes_m, P.bytes_e, P.bytes_p, P.bytes_t,
+                             P.nq, f->nnz, (int64_t)P.n * P.n, &B, two_m ? P.bytes_m : 0));
             float best_rep = 1e30f;
             for (int rep = 0; rep < 2; ++rep) {
                 float ms = 0.f;
@@ -1810,14 +1814,14 @@ phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, const phx_
         const TcPlan& P = plans[j];
         bw = std::max(bw, P.bytes_w); bm = std::max(bm, P.bytes_m); be = std::max(be, P.bytes_e);
         bp = std::max(bp, P.bytes_p); bt = std::max(bt, P.bytes_t);
-        if (!P.chain || side > 0) bx = std::max(bx, P.bytes_m);
+        if (!P.chain) bx = std::max(bx, P.bytes_m);
         mnq = std::max<int64_t>(mnq, P.nq); mnnz = std::max<int64_t>(mnnz, jobs[j].fc3->nnz);
         mn2 = std::max<int64_t>(mn2, (int64_t)P.n * P.n);
         mnb = std::max<int64_t>(mnb, (int64_t)P.nq * P.n);
         mg = std::max<int64_t>(mg, (int64_t)jobs[j].n_irr * P.n);
     }
     TcBuffers B;
-    PHX_TRY(tc_alloc(ctx, PREC, bw, bm, bx, be, bp, bt, mnq, mnnz, mn2, &B));
+    PHX_TRY(tc_alloc(ctx, PREC, bw, bm, bx, be, bp, bt, mnq, mnnz, mn2, &B, side > 0 ? bm : 0));
     double* nB = (double*)phx_ws(ctx, "b.nB", (size_t)mnb * 8);
     double* gacc = (double*)phx_ws(ctx, "b.gacc", (size_t)mg * 8);
     double* acc9 = (double*)phx_ws(ctx, "b.acc9", (size_t)n_jobs * 9 * 8);

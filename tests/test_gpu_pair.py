@@ -133,13 +133,14 @@ def test_pair_option_range(ctx, phx):
         ctx.set_option("pair", 2)
 
 
+@pytest.mark.parametrize("chain", [1, 2])
 @pytest.mark.parametrize("kind", ["fcc32-222", "cell72-333"])
-def test_side_stream_equals_one_stream(ctx, phx, kind):
-    """The fold and Fourier GEMM on a side stream next to the chained kernel (two M buffers,
-    event-ordered) give the one-stream result; only the CTA split of the items and so the
-    order of the FP64 accumulation changes."""
+def test_side_stream_equals_one_stream(ctx, phx, kind, chain):
+    """The fold and Fourier GEMM on a side stream next to the contractions (the chained kernel
+    or the two GEMMs; two M buffers, event-ordered) give the one-stream result; only the CTA
+    split of the items and so the order of the FP64 accumulation changes."""
     s = _setup(ctx, phx, kind)
-    ctx.set_option("chain", 1)
+    ctx.set_option("chain", chain)
     out = {}
     for side in (0, -1, 16):
         ctx.set_option("side_sms", side)
@@ -153,5 +154,5 @@ def test_side_stream_equals_one_stream(ctx, phx, kind):
                               precision="bf16x3")
     for side in (-1, 16):
         d = _rel(out[side], out[0])
-        print(f"{kind}: side {side} vs one stream {d:.2e}")
+        print(f"{kind} chain={chain}: side {side} vs one stream {d:.2e}")
         assert d < 1e-12

@@ -100,6 +100,28 @@ def test_harmonic_ragged_two_atom(ctx):
     _check_harmonic(w, f2, q, freq, evec, vel, vv)
 
 
+def test_velocity_products_fp32_option(ctx):
+    """PHX_OPT_VEL_FP32: dD/dq E with FP32 products and sums, FP64 in and out.  Frequencies and
+    eigenvectors are unchanged (the eigensolve stays FP64); velocities and the basis-invariant
+    velocity products stay within 1e-6 of the FP64 run (relative to their largest entry)."""
+    w = P.fcc_massdisorder_32()
+    f2 = w.ifc2()
+    c = w.crystal
+    q = O.grid.mesh_qred(w.mesh)[np.r_[0:3, 100:103, 257, 511]]
+    ref = ctx.harmonic(c.lattice, c.masses, f2.idx, f2.val.reshape(-1, 9), q)
+    ctx.set_option("vel_fp32", 1)
+    try:
+        assert ctx.get_option("vel_fp32") == 1
+        got = ctx.harmonic(c.lattice, c.masses, f2.idx, f2.val.reshape(-1, 9), q)
+    finally:
+        ctx.set_option("vel_fp32", 0)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    for a, b in ((got[2], ref[2]), (got[3], ref[3])):
+        d = np.abs(a - b).max() / np.abs(b).max()
+        print(f"FP32 velocity products: max rel diff {d:.2e}")
+        assert 0 < np.abs(b).max() and d < 1e-6
+
+
 # ----------------------------------------------------------------------------- linewidths, FP64
 
 def test_gamma_fp64_fcc1_all_irreducible(ctx, phx, fcc1):

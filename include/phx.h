@@ -116,7 +116,8 @@ const char* phx_version(void);
  *   PHX_OPT_SIDE_SMS: the fold and Fourier stages (S3, S4) of the next q' tile run on a second
  *     stream over this many SMs while the eigenvector contractions of the current tile (the
  *     chained kernel or the two GEMMs) run on the others (M double-buffered); -1 (default) =
- *     the library's choice, 0 = one stream; at most 76.
+ *     the library's choice (48 of 152 SMs for linewidths, 34 with the scattering rows, 32 for
+ *     several temperatures), 0 = one stream; at most 76.
  *   PHX_OPT_VEL_FP32: 1 = phx_harmonic forms the velocity products dD/dq E (Eq. (groupvel))
  *     with FP32 products and sums (FP64 inputs and outputs: relative error ~1e-7, far below
  *     the 1e-5 bar on kappa); 0 (default) = FP64.  The eigensolve stays FP64 either way.

@@ -1434,11 +1434,19 @@ phx_status ensure_side(phx_ctx* ctx) {
 // fcc32 8^3: 24 / 32 / 40 / 48 side SMs give 713 / 556 / 464 / 412 ms per step against 441 ms
 // on one stream; the fold and Fourier GEMM of a tile then take about as long on 48 SMs as
 // the chained kernel on the other 104).
-int side_sms(const phx_ctx* ctx, int sms) {
+// The scattering-row (Gamma1) and multi-temperature epilogues make the contractions longer
+// for the same side-stream work, so their default share is smaller (`mode`: CHAIN_G, CHAIN_GT,
+// CHAIN_GS; the environment variable PHX_SIDE_SMS_GT / PHX_SIDE_SMS_GS overrides those).
+// Measured at fcc32 8^3: the Gamma1 pass 610 / 524 / 533 / 561 ms per step at 28 / 34 / 40 /
+// 48 side SMs; four temperatures in one pass 519 / 530 / 570 ms at 32 / 40 / 48.
+int side_sms(const phx_ctx* ctx, int sms, int mode = 0) {
     int v = ctx->opt_side_sms;
     if (v < 0) {
-        v = 48 * sms / 152;
-        if (const char* env = getenv("PHX_SIDE_SMS")) v = atoi(env);
+        const int base = mode == 2 ? 34 : mode == 1 ? 32 : 48;
+        v = base * sms / 152;
+        const char* env = getenv(mode == 2 ? "PHX_SIDE_SMS_GS" : mode == 1 ? "PHX_SIDE_SMS_GT" : "PHX_SIDE_SMS");
+        if (!env) env = getenv("PHX_SIDE_SMS");
+        if (env) v = atoi(env);
     }
     return std::max(0, std::min(v, sms / 2));
 }
@@ -1547,7 +1555,8 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
     // M alternates between two buffers by tile and the q' lists between two by q; events order
     // every producer before its consumer and every consumer before the producer that
     // overwrites its buffer.
-    const int side = (ctx->side_stream && B.m2_bytes >= P.bytes_m) ? side_sms(ctx, sms) : 0;
+    const int side = (ctx->side_stream && B.m2_bytes >= P.bytes_m)
+                         ? side_sms(ctx, sms, n_t > 0 ? CHAIN_GT : (g1 ? CHAIN_GS : CHAIN_G)) : 0;
     cudaStream_t s2 = side > 0 ? ctx->side_stream : s;
     cudaEvent_t* ev = ctx->side_ev;       // [0] fork, [1] join, [2..3] M ready, [4..5] M free, [6..7] lists free
     const int main_ctas = sms - side, side_ctas = side > 0 ? side : sms;

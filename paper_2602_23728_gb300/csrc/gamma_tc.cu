@@ -1128,21 +1128,6 @@ struct Operand {
     int kr = 0;
 };
 
-phx_status alloc_operand(phx_ctx* ctx, const char* name, int prec, int64_t rows, int kr, Operand* o) {
-    const int esz = prec == P_BF16X3 ? 2 : 4;
-    const size_t bytes = (size_t)rows * kr * esz;
-    std::string nh = std::string(name) + ".hi", nl = std::string(name) + ".lo";
-    o->hi = phx_ws(ctx, nh.c_str(), bytes);
-    if (!o->hi) return PHX_ERR_NOMEM;
-    if (prec == P_BF16X3) {
-        o->lo = phx_ws(ctx, nl.c_str(), bytes);
-        if (!o->lo) return PHX_ERR_NOMEM;
-    }
-    o->rows = rows;
-    o->kr = kr;
-    return PHX_OK;
-}
-
 size_t smem_bytes(int prec, bool stream_b, int nk, int mg, int stages) {
     const int planes = prec == P_BF16X3 ? 2 : 1;
     const size_t b_bytes = stream_b ? 0 : (size_t)planes * nk * 2 * mg * kChunkBytes;

@@ -413,18 +413,31 @@ ql_back_kernel(const double2* __restrict__ Rg, const double* __restrict__ scratc
                 const double den = dl + copysign(hypot(dl, b), dl);
                 const double mu = d[hi] - (den != 0.0 ? b * (b / den) : b);
                 double x = d[lo] - mu, z = e[lo];
+                // d[k] and e[k] of the rotation in flight are carried in registers (each rotation
+                // rewrites them for the next), so the serial chain touches shared memory only
+                // for the incoming d[k+1], e[k+1] and the outgoing values
+                double a = d[lo], bb = e[lo];
                 for (int k = lo; k < hi; ++k) {
-                    const double r = hypot(x, z);
-                    const double c = r > 0.0 ? x / r : 1.0, sn = r > 0.0 ? z / r : 0.0;
+                    // Givens rotation from one reciprocal square root (the entries are far from
+                    // the FP64 overflow and underflow limits, so |(x, z)|^2 is formed directly;
+                    // GB300's FP64 pipe is narrow and this chain is the kernel's serial path)
+                    const double r2 = fma(x, x, z * z);
+                    const double ir = r2 > 0.0 ? rsqrt(r2) : 0.0;
+                    const double r = r2 * ir;
+                    const double c = r2 > 0.0 ? x * ir : 1.0, sn = r2 > 0.0 ? z * ir : 0.0;
                     if (k > lo) e[k - 1] = r;                    // the bulge at (k+1, k-1) folds into e[k-1]
-                    const double a = d[k], bb = e[k], dd = d[k + 1];
+                    const double dd = d[k + 1], en = k + 1 < hi ? e[k + 1] : 0.0;
                     d[k] = c * c * a + 2.0 * c * sn * bb + sn * sn * dd;
-                    d[k + 1] = sn * sn * a - 2.0 * c * sn * bb + c * c * dd;
-                    e[k] = c * sn * (dd - a) + (c * c - sn * sn) * bb;
+                    const double dk1 = sn * sn * a - 2.0 * c * sn * bb + c * c * dd;
+                    const double ek = c * sn * (dd - a) + (c * c - sn * sn) * bb;
+                    d[k + 1] = dk1;
+                    e[k] = ek;
                     if (k + 1 < hi) {                            // new bulge at (k+2, k)
-                        x = e[k];
-                        z = sn * e[k + 1];
-                        e[k + 1] *= c;
+                        x = ek;
+                        z = sn * en;
+                        e[k + 1] = en * c;
+                        a = dk1;
+                        bb = en * c;
                     }
                     rc[k] = c;
                     rs[k] = sn;
@@ -438,13 +451,23 @@ ql_back_kernel(const double2* __restrict__ Rg, const double* __restrict__ scratc
         if (hi <= lo) break;
         // Z <- Z Q_lo^T ... Q_{hi-1}^T on columns (k, k+1): column k is final after rotation k,
         // column k+1 is carried to the next rotation in a register
+        // (the columns a block of 8 rotations reads are loaded together, so their latencies
+        // overlap instead of following each store)
         for (int row = tid; row < n; row += nt) {
             double carry = Z[(int64_t)lo * n + row];
-            for (int k = lo; k < hi; ++k) {
-                const double c = rc[k], sn = rs[k];
-                const double zk1 = Z[(int64_t)(k + 1) * n + row];
-                Z[(int64_t)k * n + row] = c * carry + sn * zk1;
-                carry = c * zk1 - sn * carry;
+            for (int k0 = lo; k0 < hi; k0 += 8) {
+                const int kb = min(8, hi - k0);
+                double zc[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) zc[u] = u < kb ? Z[(int64_t)(k0 + u + 1) * n + row] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (u >= kb) break;
+                    const int k = k0 + u;
+                    const double c = rc[k], sn = rs[k];
+                    Z[(int64_t)k * n + row] = c * carry + sn * zc[u];
+                    carry = c * zc[u] - sn * carry;
+                }
             }
             Z[(int64_t)hi * n + row] = carry;
         }

@@ -638,7 +638,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     t0 = time.perf_counter()
-    ctx.gamma_batched(jobs, precision=args.precision)            # autotune + capture + first run
+    tuned = ctx.gamma_batched(jobs, precision=args.precision)    # autotune + capture + first run
     torch.cuda.synchronize()
     t_first = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
@@ -705,7 +705,8 @@ def run_batched(args):
             "sequential_single_job_calls": {"value": trip / (ms_seq / 1e3), "ms": ms_seq,
                                             "kernel_ms": seq_kernel_ms, "per_job_ms": per_job_ms,
                                             "note": "timed with per-launch events on"},
-            "first_call_s_incl_autotune_and_capture": t_first, "setup_s": t_setup}
+            "first_call_s_incl_autotune_and_capture": t_first, "setup_s": t_setup,
+            "autotuned_q_tile_chain_side_sms": tuned}
     if fp64:
         line["fp64_path"] = fp64
         line["speedup_vs_fp64_path"] = line["value"] / fp64["value"]
@@ -719,9 +720,11 @@ def run_batched(args):
 
 def run_surrogate(args):
     """4-atom fcc cell, 24^3 mesh at 40 K: exact linewidths on the 8^3 subgrid train the MLP
-    ensemble, which fills the dense mesh (5 % of q-points fall back to the exact kernel).  The
-    value is the dense mesh's exact-equivalent triplets divided by the surrogate pipeline's
-    time; the exact dense run and the coarse-mesh conductivity are reported beside it."""
+    ensemble, which fills the dense mesh (q-points outside the network's domain and 5 % more by
+    ensemble spread fall back to the exact kernel).  The value is the dense mesh's
+    exact-equivalent triplets divided by the surrogate pipeline's time (the run of median time
+    among independent trainings); the exact dense run and the coarse-mesh conductivity are
+    reported beside it."""
     import torch
     import paper_2602_23728_gb300 as phx
     import phx_inputs as P
@@ -732,14 +735,22 @@ def run_surrogate(args):
     c = w.crystal
     f2, f3 = w.ifc2(), w.ifc3()
     runs = []
-    for k in range(max(args.steps, 1) + 1):          # the first run warms up
+    # every timed run is an independent training (seeds 1, 2, ...): one training is one draw of
+    # the seeded splits and initial weights, so times and errors are reported as medians
+    for k in range(max(args.steps, 1) + 1):          # the first run (seed 0) warms up
         r = surrogate.run(ctx, phx, c.lattice, c.masses, f2.idx, f2.val, f3.idx, f3.val, w.mesh, 3, w.rotations,
-                          w.temperature, precision=args.precision, seed=1)
+                          w.temperature, precision=args.precision, seed=k)
         if k > 0:
             runs.append(r)
-    r = runs[-1]
+
+    def t_pipeline(r):
+        t = r["timings"]
+        return t["exact_subgrid"] + t["features"] + t["train"] + t["infer"] + t["fallback"]
+    order = np.argsort([t_pipeline(x) for x in runs])
+    r = runs[order[len(order) // 2]]                 # the run of median pipeline time
     t = r["timings"]
-    t_sur = t["exact_subgrid"] + t["features"] + t["train"] + t["infer"] + t["fallback"]
+    t_sur = t_pipeline(r)
+    errs = [x["kappa_rel_err_surrogate"] for x in runs]
     line = {"metric": METRIC, "value": r["triplets_exact"] / t_sur, "unit": UNIT, "n_gpus": 1, "steps": len(runs),
             "warmup": 1, "ms_per_step": 1e3 * t_sur, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
@@ -747,10 +758,11 @@ def run_surrogate(args):
                                    "MLP 4-128-128-128-1 x4 trained on the 8^3 subgrid (35 irreducible q)",
                        "exact_equivalent_triplets": r["triplets_exact"]},
             "exact_dense_path": {"value": r["triplets_exact"] / t["exact_full"], "s": t["exact_full"]},
-            "kappa_rel_err": {"surrogate": r["kappa_rel_err_surrogate"], "coarse_mesh_exact": r["kappa_rel_err_coarse"],
+            "kappa_rel_err": {"surrogate_median": float(np.median(errs)), "surrogate_per_run": errs,
+                              "coarse_mesh_exact": r["kappa_rel_err_coarse"],
                               "nearest_subgrid_interpolation": r["kappa_rel_err_interp"]},
             "heldout_rel_err": {"median": r["heldout_median_rel_err"], "max": r["heldout_max_rel_err"]},
-            "timings_s": t, "n_fallback_q": r["n_fallback_q"], "n_irr": r["n_irr"],
+            "timings_s": t, "n_fallback_q": r["n_fallback_q"], "n_outside_q": r["n_outside_q"], "n_irr": r["n_irr"],
             "final_loss": list(map(float, r["final_loss"])), "epochs_run": r["epochs_run"]}
     print(json.dumps(line, default=float), flush=True)
     ctx.close()

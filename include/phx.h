@@ -121,6 +121,12 @@ const char* phx_version(void);
  *   PHX_OPT_VEL_FP32: 1 = phx_harmonic forms the velocity products dD/dq E (Eq. (groupvel))
  *     with FP32 products and sums (FP64 inputs and outputs: relative error ~1e-7, far below
  *     the 1e-5 bar on kappa); 0 (default) = FP64.  The eigensolve stays FP64 either way.
+ *   PHX_OPT_HARMONIC_TR: 1 (default) = phx_harmonic solves one q of every {q, -q} pair of its q
+ *     list (mod G, components within 1e-9) and fills the other by time reversal: D(-q) is the
+ *     complex conjugate of D(q) (Eq. (dynmat_reciprocal) with the G-periodic phase convention),
+ *     so f(-q) = f(q), e(-q) = conj e(q), v(-q) = -v(q), v (x) v unchanged; a q listed twice is
+ *     copied.  0 = every q is solved on its own.  Either way every output is an FP64 solution of
+ *     Eqs. (eigenvalue_crystal), (groupvel); only the basis of degenerate eigenvectors can differ.
  *   PHX_OPT_WAIT_LIMIT_NS: bound of every device barrier wait of the tensor-core kernels
  *     (default 2e9 ns); a wait that runs out makes the kernel retire and the call return
  *     PHX_ERR_TIMEOUT (host-memory calls; device-memory calls leave the status to the next
@@ -134,7 +140,8 @@ typedef enum {
     PHX_OPT_STARVE = 2,
     PHX_OPT_PAIR = 3,
     PHX_OPT_SIDE_SMS = 4,
-    PHX_OPT_VEL_FP32 = 5
+    PHX_OPT_VEL_FP32 = 5,
+    PHX_OPT_HARMONIC_TR = 6
 } phx_option;
 phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value);
 /* The value an option has in effect: for PHX_OPT_SIDE_SMS the SM count the tensor-core path
@@ -279,11 +286,15 @@ phx_status phx_gamma_cell(phx_ctx* ctx, const phx_fc3* fc3, const double* freq_t
  * conductivity (as phx_unfold + phx_kappa_rta) are enqueued as one CUDA graph, captured on the
  * first call and replayed by later calls with the same job list (same pointers and
  * parameters).  Job arrays are device memory except irr_q (host).  Precision PHX_BF16X3 or
- * PHX_TF32.  The q' tile and the contraction kernel of each job class (modes, mesh, lattice
- * differences) are taken from tune[j] when tune is given and tune[j].q_tile > 0, else chosen
- * by timing every candidate (q' tiles 8..128, and where it fits for the class the chained
- * kernel against the two GEMMs) twice on one irreducible q-point of the first job of the
- * class and keeping the fastest (cached per context).
+ * PHX_TF32.  The q' tile, the contraction kernel and the side-stream share of each job class
+ * (modes, mesh, lattice differences) are taken from tune[j] when tune is given and
+ * tune[j].q_tile > 0; otherwise they are chosen by timing on up to three irreducible q-points
+ * of the first job of the class (best of two runs each): every q' tile 8..128 with, where it fits
+ * for the class, the chained kernel and the two GEMMs, at the context's side-stream share;
+ * then, for the fastest (tile, kernel) and unless PHX_OPT_SIDE_SMS is set, side streams of
+ * 0, 24, 32, 40, 48 and 56 of 152 SMs (scaled to the device).  Choices are cached per
+ * context, and written back into tune[j] (when tune is given) for every job whose q_tile was
+ * 0 on entry.
  * The call enqueues on `stream` (ordered after work already on it) and returns without
  * synchronising.  Errors: as phx_gamma; PHX_ERR_UNSUPPORTED for PHX_FP64. */
 typedef struct {
@@ -305,13 +316,16 @@ typedef struct {
 } phx_job;
 
 typedef struct {
-    int32_t q_tile;                /* q' per Fourier tile; 0 = autotune (tile and kernel)  */
+    int32_t q_tile;                /* q' per Fourier tile; 0 = autotune (all three fields,
+                                      written back on return)                             */
     int32_t chain;                 /* with q_tile > 0: 1 chained kernel (if it fits), 0 the
                                       two GEMMs, -1 as PHX_OPT_CHAIN                       */
+    int32_t side_sms;              /* with q_tile > 0: SMs of the fold/Fourier side stream
+                                      (0 = one stream), -1 as PHX_OPT_SIDE_SMS             */
 } phx_tune;
 
 phx_status phx_gamma_batched(phx_ctx* ctx, int32_t n_jobs, const phx_job* jobs, int32_t prec,
-                             const phx_tune* tune, void* stream);
+                             phx_tune* tune, void* stream);
 
 /* ---------------------------------------------------------------- learned linewidths
  * No counterpart in the paper's equations: a small MLP ensemble that predicts log(gamma) on a
@@ -359,14 +373,21 @@ phx_status phx_mlp_train_es(phx_mlp* m, const double* X, const double* y, int32_
 /* Ensemble mean and standard deviation of log(gamma) per row (device; stdv may be NULL). */
 phx_status phx_mlp_predict(phx_mlp* m, const double* X, int32_t rows, double* mean, double* stdv,
                            void* stream);
+/* Domain of the network: outside[r] = 1 when some input of row r (log scale, as the network
+ * reads it) lies outside the range of the rows the ensemble was last trained on (the gradient
+ * rows of phx_mlp_train / phx_mlp_train_es), else 0; before any training every row is inside.
+ * A prediction there is an extrapolation, which the ensemble spread does not bound.
+ * X [rows][n_in] and outside [rows] device arrays; enqueued on stream. */
+phx_status phx_mlp_outside(phx_mlp* m, const double* X, int32_t rows, int32_t* outside, void* stream);
 /* Linewidths from a prediction, for rows grouped by irreducible q-point (n_groups groups of n
  * rows, row = group * n + band): gamma[r] = exp(mean[r]) * wp2[r] (wp2 NULL: factor 1) where
  * freq_thz[r] >= f_min_thz, else 0; score[g] (optional, needs stdv) = the largest stdv over
- * the live rows of group g (0 if none), the ensemble-spread measure that picks the q-points
- * sent back to the exact kernel.  Device arrays; enqueued on stream. */
+ * the live rows of group g (0 if none), or +infinity when outside (optional, from
+ * phx_mlp_outside) flags a live row of the group: the measure that picks the q-points sent
+ * back to the exact kernel.  Device arrays; enqueued on stream. */
 phx_status phx_mlp_reconstruct(phx_ctx* ctx, int32_t n_groups, int32_t n, const double* mean, const double* stdv,
-                               const double* wp2, const double* freq_thz, double f_min_thz, double* gamma,
-                               double* score, void* stream);
+                               const double* wp2, const double* freq_thz, double f_min_thz, const int32_t* outside,
+                               double* gamma, double* score, void* stream);
 
 /* ---------------------------------------------------------------- transport
  * Map irreducible linewidths to the full mesh (Sec. "Overview of New Capabilities"):

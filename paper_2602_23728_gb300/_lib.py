@@ -54,7 +54,7 @@ class Job(C.Structure):
 
 
 class Tune(C.Structure):
-    _fields_ = [("q_tile", C.c_int32), ("chain", C.c_int32)]
+    _fields_ = [("q_tile", C.c_int32), ("chain", C.c_int32), ("side_sms", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -130,20 +130,22 @@ lib.phx_mlp_train_es.argtypes = [_P, _P, _P, _I, _I, _I, C.c_double, _I, _I, _P,
 lib.phx_mlp_train_es.restype = C.c_int
 lib.phx_mlp_predict.argtypes = [_P, _P, _I, _P, _P, _P]
 lib.phx_mlp_predict.restype = C.c_int
-lib.phx_mlp_reconstruct.argtypes = [_P, _I, _I, _P, _P, _P, _P, C.c_double, _P, _P, _P]
+lib.phx_mlp_reconstruct.argtypes = [_P, _I, _I, _P, _P, _P, _P, C.c_double, _P, _P, _P, _P]
+lib.phx_mlp_outside.argtypes = [_P, _P, _I, _P, _P]
+lib.phx_mlp_outside.restype = C.c_int
 lib.phx_mlp_reconstruct.restype = C.c_int
 
 KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4, "fp64_epilogue": 5,
            "eigensolver": 6, "cell_sparse": 7, "cell_transpose": 8, "cell_gemm": 9, "eig_tridiag": 10,
            "eig_vectors": 11, "eig_back": 12, "eig_bisect": 13, "sc_step": 14, "chain": 15}
 
-OPTIONS = {"chain": 0, "wait_limit_ns": 1, "starve": 2, "pair": 3, "side_sms": 4, "vel_fp32": 5}
+OPTIONS = {"chain": 0, "wait_limit_ns": 1, "starve": 2, "pair": 3, "side_sms": 4, "vel_fp32": 5, "harmonic_tr": 6}
 
 EXPORTED = ["phx_set_option", "phx_get_option", "phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
             "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_isotope", "phx_kappa_qhgk", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta", "phx_kappa_sc",
             "phx_kappa_rta_noalloc", "phx_gamma_batched", "phx_features", "phx_mlp_create", "phx_mlp_destroy",
             "phx_mlp_num_params", "phx_mlp_get_params", "phx_mlp_set_params", "phx_mlp_loss_grad", "phx_mlp_train",
-            "phx_mlp_predict", "phx_mlp_reconstruct", "phx_mlp_train_es"]
+            "phx_mlp_predict", "phx_mlp_reconstruct", "phx_mlp_train_es", "phx_mlp_outside"]
 
 
 class PhxError(RuntimeError):
@@ -282,6 +284,8 @@ class Context:
         'pair' (1: one evaluation per exchange pair {q', q''}, 0: every q'),
         'side_sms' (SMs of the fold/Fourier side stream next to the contractions; -1 default, 0 off),
         'vel_fp32' (1: velocity products of harmonic() with FP32 products and sums),
+        'harmonic_tr' (1, default: harmonic() solves one q of each {q, -q} pair and fills the other
+        by time reversal; 0: every q solved on its own),
         'wait_limit_ns' (bound of every device barrier wait), 'starve' (test hook)."""
         self._check(lib.phx_set_option(self.h, OPTIONS[name], int(value)))
 
@@ -398,13 +402,14 @@ class Context:
                                        PRECISIONS[precision], _ptr(gamma), mem, stream))
         return gamma
 
-    def gamma_batched(self, jobs, precision="bf16x3", q_tiles=None, chain=None):
+    def gamma_batched(self, jobs, precision="bf16x3", q_tiles=None, chain=None, side_sms=None):
         """phx_gamma_batched.  jobs: list of dicts with keys fc3 (FC3), freq, evec (CUDA tensors),
         irr (numpy int32), irr_dev (CUDA int32), T, shape, sigma, window, f_min, gamma (CUDA out),
         and optionally vv, full_to_irr, gamma_full, kappa (CUDA) and volume for the conductivity.
-        q_tiles: None (autotune the tile and the contraction kernel) or a list of q' tiles per
-        job; chain: with q_tiles, a list per job (1 chained kernel, 0 two GEMMs, -1 context
-        option) or None (-1 for all)."""
+        q_tiles: None (autotune the tile, the contraction kernel and the side-stream share) or a
+        list of q' tiles per job; chain, side_sms: with q_tiles, lists per job (chain: 1 chained
+        kernel, 0 two GEMMs; side_sms: SMs of the side stream, 0 one stream; -1 the context
+        option) or None (-1 for all).  Returns the (q_tile, chain, side_sms) used per job."""
         import torch
         arr = (Job * len(jobs))()
         keep = []
@@ -427,16 +432,16 @@ class Context:
             a.gamma_full = _ptr(j.get("gamma_full"))
             a.volume = float(j.get("volume", 0.0))
             a.kappa = _ptr(j.get("kappa"))
-        tune = None
-        if q_tiles is not None:
-            tune = (Tune * len(jobs))()
-            for k, q in enumerate(q_tiles):
-                tune[k].q_tile = int(q)
-                tune[k].chain = -1 if chain is None else int(chain[k])
+        tune = (Tune * max(1, len(jobs)))()
+        for k in range(len(jobs)):
+            tune[k].q_tile = 0 if q_tiles is None else int(q_tiles[k])
+            tune[k].chain = -1 if chain is None else int(chain[k])
+            tune[k].side_sms = -1 if side_sms is None else int(side_sms[k])
         dev = jobs[0]["freq"].device if jobs else torch.device("cuda", self.device)
         stream = torch.cuda.current_stream(dev).cuda_stream
         self._check(lib.phx_gamma_batched(self.h, len(jobs), C.addressof(arr), PRECISIONS[precision],
-                                          C.addressof(tune) if tune is not None else None, stream))
+                                          C.addressof(tune), stream))
+        return [(tune[k].q_tile, tune[k].chain, tune[k].side_sms) for k in range(len(jobs))]
 
     # ------------------------------------------------------------------ learned linewidths
     def features(self, mesh, freq, vel, irr_dev, temperature, shape="gauss", sigma=0.1, window=2.0, f_min=0.01,
@@ -456,9 +461,10 @@ class Context:
     def mlp(self, n_in=4, width=128, depth=3, ensemble=4, seed=0):
         return MLP(self, n_in, width, depth, ensemble, seed)
 
-    def mlp_reconstruct(self, n, mean, std, wp2, freq_rows, f_min=0.01):
+    def mlp_reconstruct(self, n, mean, std, wp2, freq_rows, f_min=0.01, outside=None):
         """phx_mlp_reconstruct on CUDA tensors: (gamma [rows], score [rows / n]) from the
-        ensemble's log prediction (wp2 None: no residual factor)."""
+        ensemble's log prediction (wp2 None: no residual factor; outside: int32 flags from
+        MLP.outside, which make their q-point's score infinite)."""
         import torch
         rows = mean.shape[0]
         if rows % n:
@@ -467,10 +473,13 @@ class Context:
             if a is not None and (not a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous()
                                   or a.numel() != rows):
                 raise ValueError("mlp_reconstruct: contiguous float64 CUDA tensors of one row count")
+        if outside is not None and (not outside.is_cuda or outside.dtype != torch.int32 or not outside.is_contiguous()
+                                    or outside.numel() != rows):
+            raise ValueError("mlp_reconstruct: outside must be a contiguous int32 CUDA tensor of the row count")
         gamma = torch.empty(rows, dtype=torch.float64, device=mean.device)
         score = torch.empty(rows // n, dtype=torch.float64, device=mean.device) if std is not None else None
         self._check(lib.phx_mlp_reconstruct(self.h, rows // n, n, _ptr(mean), _ptr(std), _ptr(wp2), _ptr(freq_rows),
-                                            float(f_min), _ptr(gamma), _ptr(score),
+                                            float(f_min), _ptr(outside), _ptr(gamma), _ptr(score),
                                             torch.cuda.current_stream(mean.device).cuda_stream))
         return gamma, score
 
@@ -611,6 +620,17 @@ class MLP:
         std = torch.zeros(rows, dtype=torch.float64, device=X.device) if std is None else std
         self.ctx._check(lib.phx_mlp_predict(self.h, _ptr(X), rows, _ptr(mean), _ptr(std), self._stream(X)))
         return mean, std
+
+    def outside(self, X, out=None):
+        """int32 flag per row of X (CUDA float64 [rows][n_in]): 1 where an input lies outside the
+        range of the last training rows."""
+        import torch
+        if not X.is_cuda or X.dtype != torch.float64 or not X.is_contiguous() or X.dim() != 2 or X.shape[1] != self.n_in:
+            raise ValueError("outside: X must be a contiguous float64 CUDA tensor [rows][n_in]")
+        rows = X.shape[0]
+        out = torch.zeros(rows, dtype=torch.int32, device=X.device) if out is None else out
+        self.ctx._check(lib.phx_mlp_outside(self.h, _ptr(X), rows, _ptr(out), self._stream(X)))
+        return out
 
     def close(self):
         if self.h:

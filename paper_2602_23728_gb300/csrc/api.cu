@@ -215,6 +215,11 @@ phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value) {
             if (value < 0 || value > 1) return phx_set_error(ctx, PHX_ERR_INVALID, "PHX_OPT_PAIR %lld", (long long)value);
             ctx->opt_pair = (int)value;
             return PHX_OK;
+        case PHX_OPT_HARMONIC_TR:
+            if (value < 0 || value > 1)
+                return phx_set_error(ctx, PHX_ERR_INVALID, "PHX_OPT_HARMONIC_TR %lld", (long long)value);
+            ctx->opt_harm_tr = (int)value;
+            return PHX_OK;
         default:
             return phx_set_error(ctx, PHX_ERR_INVALID, "unknown option %d", option);
     }
@@ -230,6 +235,7 @@ phx_status phx_get_option(phx_ctx* ctx, int32_t option, int64_t* value) {
         case PHX_OPT_PAIR: *value = ctx->opt_pair; return PHX_OK;
         case PHX_OPT_SIDE_SMS: *value = phx_side_sms(ctx); return PHX_OK;
         case PHX_OPT_VEL_FP32: *value = ctx->opt_vel_fp32; return PHX_OK;
+        case PHX_OPT_HARMONIC_TR: *value = ctx->opt_harm_tr; return PHX_OK;
         default: return phx_set_error(ctx, PHX_ERR_INVALID, "unknown option %d", option);
     }
 }
@@ -435,12 +441,23 @@ phx_status phx_harmonic(phx_ctx* ctx, const phx_cell* cell, const phx_ifc2* fc2,
     double* Y = want_v ? (double*)phx_ws(ctx, "h.Y", (size_t)chunk * 3 * n2 * 16) : nullptr;
     if (!large && (!D || !Vw || !hsc || (want_v && (!dD || !Y)))) return PHX_ERR_NOMEM;
     if (!large) PHX_CUDA_CHECK(ctx, cudaMemsetAsync(ctx->status_word, 0, 4, s));
+    // time reversal (Eq. (dynmat_reciprocal): D(-q) = conj D(q)): one q of every {q, -q} pair of
+    // the list is solved, the other filled from it after the loop
+    int32_t *tr_code = nullptr, *tr_skip = nullptr;
+    if (!large && ctx->opt_harm_tr && nq > 1) {
+        tr_code = (int32_t*)phx_ws(ctx, "h.trc", (size_t)nq * 4);
+        tr_skip = (int32_t*)phx_ws(ctx, "h.trs", (size_t)nq * 4);
+        if (!tr_code || !tr_skip) return PHX_ERR_NOMEM;
+        PHX_CUDA_CHECK(ctx, phx_launch_tr_classes(dq, nq, tr_code, tr_skip, s));
+        ctx->launches += 1;
+    }
     for (int q0 = 0; !large && q0 < nq; q0 += chunk) {
         const int c = std::min(chunk, nq - q0);
-        PHX_CUDA_CHECK(ctx, phx_launch_dynmat(dq + 3 * q0, c, na, d_idx, d_val, d_ps, d_m, d_lat, D, dD, s));
+        const int32_t* skip = tr_skip ? tr_skip + q0 : nullptr;
+        PHX_CUDA_CHECK(ctx, phx_launch_dynmat(dq + 3 * q0, c, na, d_idx, d_val, d_ps, d_m, d_lat, D, dD, s, skip));
         const int ps = phx_prof_begin(ctx, s);
         PHX_CUDA_CHECK(ctx, phx_launch_jacobi(D, Vw, n, c, o_f + (int64_t)q0 * n, o_e + (int64_t)q0 * n2 * 2,
-                                              (int32_t*)ctx->status_word, s, hsc));
+                                              (int32_t*)ctx->status_word, s, hsc, skip));
         phx_prof_end(ctx, ps, s, PHX_K_EIGEN, 0.0, 0.0);
         ctx->launches += 2;
         if (want_v) {
@@ -450,12 +467,17 @@ phx_status phx_harmonic(phx_ctx* ctx, const phx_cell* cell, const phx_ifc2* fc2,
             p.C = Y; p.strideC = n2;
             p.lda = n; p.ldb = n; p.ldc = n;
             p.fp32 = ctx->opt_vel_fp32;
+            p.skip = skip; p.skip_div = 3;
             PHX_CUDA_CHECK(ctx, phx_launch_zgemm(n, n, n, 3 * c, p, s));
             PHX_CUDA_CHECK(ctx, phx_launch_velocity(o_e + (int64_t)q0 * n2 * 2, Y, o_f + (int64_t)q0 * n, n, c,
                                                     o_v ? o_v + (int64_t)q0 * n * 3 : nullptr,
-                                                    o_vv ? o_vv + (int64_t)q0 * n * 9 : nullptr, s));
+                                                    o_vv ? o_vv + (int64_t)q0 * n * 9 : nullptr, s, skip));
             ctx->launches += 2;
         }
+    }
+    if (tr_code) {
+        PHX_CUDA_CHECK(ctx, phx_launch_tr_fill(tr_code, nq, n, o_f, o_e, o_v, o_vv, s));
+        ctx->launches += 1;
     }
     int32_t st = 0;
     if (mem == PHX_MEM_HOST) {

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <array>
 #include <map>
 #include <string>
 #include <vector>
@@ -53,12 +54,13 @@ struct phx_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<uint8_t> graph_key;
     int64_t graph_launches = 0;
-    std::map<std::vector<int>, std::pair<int, int>> tune_q;   // job class -> (q' tile, chained kernel)
+    std::map<std::vector<int>, std::array<int, 3>> tune_q;   // job class -> (q' tile, chained kernel, side SMs)
     // options (phx_set_option)
     int opt_chain = 0;                            // 0 auto, 1 force the chained kernel, 2 never
     int opt_pair = 1;                             // evaluate each exchange pair {q', q''} once
     int opt_side_sms = -1;                        // SMs of the side stream (-1: default, 0: one stream)
     int opt_vel_fp32 = 0;                         // velocity products of phx_harmonic in FP32
+    int opt_harm_tr = 1;                          // phx_harmonic solves one q of each {q, -q} pair
     unsigned long long opt_wait_ns = 2000000000ull;   // bound of every device barrier wait
     int opt_starve = 0;                           // test hook: tensor-core producers issue nothing
 };
@@ -160,14 +162,27 @@ static inline phx_status phx_stage_out_buf(phx_ctx* ctx, const char* name, T* p,
 // Each launcher enqueues on `stream` and returns the launch error.
 
 // harmonic.cu
+// skip (optional, per q of the launch): nonzero = the q is filled later from its time-reversal
+// partner by phx_launch_tr_fill, so the kernel leaves it alone
 cudaError_t phx_launch_dynmat(const double* q_frac, int nq, int n_atoms, const int32_t* blk_idx,
                               const double* blk_val, const int32_t* pair_start, const double* masses,
-                              const double* lattice, double* D, double* dD, cudaStream_t s);
+                              const double* lattice, double* D, double* dD, cudaStream_t s,
+                              const int32_t* skip = nullptr);
 // scratch: 4 n doubles per matrix (Householder path for n <= 96; nullptr selects Jacobi)
 cudaError_t phx_launch_jacobi(double* A, double* V, int n, int nq, double* freq, double* evec,
-                              int32_t* status, cudaStream_t s, double* scratch = nullptr);
+                              int32_t* status, cudaStream_t s, double* scratch = nullptr,
+                              const int32_t* skip = nullptr);
 cudaError_t phx_launch_velocity(const double* evec, const double* Y, const double* freq, int n,
-                                int nq, double* vel, double* vv, cudaStream_t s);
+                                int nq, double* vel, double* vv, cudaStream_t s, const int32_t* skip = nullptr);
+// Time-reversal classes of a q list: q_i and q_j are in one class when q_j = q_i or q_j = -q_i
+// (mod G, components within 1e-9).  code[i] = 2 r + c with r the smallest index of the class and
+// c = 1 when q_r = -q_i (and not q_r = q_i); skip[i] = (r != i).
+cudaError_t phx_launch_tr_classes(const double* q_frac, int nq, int32_t* code, int32_t* skip, cudaStream_t s);
+// Fill every q with r != i from its class representative: D(-q) = conj D(q) (the dynamical
+// matrix is G-periodic and Hermitian), so f(-q) = f(q), e(-q) = conj e(q), v(-q) = -v(q) and
+// v (x) v unchanged; a copy where q_r = q_i.  vel, vv may be null.
+cudaError_t phx_launch_tr_fill(const int32_t* code, int nq, int n, double* freq, double* evec, double* vel,
+                               double* vv, cudaStream_t s);
 // eigh_large.cu: Gamma point of a cell with more than 64 atoms (device pair CSR in, device out)
 constexpr int kPhxMaxLargeModes = 8192;
 phx_status phx_eigh_gamma_large(phx_ctx* ctx, int na, const double* blk_val, const int32_t* pair_start,
@@ -187,6 +202,8 @@ struct ZgemmBatch {
     int lda, ldb, ldc;
     int transA;                          // 1: A stored [K][M] (plain transpose, no conjugate)
     int fp32;                            // 1: products and sums in FP32 (FP64 inputs and output)
+    const int32_t* skip;                 // optional: batch b is not computed when skip[b / skip_div] != 0
+    int skip_div;
 };
 cudaError_t phx_launch_zgemm(int M, int N, int K, int batch, const ZgemmBatch& p, cudaStream_t s);
 

@@ -1214,6 +1214,7 @@ struct TcPlan {
     bool chain = false;
     int c_ra = 0, c_rb3 = 0, c_stages = 0;
     size_t c_smem = 0;
+    int side = -1;                          // SMs of the side stream (-1: the context's choice)
     // workspace bytes per operand plane
     size_t bytes_w = 0, bytes_m = 0, bytes_e = 0, bytes_p = 0, bytes_t = 0;
 };
@@ -1541,7 +1542,9 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
     // every producer before its consumer and every consumer before the producer that
     // overwrites its buffer.
     const int side = (ctx->side_stream && B.m2_bytes >= P.bytes_m)
-                         ? side_sms(ctx, sms, n_t > 0 ? CHAIN_GT : (g1 ? CHAIN_GS : CHAIN_G)) : 0;
+                         ? (P.side >= 0 ? std::min(P.side, sms / 2)
+                                        : side_sms(ctx, sms, n_t > 0 ? CHAIN_GT : (g1 ? CHAIN_GS : CHAIN_G)))
+                         : 0;
     cudaStream_t s2 = side > 0 ? ctx->side_stream : s;
     cudaEvent_t* ev = ctx->side_ev;       // [0] fork, [1] join, [2..3] M ready, [4..5] M free, [6..7] lists free
     const int main_ctas = sms - side, side_ctas = side > 0 ? side : sms;
@@ -1716,23 +1719,50 @@ phx_status phx_gamma_tc_multi_t(phx_ctx* ctx, const phx_fc3* f, const double* fr
 
 namespace {
 
-// Best (q' tile, contraction kernel) of a job class: every tile 8..128 with the two GEMMs and,
-// where it fits, with the chained kernel, each timed twice (the faster sample counts) on one
-// irreducible q-point of the job.
+// Best (q' tile, contraction kernel, side-stream share) of a job class, timed on up to three
+// irreducible q-points of the job (the side stream overlaps the next q-point's fold and Fourier
+// GEMM with this one's contractions, which a single q-point does not show; best of two runs
+// per candidate): every tile 8..128 with the two GEMMs and, where it fits, with the chained
+// kernel, at the context's side share; then the side share for the fastest pair (0, 24, 32,
+// 40, 48, 56 of 152 SMs, scaled to the device) unless the context fixes it.
 template <int PREC>
-phx_status autotune_q(phx_ctx* ctx, const phx_job& job, cudaStream_t s, int* best_q, int* best_chain) {
+phx_status autotune_q(phx_ctx* ctx, const phx_job& job, cudaStream_t s, int* best_q, int* best_chain,
+                      int* best_side) {
     const phx_fc3* f = job.fc3;
-    const int iq = job.irr_q[job.n_irr > 1 ? 1 : 0];
+    const int n_time = std::min(job.n_irr, 3);
+    const int32_t* iq = job.irr_q;
+    const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
     GammaParams gp{};
     gp.n = f->n; gp.nq = f->nq; gp.T = job.temperature; gp.shape = job.br.shape; gp.sigma = job.br.sigma_thz;
     gp.window = job.br.window; gp.f_min = job.f_min_thz;
     double* nB = (double*)phx_ws(ctx, "b.nB", (size_t)f->nq * f->n * 8);
-    double* gacc = (double*)phx_ws(ctx, "b.gacc", (size_t)f->n * 8);
+    double* gacc = (double*)phx_ws(ctx, "b.gacc", (size_t)n_time * f->n * 8);
     if (!nB || !gacc) return PHX_ERR_NOMEM;
     PHX_CUDA_CHECK(ctx, phx_launch_occupations(job.freq_thz, f->nq * f->n, job.temperature, 0, nB, nullptr, s));
+    auto time_plan = [&](const TcPlan& P, float* out_ms) -> phx_status {
+        const int side = P.side >= 0 ? P.side : side_sms(ctx, sms);
+        TcBuffers B;
+        if (side > 0) PHX_TRY(ensure_side(ctx));
+        PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.chain ? 0 : P.bytes_m, P.bytes_e, P.bytes_p, P.bytes_t,
+                         P.nq, f->nnz, (int64_t)P.n * P.n, &B, side > 0 ? P.bytes_m : 0));
+        float best_rep = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            float ms = 0.f;
+            PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_in, s));
+            PHX_TRY(tc_enqueue<PREC>(ctx, P, f, B, job.freq_thz, job.evec, nB, iq, n_time, gp, gacc, nullptr, s));
+            PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_out, s));
+            PHX_CUDA_CHECK(ctx, cudaEventSynchronize(ctx->ev_out));
+            PHX_CUDA_CHECK(ctx, cudaEventElapsedTime(&ms, ctx->ev_in, ctx->ev_out));
+            best_rep = std::min(best_rep, ms);
+        }
+        *out_ms = best_rep;
+        return PHX_OK;
+    };
     float best_ms = 1e30f;
+    TcPlan best{};
     *best_q = 0;
     *best_chain = 0;
+    *best_side = -1;
     for (int chain = 0; chain < 2; ++chain) {
         int last_q = -1;
         for (int cand : {8, 16, 32, 64, 128}) {
@@ -1741,30 +1771,31 @@ phx_status autotune_q(phx_ctx* ctx, const phx_job& job, cudaStream_t s, int* bes
             if (P.chain != (chain == 1)) break;          // the chained kernel does not fit this class
             if (P.Q == last_q) continue;                 // clamped to the mesh size already tried
             last_q = P.Q;
-            TcBuffers B;
-            const bool two_m = side_sms(ctx, ctx->sm_count > 0 ? ctx->sm_count : 148) > 0;
-            if (two_m) PHX_TRY(ensure_side(ctx));
-            PHX_TRY(tc_alloc(ctx, PREC, P.bytes_w, P.bytes_m, P.chain ? 0 : P.bytes_m, P.bytes_e, P.bytes_p, P.bytes_t,
-                             P.nq, f->nnz, (int64_t)P.n * P.n, &B, two_m ? P.bytes_m : 0));
-            float best_rep = 1e30f;
-            for (int rep = 0; rep < 2; ++rep) {
-                float ms = 0.f;
-                PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_in, s));
-                PHX_TRY(tc_enqueue<PREC>(ctx, P, f, B, job.freq_thz, job.evec, nB, &iq, 1, gp, gacc, nullptr, s));
-                PHX_CUDA_CHECK(ctx, cudaEventRecord(ctx->ev_out, s));
-                PHX_CUDA_CHECK(ctx, cudaEventSynchronize(ctx->ev_out));
-                PHX_CUDA_CHECK(ctx, cudaEventElapsedTime(&ms, ctx->ev_in, ctx->ev_out));
-                best_rep = std::min(best_rep, ms);
-            }
-            if (best_rep < best_ms) { best_ms = best_rep; *best_q = P.Q; *best_chain = chain; }
+            float ms = 0.f;
+            PHX_TRY(time_plan(P, &ms));
+            if (ms < best_ms) { best_ms = ms; best = P; *best_q = P.Q; *best_chain = chain; }
         }
     }
     if (*best_q == 0) return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "autotune: no q' tile fits");
+    if (ctx->opt_side_sms < 0) {
+        const int dflt = side_sms(ctx, sms);
+        int chosen = dflt;
+        for (int base : {0, 24, 32, 40, 48, 56}) {
+            const int cand = std::min(base * sms / 152, sms / 2);
+            if (cand == dflt) continue;                  // timed above
+            TcPlan P = best;
+            P.side = cand;
+            float ms = 0.f;
+            PHX_TRY(time_plan(P, &ms));
+            if (ms < best_ms) { best_ms = ms; chosen = cand; }
+        }
+        *best_side = chosen;
+    }
     return PHX_OK;
 }
 
 template <int PREC>
-phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, const phx_tune* tune, cudaStream_t user) {
+phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, phx_tune* tune, cudaStream_t user) {
     if (!ctx->cap_stream) {
         PHX_CUDA_CHECK(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
         PHX_CUDA_CHECK(ctx, cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDefault));
@@ -1777,30 +1808,39 @@ phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, const phx_
 
     // plans (q' tile from the caller, the autotune table, or a fresh tuning run)
     std::vector<TcPlan> plans(n_jobs);
-    std::vector<int> qtiles(n_jobs, 0), chains(n_jobs, -1);
+    std::vector<int> qtiles(n_jobs, 0), chains(n_jobs, -1), sides(n_jobs, -1);
     for (int j = 0; j < n_jobs; ++j) {
         const phx_job& jb = jobs[j];
         PHX_TRY(tc_prepare_fc3(ctx, const_cast<phx_fc3*>(jb.fc3)));
-        int q = (tune && tune[j].q_tile > 0) ? tune[j].q_tile : 0;
-        int ch = (tune && tune[j].q_tile > 0) ? tune[j].chain : -1;
+        const bool given = tune && tune[j].q_tile > 0;
+        int q = given ? tune[j].q_tile : 0;
+        int ch = given ? tune[j].chain : -1;
+        int sd = given ? tune[j].side_sms : -1;
         if (q == 0) {
-            const std::vector<int> key = {PREC, jb.fc3->n, jb.fc3->mesh[0], jb.fc3->mesh[1], jb.fc3->mesh[2], jb.fc3->n_d};
+            const std::vector<int> key = {PREC, jb.fc3->n, jb.fc3->mesh[0], jb.fc3->mesh[1], jb.fc3->mesh[2],
+                                          jb.fc3->n_d, ctx->opt_side_sms};
             auto it = ctx->tune_q.find(key);
             if (it == ctx->tune_q.end()) {
-                PHX_TRY(autotune_q<PREC>(ctx, jb, cs, &q, &ch));
-                ctx->tune_q[key] = {q, ch};
+                PHX_TRY(autotune_q<PREC>(ctx, jb, cs, &q, &ch, &sd));
+                ctx->tune_q[key] = {q, ch, sd};
             } else {
-                q = it->second.first;
-                ch = it->second.second;
+                q = it->second[0];
+                ch = it->second[1];
+                sd = it->second[2];
             }
+            if (tune) { tune[j].q_tile = q; tune[j].chain = ch; tune[j].side_sms = sd; }
         }
         qtiles[j] = q;
         chains[j] = ch;
+        sides[j] = sd;
         PHX_TRY(tc_plan(ctx, jb.fc3, PREC, q, &plans[j], ch));
+        plans[j].side = sd;
     }
     // workspace for the largest job, allocated before any capture (as are the side stream and its
     // events: chained jobs then keep a second M buffer in the X workspace)
-    const int side = side_sms(ctx, ctx->sm_count > 0 ? ctx->sm_count : 148);
+    const int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
+    int side = 0;
+    for (int j = 0; j < n_jobs; ++j) side = std::max(side, sides[j] >= 0 ? std::min(sides[j], sms / 2) : side_sms(ctx, sms));
     if (side > 0) PHX_TRY(ensure_side(ctx));
     size_t bw = 0, bm = 0, bx = 0, be = 0, bp = 0, bt = 0;
     int64_t mnq = 1, mnnz = 1, mn2 = 1, mnb = 1, mg = 1;
@@ -1822,12 +1862,19 @@ phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, const phx_
     if (!nB || !gacc || !acc9) return PHX_ERR_NOMEM;
 
     // graph key: the job list, the precision, the pair option and the tiles
-    std::vector<uint8_t> key(sizeof(phx_job) * n_jobs + sizeof(int) * (2 * n_jobs + 1));
-    std::memcpy(key.data(), jobs, sizeof(phx_job) * n_jobs);
-    std::memcpy(key.data() + sizeof(phx_job) * n_jobs, qtiles.data(), sizeof(int) * n_jobs);
-    std::memcpy(key.data() + sizeof(phx_job) * n_jobs + sizeof(int) * n_jobs, chains.data(), sizeof(int) * n_jobs);
-    const int prec_v = PREC + 16 * ctx->opt_pair + 32 * side;   // the pair and side-stream options change the launches
-    std::memcpy(key.data() + sizeof(phx_job) * n_jobs + sizeof(int) * 2 * n_jobs, &prec_v, sizeof(int));
+    std::vector<uint8_t> key(sizeof(phx_job) * n_jobs + sizeof(int) * (3 * n_jobs + 2));
+    uint8_t* kp = key.data();
+    std::memcpy(kp, jobs, sizeof(phx_job) * n_jobs);
+    kp += sizeof(phx_job) * n_jobs;
+    std::memcpy(kp, qtiles.data(), sizeof(int) * n_jobs);
+    kp += sizeof(int) * n_jobs;
+    std::memcpy(kp, chains.data(), sizeof(int) * n_jobs);
+    kp += sizeof(int) * n_jobs;
+    std::memcpy(kp, sides.data(), sizeof(int) * n_jobs);
+    kp += sizeof(int) * n_jobs;
+    // the pair and side-stream options change the launches
+    const int opts[2] = {PREC + 16 * ctx->opt_pair, side_sms(ctx, sms)};
+    std::memcpy(kp, opts, sizeof(opts));
     // host irr lists are part of the key by content
     for (int j = 0; j < n_jobs; ++j) {
         const uint8_t* b = (const uint8_t*)jobs[j].irr_q;
@@ -1906,7 +1953,7 @@ phx_status run_batched(phx_ctx* ctx, int n_jobs, const phx_job* jobs, const phx_
 }  // namespace
 
 extern "C" phx_status phx_gamma_batched(phx_ctx* ctx, int32_t n_jobs, const phx_job* jobs, int32_t prec,
-                                        const phx_tune* tune, void* stream) {
+                                        phx_tune* tune, void* stream) {
     if (!ctx) return PHX_ERR_INVALID;
     if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return phx_set_error(ctx, PHX_ERR_INVALID, "phx_gamma_batched: bad job list");
     if (n_jobs == 0) return PHX_OK;

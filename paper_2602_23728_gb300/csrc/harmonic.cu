@@ -28,8 +28,9 @@ __global__ void dynmat_kernel(const double* __restrict__ q_frac, int n_atoms,
                               const int32_t* __restrict__ blk_idx, const double* __restrict__ blk_val,
                               const int32_t* __restrict__ pair_start, const double* __restrict__ masses,
                               const double* __restrict__ lattice, double2* __restrict__ D,
-                              double2* __restrict__ dD) {
+                              double2* __restrict__ dD, const int32_t* __restrict__ skip) {
     const int q = blockIdx.x;
+    if (skip && skip[q]) return;
     const int n = 3 * n_atoms;
     const int64_t nn = (int64_t)n * n;
     const double q0 = q_frac[3 * q], q1 = q_frac[3 * q + 1], q2 = q_frac[3 * q + 2];
@@ -92,7 +93,8 @@ __device__ __forceinline__ int rr_player(int x, int r, int m) {
 template <bool kSmem>
 __global__ void __launch_bounds__(kJacobiThreads)
 jacobi_kernel(double2* __restrict__ Ag, double2* __restrict__ Vg, int n, double* __restrict__ freq,
-              double2* __restrict__ evec, int32_t* __restrict__ status) {
+              double2* __restrict__ evec, int32_t* __restrict__ status, const int32_t* __restrict__ skip) {
+    if (skip && skip[blockIdx.x]) return;
     extern __shared__ double2 shA[];
     __shared__ double rc[kMaxPairs], rs[kMaxPairs], rpc[kMaxPairs], rps[kMaxPairs];
     __shared__ int rp[kMaxPairs], rq[kMaxPairs], ract[kMaxPairs];
@@ -255,7 +257,9 @@ constexpr int kQlThreads = 128;
 
 // per-matrix scratch (doubles): d[n], e re/im [2n], beta[n]
 __global__ void __launch_bounds__(256)
-hh_reduce_kernel(const double2* __restrict__ Dg, double2* __restrict__ Rg, double* __restrict__ scratch, int n) {
+hh_reduce_kernel(const double2* __restrict__ Dg, double2* __restrict__ Rg, double* __restrict__ scratch, int n,
+                 const int32_t* __restrict__ skip) {
+    if (skip && skip[blockIdx.x]) return;
     extern __shared__ double2 A[];                           // n x n, row-major
     __shared__ double red[32];
     const int qi = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -357,7 +361,9 @@ hh_reduce_kernel(const double2* __restrict__ Dg, double2* __restrict__ Rg, doubl
 
 __global__ void __launch_bounds__(kQlThreads)
 ql_back_kernel(const double2* __restrict__ Rg, const double* __restrict__ scratch, double* __restrict__ Zg, int n,
-               double* __restrict__ freq, double2* __restrict__ evec, int32_t* __restrict__ status) {
+               double* __restrict__ freq, double2* __restrict__ evec, int32_t* __restrict__ status,
+               const int32_t* __restrict__ skip) {
+    if (skip && skip[blockIdx.x]) return;
     __shared__ double d[kHhqlMaxModes], e[kHhqlMaxModes], rc[kHhqlMaxModes], rs[kHhqlMaxModes];
     __shared__ double2 ph[kHhqlMaxModes];
     __shared__ int rank_of[kHhqlMaxModes];
@@ -537,9 +543,10 @@ ql_back_kernel(const double2* __restrict__ Rg, const double* __restrict__ scratc
 // One CTA per q.  Y[q][a] = dD_a(q) E(q) (complex), E sorted by frequency.
 __global__ void velocity_kernel(const double2* __restrict__ E, const double2* __restrict__ Y,
                                 const double* __restrict__ freq, int n, double* __restrict__ vel,
-                                double* __restrict__ vv) {
+                                double* __restrict__ vv, const int32_t* __restrict__ skip) {
     __shared__ int grp_lo[kMaxModes], grp_hi[kMaxModes];
     const int q = blockIdx.x;
+    if (skip && skip[q]) return;
     const int64_t nn = (int64_t)n * n;
     const double* f = freq + (int64_t)q * n;
     if (threadIdx.x == 0) {
@@ -601,19 +608,98 @@ __global__ void velocity_kernel(const double2* __restrict__ E, const double2* __
     }
 }
 
+// |x - nearest integer| below the tolerance of q-point identity (reduced coordinates)
+__device__ __forceinline__ bool near_integer(double x) { return fabs(x - rint(x)) < 1e-9; }
+
+// One thread per q_i: the first j (ascending, j < i) with q_j = q_i or q_j = -q_i mod G.  The
+// classes are unions of two G-translate sets, so the first index met is the class minimum and
+// every member finds the same one.  q_j tiles are staged in shared memory.
+__global__ void __launch_bounds__(256)
+tr_classes_kernel(const double* __restrict__ q_frac, int nq, int32_t* __restrict__ code, int32_t* __restrict__ skip) {
+    __shared__ double tq[3][256];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = i < nq;
+    const double a0 = act ? q_frac[3 * i] : 0.0, a1 = act ? q_frac[3 * i + 1] : 0.0,
+                 a2 = act ? q_frac[3 * i + 2] : 0.0;
+    int rep = i, cj = 0;
+    bool done = !act;
+    const int j_end = min(nq, (blockIdx.x + 1) * blockDim.x);   // no j at or beyond the block's last i
+    for (int t0 = 0; t0 < j_end; t0 += 256) {
+        const int jl = t0 + threadIdx.x;
+        if (jl < nq)
+            for (int c = 0; c < 3; ++c) tq[c][threadIdx.x] = q_frac[3 * jl + c];
+        __syncthreads();
+        const int lim = min(256, j_end - t0);
+        for (int k = 0; k < lim && !done; ++k) {
+            const int j = t0 + k;
+            if (j >= i) { done = true; break; }
+            const double b0 = tq[0][k], b1 = tq[1][k], b2 = tq[2][k];
+            const bool same = near_integer(b0 - a0) && near_integer(b1 - a1) && near_integer(b2 - a2);
+            const bool neg = near_integer(b0 + a0) && near_integer(b1 + a1) && near_integer(b2 + a2);
+            if (same || neg) {
+                rep = j;
+                cj = same ? 0 : 1;
+                done = true;
+            }
+        }
+        if (__syncthreads_and(done)) break;
+    }
+    if (act) {
+        code[i] = 2 * rep + cj;
+        skip[i] = rep != i;
+    }
+}
+
+// One CTA per q: copy (or conjugate) the representative's outputs into q's rows.
+__global__ void __launch_bounds__(256)
+tr_fill_kernel(const int32_t* __restrict__ code, int n, double* __restrict__ freq, double2* __restrict__ evec,
+               double* __restrict__ vel, double* __restrict__ vv) {
+    const int i = blockIdx.x;
+    const int c = code[i], r = c >> 1;
+    if (r == i) return;
+    const bool cj = (c & 1) != 0;
+    const int64_t nn = (int64_t)n * n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) freq[(int64_t)i * n + k] = freq[(int64_t)r * n + k];
+    for (int64_t k = threadIdx.x; k < nn; k += blockDim.x) {
+        double2 e = evec[(int64_t)r * nn + k];
+        if (cj) e.y = -e.y;
+        evec[(int64_t)i * nn + k] = e;
+    }
+    if (vel)
+        for (int k = threadIdx.x; k < 3 * n; k += blockDim.x) {
+            const double v = vel[(int64_t)r * 3 * n + k];
+            vel[(int64_t)i * 3 * n + k] = cj ? -v : v;
+        }
+    if (vv)
+        for (int k = threadIdx.x; k < 9 * n; k += blockDim.x) vv[(int64_t)i * 9 * n + k] = vv[(int64_t)r * 9 * n + k];
+}
+
 }  // namespace
+
+cudaError_t phx_launch_tr_classes(const double* q_frac, int nq, int32_t* code, int32_t* skip, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    tr_classes_kernel<<<(nq + 255) / 256, 256, 0, s>>>(q_frac, nq, code, skip);
+    return cudaGetLastError();
+}
+
+cudaError_t phx_launch_tr_fill(const int32_t* code, int nq, int n, double* freq, double* evec, double* vel,
+                               double* vv, cudaStream_t s) {
+    if (nq <= 0) return cudaSuccess;
+    tr_fill_kernel<<<nq, 256, 0, s>>>(code, n, freq, (double2*)evec, vel, vv);
+    return cudaGetLastError();
+}
 
 cudaError_t phx_launch_dynmat(const double* q_frac, int nq, int n_atoms, const int32_t* blk_idx,
                               const double* blk_val, const int32_t* pair_start, const double* masses,
-                              const double* lattice, double* D, double* dD, cudaStream_t s) {
+                              const double* lattice, double* D, double* dD, cudaStream_t s, const int32_t* skip) {
     if (nq <= 0) return cudaSuccess;
     dynmat_kernel<<<nq, 256, 0, s>>>(q_frac, n_atoms, blk_idx, blk_val, pair_start, masses, lattice,
-                                     (double2*)D, (double2*)dD);
+                                     (double2*)D, (double2*)dD, skip);
     return cudaGetLastError();
 }
 
 cudaError_t phx_launch_jacobi(double* A, double* V, int n, int nq, double* freq, double* evec,
-                              int32_t* status, cudaStream_t s, double* scratch) {
+                              int32_t* status, cudaStream_t s, double* scratch, const int32_t* skip) {
     if (nq <= 0) return cudaSuccess;
     if (n > kMaxModes) return cudaErrorInvalidValue;
     const size_t smem = (size_t)n * n * sizeof(double2);
@@ -625,8 +711,9 @@ cudaError_t phx_launch_jacobi(double* A, double* V, int n, int nq, double* freq,
         // with Z (real) in A's buffer
         cudaError_t e = cudaFuncSetAttribute(hh_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        hh_reduce_kernel<<<nq, 256, smem, s>>>((const double2*)A, (double2*)V, scratch, n);
-        ql_back_kernel<<<nq, kQlThreads, 0, s>>>((const double2*)V, scratch, A, n, freq, (double2*)evec, status);
+        hh_reduce_kernel<<<nq, 256, smem, s>>>((const double2*)A, (double2*)V, scratch, n, skip);
+        ql_back_kernel<<<nq, kQlThreads, 0, s>>>((const double2*)V, scratch, A, n, freq, (double2*)evec, status,
+                                                 skip);
         return cudaGetLastError();
     }
     const size_t static_bytes = 8 * 1024;     // rotation tables etc. (upper bound)
@@ -635,17 +722,17 @@ cudaError_t phx_launch_jacobi(double* A, double* V, int n, int nq, double* freq,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         jacobi_kernel<true><<<nq, kJacobiThreads, smem, s>>>((double2*)A, (double2*)V, n, freq,
-                                                             (double2*)evec, status);
+                                                             (double2*)evec, status, skip);
     } else {
         jacobi_kernel<false><<<nq, kJacobiThreads, 0, s>>>((double2*)A, (double2*)V, n, freq,
-                                                           (double2*)evec, status);
+                                                           (double2*)evec, status, skip);
     }
     return cudaGetLastError();
 }
 
 cudaError_t phx_launch_velocity(const double* evec, const double* Y, const double* freq, int n,
-                                int nq, double* vel, double* vv, cudaStream_t s) {
+                                int nq, double* vel, double* vv, cudaStream_t s, const int32_t* skip) {
     if (nq <= 0) return cudaSuccess;
-    velocity_kernel<<<nq, 128, 0, s>>>((const double2*)evec, (const double2*)Y, freq, n, vel, vv);
+    velocity_kernel<<<nq, 128, 0, s>>>((const double2*)evec, (const double2*)Y, freq, n, vel, vv, skip);
     return cudaGetLastError();
 }

@@ -329,6 +329,47 @@ __global__ void input_kernel(const double* __restrict__ X, int M, int F, const f
     }
 }
 
+// column min / max of log(max(x, 1e-12)) over the first M rows (one block per column), rounded
+// outward to float so that every row of the set lies inside its own range
+__global__ void range_kernel(const double* __restrict__ X, int M, int F, float* __restrict__ lo,
+                             float* __restrict__ hi) {
+    __shared__ double s1[256], s2[256];
+    const int f = blockIdx.x;
+    double a = INFINITY, b = -INFINITY;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const double v = log(fmax(X[(int64_t)i * F + f], 1e-12));
+        a = fmin(a, v);
+        b = fmax(b, v);
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s1[threadIdx.x] = fmin(s1[threadIdx.x], s1[threadIdx.x + o]);
+            s2[threadIdx.x] = fmax(s2[threadIdx.x], s2[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        lo[f] = __double2float_rd(s1[0]);
+        hi[f] = __double2float_ru(s2[0]);
+    }
+}
+
+// outside[r] = 1 when some input of row r lies outside the range of the training inputs (log scale)
+__global__ void outside_kernel(const double* __restrict__ X, int M, int F, const float* __restrict__ lo,
+                               const float* __restrict__ hi, int32_t* __restrict__ outside) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < M; r += gridDim.x * blockDim.x) {
+        int o = 0;
+        for (int f = 0; f < F; ++f) {
+            const double v = log(fmax(X[(int64_t)r * F + f], 1e-12));
+            if (v < (double)lo[f] || v > (double)hi[f]) o = 1;
+        }
+        outside[r] = o;
+    }
+}
+
 // column mean / std of log(max(x, floor)) (one block per column); std floored at 1e-6
 __global__ void moments_kernel(const double* __restrict__ X, int M, int F, int take_log, float* __restrict__ mu,
                                float* __restrict__ sd) {
@@ -459,6 +500,7 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(int n, const double* _
                                                           const double* __restrict__ stdv,
                                                           const double* __restrict__ wp2,
                                                           const double* __restrict__ freq, double f_min,
+                                                          const int32_t* __restrict__ outside,
                                                           double* __restrict__ gamma, double* __restrict__ score) {
     __shared__ double red[8];
     const int64_t r0 = (int64_t)blockIdx.x * n;
@@ -471,6 +513,7 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(int n, const double* _
             g = exp(mean[r]);
             if (wp2) g *= wp2[r];
             if (stdv) mx = fmax(mx, stdv[r]);
+            if (outside && outside[r]) mx = INFINITY;
         }
         gamma[r] = g;
     }
@@ -506,6 +549,7 @@ struct phx_mlp {
     float *par = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
     float *mu = nullptr, *sd = nullptr;        // input (n_in) and target (1) standardisation
     float *ymu = nullptr, *ysd = nullptr;
+    float *xlo = nullptr, *xhi = nullptr;      // range of the log inputs of the last training rows
     int64_t cap = 0;                           // activation buffers capacity (rows)
     float *act = nullptr, *pre = nullptr;      // [depth+2][E][rows][width]
     float *xin = nullptr, *ystd = nullptr, *dbuf0 = nullptr, *dbuf1 = nullptr;
@@ -662,6 +706,8 @@ phx_status phx_mlp_create(phx_ctx* ctx, int32_t n_in, int32_t width, int32_t dep
               cudaMalloc(&m->m1, pb) == cudaSuccess && cudaMalloc(&m->m2, pb) == cudaSuccess &&
               cudaMalloc(&m->mu, sizeof(float) * 64) == cudaSuccess && cudaMalloc(&m->sd, sizeof(float) * 64) == cudaSuccess &&
               cudaMalloc(&m->ymu, sizeof(float)) == cudaSuccess && cudaMalloc(&m->ysd, sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->xlo, sizeof(float) * 64) == cudaSuccess &&
+              cudaMalloc(&m->xhi, sizeof(float) * 64) == cudaSuccess &&
               cudaMalloc(&m->loss, sizeof(double) * ensemble) == cudaSuccess &&
               cudaMalloc(&m->vloss, sizeof(double) * ensemble) == cudaSuccess &&
               cudaMalloc(&m->best, pb) == cudaSuccess &&
@@ -686,6 +732,12 @@ phx_status phx_mlp_create(phx_ctx* ctx, int32_t n_in, int32_t width, int32_t dep
     }
     float one = 1.f, zero = 0.f;
     for (int f = 0; f < 64; ++f) { cudaMemcpy(m->mu + f, &zero, 4, cudaMemcpyHostToDevice); cudaMemcpy(m->sd + f, &one, 4, cudaMemcpyHostToDevice); }
+    // no training rows yet: every input is inside
+    const float big = 3.0e38f, nbig = -3.0e38f;
+    for (int f = 0; f < 64; ++f) {
+        cudaMemcpy(m->xlo + f, &nbig, 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(m->xhi + f, &big, 4, cudaMemcpyHostToDevice);
+    }
     cudaMemcpy(m->ymu, &zero, 4, cudaMemcpyHostToDevice);
     cudaMemcpy(m->ysd, &one, 4, cudaMemcpyHostToDevice);
     *out = m;
@@ -696,6 +748,7 @@ void phx_mlp_destroy(phx_mlp* m) {
     if (!m) return;
     cudaFree(m->par); cudaFree(m->grad); cudaFree(m->m1); cudaFree(m->m2);
     cudaFree(m->mu); cudaFree(m->sd); cudaFree(m->ymu); cudaFree(m->ysd); cudaFree(m->loss); cudaFree(m->step);
+    cudaFree(m->xlo); cudaFree(m->xhi);
     cudaFree(m->vloss); cudaFree(m->best);
     cudaFree(m->act); cudaFree(m->pre); cudaFree(m->xin); cudaFree(m->ystd); cudaFree(m->dbuf0); cudaFree(m->dbuf1);
     delete m;
@@ -777,6 +830,7 @@ static phx_status mlp_train_impl(phx_mlp* m, const double* X, const double* y, i
     PHX_CUDA_CHECK(ctx, cudaStreamWaitEvent(s, ctx->ev_in, 0));
     moments_kernel<<<m->n_in, 256, 0, s>>>(X, rows_tr, m->n_in, 1, m->mu, m->sd);
     moments_kernel<<<1, 256, 0, s>>>(y, rows_tr, 1, 1, m->ymu, m->ysd);
+    range_kernel<<<m->n_in, 256, 0, s>>>(X, rows_tr, m->n_in, m->xlo, m->xhi);
     input_kernel<<<256, 256, 0, s>>>(X, rows, m->n_in, m->mu, m->sd, m->xin);
     target_kernel<<<64, 256, 0, s>>>(y, rows, m->ymu, m->ysd, m->ystd);
     PHX_CUDA_CHECK(ctx, cudaGetLastError());
@@ -913,16 +967,26 @@ phx_status phx_mlp_predict(phx_mlp* m, const double* X, int32_t rows, double* me
     return PHX_OK;
 }
 
+phx_status phx_mlp_outside(phx_mlp* m, const double* X, int32_t rows, int32_t* outside, void* stream) {
+    if (!m || !X || !outside || rows <= 0) return PHX_ERR_INVALID;
+    cudaSetDevice(m->ctx->device);
+    outside_kernel<<<(int)std::min<int64_t>((rows + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>(
+        X, rows, m->n_in, m->xlo, m->xhi, outside);
+    PHX_CUDA_CHECK(m->ctx, cudaGetLastError());
+    m->ctx->launches += 1;
+    return PHX_OK;
+}
+
 phx_status phx_mlp_reconstruct(phx_ctx* ctx, int32_t n_groups, int32_t n, const double* mean, const double* stdv,
-                               const double* wp2, const double* freq_thz, double f_min_thz, double* gamma,
-                               double* score, void* stream) {
+                               const double* wp2, const double* freq_thz, double f_min_thz, const int32_t* outside,
+                               double* gamma, double* score, void* stream) {
     if (!ctx) return PHX_ERR_INVALID;
     if (n_groups <= 0 || n <= 0 || !mean || !freq_thz || !gamma)
         return phx_set_error(ctx, PHX_ERR_INVALID, "phx_mlp_reconstruct: bad argument");
     if (score && !stdv) return phx_set_error(ctx, PHX_ERR_INVALID, "phx_mlp_reconstruct: score needs stdv");
     cudaSetDevice(ctx->device);
-    reconstruct_kernel<<<n_groups, 256, 0, (cudaStream_t)stream>>>(n, mean, stdv, wp2, freq_thz, f_min_thz, gamma,
-                                                                   score);
+    reconstruct_kernel<<<n_groups, 256, 0, (cudaStream_t)stream>>>(n, mean, stdv, wp2, freq_thz, f_min_thz, outside,
+                                                                   gamma, score);
     PHX_CUDA_CHECK(ctx, cudaGetLastError());
     ctx->launches += 1;
     return PHX_OK;

@@ -17,6 +17,7 @@ zgemm_kernel(int M, int N, int K, ZgemmBatch p) {
     __shared__ C2 As[BK][BM + 1];
     __shared__ C2 Bs[BK][BN + 1];
     const int b = blockIdx.z;
+    if (p.skip && p.skip[b / p.skip_div]) return;
     const int64_t ia = p.idxA ? (int64_t)p.idxA[b / p.divA] : (int64_t)(b / p.divA);
     const int64_t ib = p.idxB ? (int64_t)p.idxB[b / p.divB] : (int64_t)(b / p.divB);
     const double2* A = (const double2*)p.A + ia * p.strideA;

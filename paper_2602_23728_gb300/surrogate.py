@@ -32,7 +32,7 @@ def subgrid_points(mesh, step):
 def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh, step, rotations, temperature,
         shape="gauss", sigma=0.1, f_min=0.01, precision="bf16x3", epochs=3000, lr=3e-3, heldout_frac=0.05,
         uncertainty_pct=95.0, ensemble=4, width=128, depth=3, seed=0, exact_reference=True, residual=True,
-        early_stop=True, val_frac=0.1, check_every=50, patience=4):
+        early_stop=True, val_frac=0.1, check_every=50, patience=4, ood_fallback=True):
     """Surrogate linewidths and RTA conductivity on `mesh` trained on the subgrid of spacing
     `step`.  Returns a dict with the conductivities (surrogate, exact when asked, nearest-
     subgrid baseline), errors, timings and counts.
@@ -42,7 +42,10 @@ def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh,
 
     early_stop: a seeded val_frac of the training rows is kept out of the gradient and training
     stops once its loss has not improved for `patience` checks of `check_every` epochs (at most
-    `epochs`); otherwise exactly `epochs` full-batch Adam steps."""
+    `epochs`); otherwise exactly `epochs` full-batch Adam steps.
+
+    ood_fallback: q-points with a mode whose descriptors lie outside the range of the training
+    rows go to the exact kernel as well (on top of the uncertainty_pct rule)."""
     import torch
     dev = torch.device("cuda", ctx.device)
     n = 3 * len(masses)
@@ -126,20 +129,28 @@ def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh,
 
     t0 = _timer(torch)
     mean, std = model.predict(X_all)
+    # rows whose descriptors lie outside the range of the training rows: the network would
+    # extrapolate there (typically the acoustic modes closer to Gamma than any subgrid point)
+    outside = model.outside(X_all) if ood_fallback else None
     # linewidths (exp of the prediction, times WP2 for the residual target, 0 below f_min) and
-    # the per-q-point ensemble spread, on the device
-    pred_d, score_d = ctx.mlp_reconstruct(n, mean, std, wp2_all if residual else None, f_all.contiguous(), f_min)
+    # the per-q-point ensemble spread (infinite where a mode is outside), on the device
+    pred_d, score_d = ctx.mlp_reconstruct(n, mean, std, wp2_all if residual else None, f_all.contiguous(), f_min,
+                                          outside=outside)
     t["infer"] = _timer(torch) - t0
     score = score_d.cpu().numpy()
     # held-out check (reported, not used by the path)
     hold_d = torch.from_numpy(hold_rows).to(dev)
     hold_err = (torch.abs(pred_d[hold_d] - y_all[hold_d]) / y_all[hold_d]).cpu().numpy()
 
-    # exact fallback on the q-points whose most uncertain mode ranks in the top
-    # (100 - uncertainty_pct) % of the q-points outside the subgrid
+    # exact fallback on the q-points outside the network's domain, and on those whose most
+    # uncertain mode ranks in the top (100 - uncertainty_pct) % of the other q-points outside
+    # the subgrid
     cand = np.array([k for k in range(len(irr)) if not train_mask0[k]], dtype=np.int64)
+    ood = cand[np.isinf(score[cand])]
+    rest = cand[~np.isinf(score[cand])]
     n_fb = int(np.ceil((100.0 - uncertainty_pct) / 100.0 * len(cand)))
-    fb_q = sorted(int(irr[k]) for k in cand[np.argsort(-score[cand])[:n_fb]]) if n_fb > 0 else []
+    pick = rest[np.argsort(-score[rest], kind="stable")[:n_fb]] if n_fb > 0 else rest[:0]
+    fb_q = sorted(int(irr[k]) for k in np.concatenate([ood, pick]))
     t0 = _timer(torch)
     if fb_q:
         fb = np.array(fb_q, dtype=np.int32)
@@ -185,7 +196,8 @@ def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh,
 
     out = dict(kappa_surrogate=k_sur, kappa_interp=k_base, kappa_coarse=k_coarse, timings=t, final_loss=final_loss,
                heldout_median_rel_err=float(np.median(hold_err)), heldout_max_rel_err=float(hold_err.max()),
-               n_irr=len(irr), n_train_q=len(train_q), n_fallback_q=len(fb_q), n_train_rows=len(fit_rows) - n_val,
+               n_irr=len(irr), n_train_q=len(train_q), n_fallback_q=len(fb_q), n_outside_q=len(ood),
+               n_train_rows=len(fit_rows) - n_val,
                n_val_rows=n_val, n_heldout_rows=len(hold_rows), epochs_run=epochs_run)
     if exact_reference:
         t0 = _timer(torch)

@@ -59,14 +59,21 @@ def jobs(ctx, phx):
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
 def test_batched_matches_single_jobs_and_replays(ctx, phx, jobs, prec):
     import torch
-    ctx.gamma_batched(jobs, precision=prec)
+    import torch.cuda
+    tuned = ctx.gamma_batched(jobs, precision=prec)
     torch.cuda.synchronize()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for q, ch, sd in tuned:           # the autotuner's choices per job, written back
+        assert 8 <= q <= 128 and ch in (0, 1) and 0 <= sd <= sms // 2
     first = [j["gamma"].cpu().numpy().copy() for j in jobs]
     kap = [j["kappa"].cpu().numpy().copy() for j in jobs]
     for j in jobs:
         j["gamma"].zero_()
         j["kappa"].zero_()
-    ctx.gamma_batched(jobs, precision=prec)          # replay of the cached graph
+    # replay of the cached graph, with the tuned choices passed back in (same launches)
+    again = ctx.gamma_batched(jobs, precision=prec, q_tiles=[t[0] for t in tuned], chain=[t[1] for t in tuned],
+                              side_sms=[t[2] for t in tuned])
+    assert again == tuned
     torch.cuda.synchronize()
     for k, j in enumerate(jobs):
         assert np.array_equal(j["gamma"].cpu().numpy(), first[k]) or \
@@ -97,3 +104,17 @@ def test_batched_small_jobs_match_oracle(ctx, phx, jobs):
         big = go > 1e-3 * go.max()
         assert go.max() > 0
         assert (np.abs(g - go)[big] / go[big]).max() < 1e-4
+
+
+def test_batched_side_stream_share_changes_no_result(ctx, phx, jobs):
+    """The side-stream share (a tuned parameter) moves the fold and Fourier GEMM to other SMs
+    and changes no arithmetic: one stream and 24 side SMs agree to the FP64 accumulation order."""
+    import torch
+    out = []
+    for sd in (0, 24):
+        ctx.gamma_batched(jobs, precision="bf16x3", q_tiles=[16] * len(jobs), chain=[-1] * len(jobs),
+                          side_sms=[sd] * len(jobs))
+        torch.cuda.synchronize()
+        out.append([j["gamma"].cpu().numpy().copy() for j in jobs])
+    for a, b in zip(*out):
+        assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-30)

@@ -122,6 +122,58 @@ def test_velocity_products_fp32_option(ctx):
         assert 0 < np.abs(b).max() and d < 1e-6
 
 
+def test_harmonic_time_reversal_fill(ctx):
+    """PHX_OPT_HARMONIC_TR (default on): one q of every {q, -q} pair is solved and the other
+    filled by time reversal, D(-q) = conj D(q).  On the full 8x8x8 mesh of the 32-atom cell, and
+    on a shuffled list with a repeated point, a point given as -q + G and the self-conjugate
+    points: the filled points satisfy the oracle's eigenproblem (residual, unitarity, gauge,
+    velocities), e(-q) is exactly conj e(q), and frequencies, velocities and velocity products
+    equal the run that solves every q on its own."""
+    w = P.fcc_massdisorder_32()
+    f2 = w.ifc2()
+    c = w.crystal
+    qm = O.grid.mesh_qred(w.mesh)
+    rng = np.random.default_rng(4)
+    sub = rng.permutation(len(qm))[:40]
+    extra = np.array([qm[sub[0]], -qm[sub[0]] + np.array([1.0, 2.0, -1.0]), qm[sub[1]], qm[0], [0.5, 0.5, 0.0]])
+    for q in (qm, np.concatenate([qm[sub], extra])):
+        assert ctx.get_option("harmonic_tr") == 1
+        got = ctx.harmonic(c.lattice, c.masses, f2.idx, f2.val.reshape(-1, 9), q)
+        ctx.set_option("harmonic_tr", 0)
+        try:
+            ref = ctx.harmonic(c.lattice, c.masses, f2.idx, f2.val.reshape(-1, 9), q)
+        finally:
+            ctx.set_option("harmonic_tr", 1)
+        fmax = np.abs(ref[0]).max()
+        assert np.abs(got[0] * np.abs(got[0]) - ref[0] * np.abs(ref[0])).max() < 1e-11 * fmax ** 2
+        # per-mode velocities depend on the basis of a degenerate set: compare them on isolated
+        # modes, the basis-invariant products on all
+        gap = np.minimum(np.diff(ref[0], axis=1, prepend=-np.inf), np.diff(ref[0], axis=1, append=np.inf))
+        ok = ref[0] > 0.01
+        iso = ok & (gap > 1e-5 * fmax)
+        assert np.abs(got[2][iso] - ref[2][iso]).max() < 1e-8 * np.abs(ref[2]).max()
+        assert np.abs(got[3][ok] - ref[3][ok]).max() < 1e-8 * np.abs(ref[3]).max()
+        # pairs in the list: the later member is the conjugate (or a copy) of the earlier one
+        n_pairs = 0
+        for i in range(len(q)):
+            for j in range(i):
+                d_neg, d_same = q[j] + q[i], q[j] - q[i]
+                if np.all(np.abs(d_same - np.rint(d_same)) < 1e-9):
+                    assert np.array_equal(got[1][i], got[1][j])
+                    n_pairs += 1
+                    break
+                if np.all(np.abs(d_neg - np.rint(d_neg)) < 1e-9):
+                    assert np.array_equal(got[1][i], got[1][j].conj())
+                    assert np.array_equal(got[2][i], -got[2][j])
+                    n_pairs += 1
+                    break
+        assert n_pairs >= 3
+        # the filled points against the oracle's dynamical matrices
+        filled = [i for i in range(len(q)) if any(
+            np.all(np.abs((q[j] + q[i]) - np.rint(q[j] + q[i])) < 1e-9) for j in range(i))][:6]
+        _check_harmonic(w, f2, q[filled], got[0][filled], got[1][filled], got[2][filled], got[3][filled])
+
+
 # ----------------------------------------------------------------------------- linewidths, FP64
 
 def test_gamma_fp64_fcc1_all_irreducible(ctx, phx, fcc1):

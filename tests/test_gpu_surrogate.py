@@ -74,18 +74,25 @@ def test_mlp_gradients_match_fp64_reference(ctx):
 
 
 def test_surrogate_gain_over_coarse_mesh(ctx, phx):
-    """The trained ensemble on the dense 12^3 mesh (exact linewidths only on the 6^3 subgrid plus
-    a 5 % fallback) against the same exact kernel used without the network, on the 6^3 mesh."""
+    """The trained ensemble on the dense 12^3 mesh (exact linewidths only on the 6^3 subgrid, on
+    the q-points outside the network's domain and on a 5 % uncertainty fallback) against the same
+    exact kernel used without the network, on the 6^3 mesh.  One training is one draw of the
+    seeded splits and initial weights, whose kappa error scatters by a few percent on this small
+    training set, so the gain is judged on the median of three independent trainings."""
     from paper_2602_23728_gb300 import surrogate
     w = P.fcc_conventional_4(mesh=(12, 12, 12), temperature=40.0)
     c = w.crystal
     f2, f3 = w.ifc2(), w.ifc3()
-    r = surrogate.run(ctx, phx, c.lattice, c.masses, f2.idx, f2.val, f3.idx, f3.val, w.mesh, 2, w.rotations,
-                      w.temperature, epochs=3000, seed=1)
-    print({k: v for k, v in r.items() if not k.startswith("kappa_") or "err" in k})
-    assert r["kappa_rel_err_surrogate"] < r["kappa_rel_err_coarse"]
-    assert r["kappa_rel_err_surrogate"] < 0.05
-    assert r["heldout_median_rel_err"] < 0.25
+    errs = []
+    for seed in (1, 2, 3):
+        r = surrogate.run(ctx, phx, c.lattice, c.masses, f2.idx, f2.val, f3.idx, f3.val, w.mesh, 2, w.rotations,
+                          w.temperature, epochs=3000, seed=seed)
+        print({k: v for k, v in r.items() if not k.startswith("kappa_") or "err" in k})
+        errs.append(r["kappa_rel_err_surrogate"])
+        assert r["n_outside_q"] >= 1                      # the points nearest Gamma are outside
+        assert r["kappa_rel_err_surrogate"] < 0.05
+        assert r["heldout_median_rel_err"] < 0.25
+    assert np.median(errs) < r["kappa_rel_err_coarse"]
 
 
 def test_train_early_stopping_stops_on_unlearnable_target(ctx, phx):

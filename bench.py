@@ -906,6 +906,7 @@ def run_sc(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     ctx = new_context(phx, 0, args)
+    ctx.set_option("sc_matrix_free", args.sc_matrix_free)
     wl = Workload(phx, ctx, args.precision, dev, mesh=(args.sc_mesh,) * 3)
     w, c = wl.w, wl.c
     n, nq = wl.n, wl.nq
@@ -959,6 +960,8 @@ def run_sc(args):
                                    "96 modes, %dx%dx%d, 50 K, Gauss 0.1 THz; Gamma1 over the %d time-reversal "
                                    "representatives (R = %d rows)" % ((args.sc_mesh,) * 4 + (n_tr, R)),
                        "triplets_per_step": trip, "sc_tol": args.sc_tol, "sc_max_iter": args.sc_iter,
+                       "gamma1_form": "matrix-free (applied in every iteration's contraction pass)"
+                       if args.sc_matrix_free == 1 else "dense, resident in HBM (matrix-free if it did not fit)",
                        "gamma1_bytes": R * ((R + 127) // 128 * 128) * (8 if args.precision == "fp64" else 4),
                        "inputs_vs_l2": "Gamma1 (2.5 GB FP32) and the contraction operands stream well over the "
                                        "129 MB L2 every pass"},
@@ -1115,6 +1118,8 @@ def main():
                          "learned-linewidth pipeline; cell1000: the Gamma-only 1000-atom disordered cell "
                          "(each its own JSON line); fcc32-sc: the iterative BTE on the headline crystal")
     ap.add_argument("--sc-iter", type=int, default=100, help="fcc32-sc: maximum iterations")
+    ap.add_argument("--sc-matrix-free", type=int, default=0, choices=[0, 1, 2],
+                    help="fcc32-sc: Gamma1 dense when it fits (0), always matrix-free (1), always dense (2)")
     ap.add_argument("--sc-tol", type=float, default=1e-6, help="fcc32-sc: relative change of Tr(kappa)/3")
     ap.add_argument("--sc-mesh", type=int, default=8,
                     help="fcc32-sc: mesh edge (8 = the bench size; 4 keeps the per-launch shape of the "

@@ -121,6 +121,8 @@ const char* phx_version(void);
  *   PHX_OPT_VEL_FP32: 1 = phx_harmonic forms the velocity products dD/dq E (Eq. (groupvel))
  *     with FP32 products and sums (FP64 inputs and outputs: relative error ~1e-7, far below
  *     the 1e-5 bar on kappa); 0 (default) = FP64.  The eigensolve stays FP64 either way.
+ *   PHX_OPT_SC_MATRIX_FREE: phx_kappa_sc's Gamma1: 0 (default) = dense when it fits in the
+ *     device memory, matrix-free otherwise; 1 = always matrix-free; 2 = always dense.
  *   PHX_OPT_HARMONIC_TR: 1 (default) = phx_harmonic solves one q of every {q, -q} pair of its q
  *     list (mod G, components within 1e-9) and fills the other by time reversal: D(-q) is the
  *     complex conjugate of D(q) (Eq. (dynmat_reciprocal) with the G-periodic phase convention),
@@ -141,7 +143,8 @@ typedef enum {
     PHX_OPT_PAIR = 3,
     PHX_OPT_SIDE_SMS = 4,
     PHX_OPT_VEL_FP32 = 5,
-    PHX_OPT_HARMONIC_TR = 6
+    PHX_OPT_HARMONIC_TR = 6,
+    PHX_OPT_SC_MATRIX_FREE = 7
 } phx_option;
 phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value);
 /* The value an option has in effect: for PHX_OPT_SIDE_SMS the SM count the tensor-core path
@@ -425,10 +428,17 @@ phx_status phx_kappa_rta(phx_ctx* ctx, const phx_cell* cell, int32_t nq, int32_t
  *    linewidth sum, with weight w (decay + absorption term), adds w f'/f at column (q', nu')
  *    and w f''/f at column (q'' = -q-q', nu''); a column of a point listed through -q is
  *    added with sign -1.  Gamma1 stays on the device, R x R in FP64 (prec = PHX_FP64) or
- *    FP32 (tensor-core precisions); inputs whose Gamma1 does not fit in the device memory
- *    free at the call less 32 GB (kept for the contraction's workspace) return
- *    PHX_ERR_UNSUPPORTED (R x R x 4 bytes: 111 GB for 192 modes on a 12^3 mesh).  Its entries are accumulated with atomic adds (FP64 or FP32), so
- *    two calls on the same inputs agree to rounding, not bit for bit.
+ *    FP32 (tensor-core precisions), when it fits in the device memory free at the call less
+ *    32 GB (kept for the contraction's workspace; R x R x 4 bytes: 111 GB for 192 modes on a
+ *    12^3 mesh).  Its entries are accumulated with atomic adds (FP64 or FP32), so two calls
+ *    on the same inputs agree to rounding, not bit for bit.
+ *  - Matrix-free form (tensor-core precisions; PHX_OPT_SC_MATRIX_FREE): when Gamma1 does not
+ *    fit, or the option asks for it, nothing of order R^2 is stored: the first contraction
+ *    pass gives Gamma0, and every iteration runs one more pass whose epilogue applies the same
+ *    Gamma1 entries to lambda^(k) (y = Gamma1 lambda^(k), FP32 products, FP64 sums).  Each
+ *    iteration then costs a contraction pass instead of a pass over Gamma1; the iterates
+ *    agree with the dense form to rounding.  The FP64 path and the gamma1 output need the
+ *    dense form (PHX_ERR_UNSUPPORTED / PHX_ERR_INVALID).
  *  - Iteration (Eq. sc_iter) lambda^(k+1) = (v - Gamma1 lambda^(k)) / Gamma0 stops at the
  *    first k >= 1 with |Tr kappa^(k) - Tr kappa^(k-1)| < tol |Tr kappa^(k-1)| (*converged =
  *    1), or after max_iter iterations (*converged = 0).

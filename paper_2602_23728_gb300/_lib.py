@@ -139,7 +139,7 @@ KERNELS = {"dft": 0, "gemm_e2": 1, "gemm_e1_gamma": 2, "fold": 3, "fp64_gemm": 4
            "eigensolver": 6, "cell_sparse": 7, "cell_transpose": 8, "cell_gemm": 9, "eig_tridiag": 10,
            "eig_vectors": 11, "eig_back": 12, "eig_bisect": 13, "sc_step": 14, "chain": 15}
 
-OPTIONS = {"chain": 0, "wait_limit_ns": 1, "starve": 2, "pair": 3, "side_sms": 4, "vel_fp32": 5, "harmonic_tr": 6}
+OPTIONS = {"chain": 0, "wait_limit_ns": 1, "starve": 2, "pair": 3, "side_sms": 4, "vel_fp32": 5, "harmonic_tr": 6, "sc_matrix_free": 7}
 
 EXPORTED = ["phx_set_option", "phx_get_option", "phx_profile_enable", "phx_profile_read", "phx_create", "phx_destroy", "phx_last_error", "phx_version", "phx_irreducible", "phx_harmonic",
             "phx_fc3_create", "phx_fc3_destroy", "phx_fc3_num_d", "phx_gamma", "phx_gamma_multi_t", "phx_gamma_isotope", "phx_kappa_qhgk", "phx_gamma_cell", "phx_unfold", "phx_kappa_rta", "phx_kappa_sc",
@@ -286,6 +286,8 @@ class Context:
         'vel_fp32' (1: velocity products of harmonic() with FP32 products and sums),
         'harmonic_tr' (1, default: harmonic() solves one q of each {q, -q} pair and fills the other
         by time reversal; 0: every q solved on its own),
+        'sc_matrix_free' (kappa_sc's Gamma1: 0 dense when it fits, else matrix-free; 1 always
+        matrix-free; 2 always dense),
         'wait_limit_ns' (bound of every device barrier wait), 'starve' (test hook)."""
         self._check(lib.phx_set_option(self.h, OPTIONS[name], int(value)))
 

@@ -220,6 +220,11 @@ phx_status phx_set_option(phx_ctx* ctx, int32_t option, int64_t value) {
                 return phx_set_error(ctx, PHX_ERR_INVALID, "PHX_OPT_HARMONIC_TR %lld", (long long)value);
             ctx->opt_harm_tr = (int)value;
             return PHX_OK;
+        case PHX_OPT_SC_MATRIX_FREE:
+            if (value < 0 || value > 2)
+                return phx_set_error(ctx, PHX_ERR_INVALID, "PHX_OPT_SC_MATRIX_FREE %lld", (long long)value);
+            ctx->opt_sc_mfree = (int)value;
+            return PHX_OK;
         default:
             return phx_set_error(ctx, PHX_ERR_INVALID, "unknown option %d", option);
     }
@@ -236,6 +241,7 @@ phx_status phx_get_option(phx_ctx* ctx, int32_t option, int64_t* value) {
         case PHX_OPT_SIDE_SMS: *value = phx_side_sms(ctx); return PHX_OK;
         case PHX_OPT_VEL_FP32: *value = ctx->opt_vel_fp32; return PHX_OK;
         case PHX_OPT_HARMONIC_TR: *value = ctx->opt_harm_tr; return PHX_OK;
+        case PHX_OPT_SC_MATRIX_FREE: *value = ctx->opt_sc_mfree; return PHX_OK;
         default: return phx_set_error(ctx, PHX_ERR_INVALID, "unknown option %d", option);
     }
 }

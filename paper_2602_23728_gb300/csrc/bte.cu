@@ -145,6 +145,13 @@ __global__ void __launch_bounds__(kStepThreads) sc_step_kernel(const T* __restri
     }
 }
 
+// Matrix-free step: Fout = (v - y) / Gamma0 with y = Gamma1 F accumulated by a contraction pass
+__global__ void sc_update_kernel(int R, int64_t ld, const double* __restrict__ y, const double* __restrict__ vr,
+                                 const double* __restrict__ ig, double* __restrict__ Fout) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x)
+        for (int a = 0; a < 3; ++a) Fout[a * ld + r] = ig[r] * (vr[a * ld + r] - y[a * ld + r]);
+}
+
 // acc9[a][b] += sum_r wc[r] v[r][a] F[r][b]  (Eq. kappa_general before the 1/(N_q V) factor)
 __global__ void sc_kappa_kernel(int R, int64_t ld, const double* __restrict__ wc, const double* __restrict__ vr,
                                 const double* __restrict__ F, double* __restrict__ acc9) {
@@ -252,10 +259,22 @@ phx_status phx_kappa_sc(phx_ctx* ctx, const phx_cell* cell, const phx_fc3* fc3, 
     const size_t reserve = (size_t)32 << 30;
     const size_t have = ctx->ws.count("sc.G1") ? ctx->ws["sc.G1"].second : 0;   // reused in place
     const size_t avail = free_b + have > reserve ? free_b + have - reserve : 0;
-    if (R > INT32_MAX / 4 || mat_bytes > avail)
+    const bool fits = R <= INT32_MAX / 4 && mat_bytes <= avail;
+    // matrix-free form: every iteration applies Gamma1 to the current mean free paths inside a
+    // contraction pass (tensor-core precisions), so nothing of order R^2 is stored
+    const bool mfree = ctx->opt_sc_mfree == 1 || (ctx->opt_sc_mfree == 0 && !fits);
+    if (!mfree && !fits)
         return phx_set_error(ctx, PHX_ERR_UNSUPPORTED,
                              "phx_kappa_sc: Gamma1 of %lld rows needs %.1f GB (%.1f GB of device memory available)",
                              (long long)R, mat_bytes / 1e9, avail / 1e9);
+    if (mfree && prec == PHX_FP64)
+        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED,
+                             "phx_kappa_sc: the matrix-free iteration runs on the tensor-core precisions (Gamma1 "
+                             "of %lld rows: %.1f GB, %.1f GB available)", (long long)R, mat_bytes / 1e9, avail / 1e9);
+    if (mfree && gamma1)
+        return phx_set_error(ctx, PHX_ERR_INVALID, "phx_kappa_sc: the gamma1 output needs the dense Gamma1");
+    if (mfree && R > INT32_MAX / 4)
+        return phx_set_error(ctx, PHX_ERR_UNSUPPORTED, "phx_kappa_sc: %lld unknowns", (long long)R);
 
     cudaStream_t s = as_stream(stream);
     const int64_t n2 = (int64_t)n * n;
@@ -275,14 +294,17 @@ phx_status phx_kappa_sc(phx_ctx* ctx, const phx_cell* cell, const phx_fc3* fc3, 
     double* Fa = (double*)phx_ws(ctx, "sc.Fa", (size_t)3 * ld * 8);
     double* Fb = (double*)phx_ws(ctx, "sc.Fb", (size_t)3 * ld * 8);
     double* acc9 = (double*)phx_ws(ctx, "sc.acc9", 9 * 8);
-    void* mat = phx_ws(ctx, "sc.G1", mat_bytes);
-    if (!d_reps || !d_code || !nB || !cV || !gacc || !g0 || !vr || !wc || !ig || !Fa || !Fb || !acc9 || !mat)
+    void* mat = mfree ? nullptr : phx_ws(ctx, "sc.G1", mat_bytes);
+    double* yl = mfree ? (double*)phx_ws(ctx, "sc.y", (size_t)3 * ld * 8) : nullptr;
+    double* gacc2 = mfree ? (double*)phx_ws(ctx, "sc.gacc2", (size_t)R * 8) : nullptr;
+    if (!d_reps || !d_code || !nB || !cV || !gacc || !g0 || !vr || !wc || !ig || !Fa || !Fb || !acc9 ||
+        (!mfree && !mat) || (mfree && (!yl || !gacc2)))
         return PHX_ERR_NOMEM;
     PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(d_reps, reps.data(), (size_t)n_tr * 4, cudaMemcpyHostToDevice, s));
     PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(d_code, code.data(), (size_t)nq * 4, cudaMemcpyHostToDevice, s));
     PHX_CUDA_CHECK(ctx, phx_launch_occupations(d_f, nq * n, temperature, 0, nB, cV, s));
     PHX_CUDA_CHECK(ctx, cudaMemsetAsync(gacc, 0, (size_t)R * 8, s));
-    PHX_CUDA_CHECK(ctx, cudaMemsetAsync(mat, 0, mat_bytes, s));
+    if (!mfree) PHX_CUDA_CHECK(ctx, cudaMemsetAsync(mat, 0, mat_bytes, s));
     PHX_CUDA_CHECK(ctx, cudaMemsetAsync(vr, 0, (size_t)3 * ld * 8, s));
     PHX_CUDA_CHECK(ctx, cudaMemsetAsync(Fa, 0, (size_t)3 * ld * 8, s));
     PHX_CUDA_CHECK(ctx, cudaMemsetAsync(Fb, 0, (size_t)3 * ld * 8, s));
@@ -303,8 +325,8 @@ phx_status phx_kappa_sc(phx_ctx* ctx, const phx_cell* cell, const phx_fc3* fc3, 
     G1Target tgt{mat, ld, d_code, pref};
     if (prec == PHX_FP64)
         PHX_TRY(phx_gamma_fp64(ctx, fc3, d_f, d_e, nB, reps.data(), n_tr, gp, gacc, nullptr, s, &tgt));
-    else
-        PHX_TRY(phx_gamma_tc(ctx, fc3, d_f, d_e, nB, reps.data(), n_tr, gp, prec, gacc, nullptr, s, &tgt));
+    else   // matrix-free: the first pass gives Gamma0 only
+        PHX_TRY(phx_gamma_tc(ctx, fc3, d_f, d_e, nB, reps.data(), n_tr, gp, prec, gacc, nullptr, s, mfree ? nullptr : &tgt));
     PHX_CUDA_CHECK(ctx, phx_launch_finalize((int)R, n, d_reps, d_f, gacc, nullptr, pref, 0.0, f_min_thz, g0, nullptr, s));
     const int rblocks = (int)std::min<int64_t>((R + 255) / 256, 4096);
     sc_rows_kernel<<<rblocks, 256, 0, s>>>((int)R, n, d_reps, d_code, d_f, d_v, cV, g0, f_min_thz, ld, vr, wc, ig, Fa);
@@ -340,14 +362,29 @@ phx_status phx_kappa_sc(phx_ctx* ctx, const phx_cell* cell, const phx_fc3* fc3, 
     int done = 0;
     int conv_flag = 0;
     for (int it = 1; it <= max_iter; ++it) {
-        const int pf = phx_prof_begin(ctx, s);
-        if (prec == PHX_FP64)
-            sc_step_kernel<double><<<sblocks, kStepThreads, 0, s>>>((const double*)mat, ld, (int)R, Fcur, vr, ig, Fnext);
-        else
-            sc_step_kernel<float><<<sblocks, kStepThreads, 0, s>>>((const float*)mat, ld, (int)R, Fcur, vr, ig, Fnext);
-        PHX_CUDA_CHECK(ctx, cudaGetLastError());
-        phx_prof_end(ctx, pf, s, PHX_K_SC_STEP, 6.0 * (double)R * R, (double)R * ld * esz);
-        ctx->launches += 1;
+        if (mfree) {
+            // y = Gamma1 F from one contraction pass (Gamma0 recomputed into a scratch row)
+            PHX_CUDA_CHECK(ctx, cudaMemsetAsync(yl, 0, (size_t)3 * ld * 8, s));
+            PHX_CUDA_CHECK(ctx, cudaMemsetAsync(gacc2, 0, (size_t)R * 8, s));
+            G1Target app{nullptr, ld, d_code, pref, Fcur, yl};
+            PHX_TRY(phx_gamma_tc(ctx, fc3, d_f, d_e, nB, reps.data(), n_tr, gp, prec, gacc2, nullptr, s, &app));
+            sc_update_kernel<<<rblocks, 256, 0, s>>>((int)R, ld, yl, vr, ig, Fnext);
+            PHX_CUDA_CHECK(ctx, cudaGetLastError());
+            ctx->launches += 1;
+            int32_t st = 0;
+            PHX_CUDA_CHECK(ctx, cudaMemcpyAsync(&st, ctx->status_word, 4, cudaMemcpyDeviceToHost, s));
+            PHX_CUDA_CHECK(ctx, cudaStreamSynchronize(s));
+            if (st != 0) return phx_set_error(ctx, (phx_status)st, "phx_kappa_sc: a device wait gave up (status %d)", st);
+        } else {
+            const int pf = phx_prof_begin(ctx, s);
+            if (prec == PHX_FP64)
+                sc_step_kernel<double><<<sblocks, kStepThreads, 0, s>>>((const double*)mat, ld, (int)R, Fcur, vr, ig, Fnext);
+            else
+                sc_step_kernel<float><<<sblocks, kStepThreads, 0, s>>>((const float*)mat, ld, (int)R, Fcur, vr, ig, Fnext);
+            PHX_CUDA_CHECK(ctx, cudaGetLastError());
+            phx_prof_end(ctx, pf, s, PHX_K_SC_STEP, 6.0 * (double)R * R, (double)R * ld * esz);
+            ctx->launches += 1;
+        }
         std::swap(Fcur, Fnext);
         double* kk = kappa_hist + 9 * it;
         PHX_TRY(kappa_of(Fcur, kk));

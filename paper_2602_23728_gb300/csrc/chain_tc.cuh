@@ -68,11 +68,15 @@ struct ChainArgs {
     int64_t g1_rows, g1_ld, g1_row0;
     const int32_t* tr_code;
     float g1_scale;
+    // CHAIN_GL: the same rows applied to mean free paths, y[a][r] += sum_c Gamma1[r][c] lam[a][c]
+    // (planes [3][g1_ld], FP64; rows and columns as CHAIN_GS)
+    const double* lam;
+    double* ylam;
 };
 
 // epilogue variants: linewidths (+ WP2), linewidths at several temperatures, linewidths plus
-// the off-diagonal scattering rows
-enum { CHAIN_G = 0, CHAIN_GT = 1, CHAIN_GS = 2 };
+// the off-diagonal scattering rows, linewidths plus those rows applied to mean free paths
+enum { CHAIN_G = 0, CHAIN_GT = 1, CHAIN_GS = 2, CHAIN_GL = 3 };
 
 // 2^x by the special-function unit (approximate, flushes denormals; the weights use it on
 // arguments <= 0 only)
@@ -104,6 +108,8 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
     __shared__ float s_col[MODE == CHAIN_GS ? 2 : 1][MODE == CHAIN_GS ? kMaxNp : 1];
     __shared__ float s_row[MODE == CHAIN_GS ? 2 : 1][MODE == CHAIN_GS ? kMaxNp : 1];
     __shared__ float s_f2[MODE == CHAIN_GS ? kMaxNp : 1];
+    // CHAIN_GL: per partner mode nu' at q' the signed f' lambda(q', nu') of its column
+    __shared__ float s_lam[MODE == CHAIN_GL ? 3 : 1][MODE == CHAIN_GL ? kMaxNp : 1];
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int n = args.n, kcp = args.kcp, nkc = args.nkc, ra = args.ra, rb3 = args.rb3;
@@ -363,6 +369,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
 #pragma unroll
         for (int t = 0; t < kMaxT; ++t) nn2t[t] = 0.f;
         int c1 = 0, c2 = 0;                              // CHAIN_GS: time-reversal codes of q', q''
+        float lam2[3] = {0.f, 0.f, 0.f};                 // CHAIN_GL: f'' lambda of this lane's column
         // element weight cA (1+n'+n'') g(f-f'-f'') + cB (n'-n'') (g(f+f'-f'') - [pk] g(f+f''-f')):
         // (1, 2, no) for one ordered q' term; with exchange pairs (2, 2, yes) for q' != q'' (both
         // orderings) and (1, 1, yes) for q' = q'' (its (nu', nu'') sum already holds both)
@@ -428,6 +435,13 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                     s_tab[j] = make_float4(f1, v ? (float)args.nB[(int64_t)q1 * n + j] : 0.0f,
                                            (v && f1 >= args.f_min) ? 1.0f / f1 : 0.0f, 0.0f);
                     if (MODE == CHAIN_GS) s_f2[j] = v ? (float)args.freq[(int64_t)q2 * n + j] : 0.0f;
+                    if (MODE == CHAIN_GL) {
+                        const int cq = args.tr_code[q1];
+                        const int64_t col = (int64_t)(abs(cq) - 1) * n + j;
+                        const bool use = v && cq != 0 && col < args.g1_ld;
+                        const double fs = cq > 0 ? (double)f1 : -(double)f1;
+                        for (int a = 0; a < 3; ++a) s_lam[a][j] = use ? (float)(fs * args.lam[a * args.g1_ld + col]) : 0.0f;
+                    }
                     if (MODE == CHAIN_GT)
                         for (int t = 0; t < kMaxT; ++t)
                             s_n1t[t][j] = (v && t < args.n_t) ? (float)args.nB[t * args.nb_stride + (int64_t)q1 * n + j]
@@ -441,6 +455,14 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                         nn2t[t] = (nu2 < n && t < args.n_t) ? (float)args.nB[t * args.nb_stride + (int64_t)q2 * n + nu2]
                                                             : 0.f;
                 if (MODE == CHAIN_GS) { c1 = args.tr_code[q1]; c2 = args.tr_code[q2]; }
+                if (MODE == CHAIN_GL) {
+                    // this lane's column (q'', nu''): signed f'' lambda(q'', nu'')
+                    const int cq = args.tr_code[q2];
+                    const int64_t col = (int64_t)(abs(cq) - 1) * n + nu2;
+                    const bool use = nu2 < n && cq != 0 && col < args.g1_ld;
+                    const double fs = cq > 0 ? (double)f2 : -(double)f2;
+                    for (int a = 0; a < 3; ++a) lam2[a] = use ? (float)(fs * args.lam[a * args.g1_ld + col]) : 0.f;
+                }
                 epi_barrier(kChainEpiThreads);
                 cur_p = p;
             }
@@ -451,6 +473,7 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
             const float rowfac = norm * inv_f02;
             const float d02 = f0 - f2, s02 = f0 + f2, one_n2 = 1.f + nn2;
             float gs = 0.f, ws = 0.f;
+            float yl[3] = {0.f, 0.f, 0.f};               // CHAIN_GL: sum of e f' lambda' over columns
             float gst[kMaxT];
 #pragma unroll
             for (int t = 0; t < kMaxT; ++t) gst[t] = 0.f;
@@ -488,6 +511,12 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
                                     // not product: such lanes of D3 may hold anything)
                                     e[i] = live ? v2 * w * rowfac : 0.f;
                                     gs += e[i];
+                                } else if (MODE == CHAIN_GL) {
+                                    const float el = live ? v2 * w * rowfac : 0.f;
+                                    gs += el;
+                                    yl[0] = fmaf(el, s_lam[0][jj], yl[0]);
+                                    yl[1] = fmaf(el, s_lam[1][jj], yl[1]);
+                                    yl[2] = fmaf(el, s_lam[2][jj], yl[2]);
                                 } else {
                                     gs = fmaf(v2, w, gs);
                                     if (want_w) ws += w;
@@ -528,6 +557,28 @@ __global__ void __launch_bounds__(kChainThreads, 1) chain_kernel(const __grid_co
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) dg += __shfl_xor_sync(0xffffffffu, dg, off);
                     if (lane == 0 && ok && !abort_flag && dg != 0.0) atomicAdd(&args.gacc[t * args.t_stride + args.nu0 + nu], dg);
+                }
+            } else if (MODE == CHAIN_GL) {
+                // linewidth, and y of row (q, nu) += (scale / f) sum e (f' lambda' + f'' lambda'')
+                double dg = (double)gs;
+                double dy[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) dy[a] = (double)fmaf(gs, lam2[a], yl[a]);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    dg += __shfl_xor_sync(0xffffffffu, dg, off);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) dy[a] += __shfl_xor_sync(0xffffffffu, dy[a], off);
+                }
+                const int64_t row = args.g1_row0 + nu;
+                if (lane == 0 && ok && !abort_flag) {
+                    if (dg != 0.0) atomicAdd(&args.gacc[args.nu0 + nu], dg);
+                    if (row < args.g1_rows) {
+                        const double rs = (double)args.g1_scale / (double)f0;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            if (dy[a] != 0.0) atomicAdd(&args.ylam[a * args.g1_ld + row], rs * dy[a]);
+                    }
                 }
             } else {
                 double dg = MODE == CHAIN_GS ? (double)gs : (live ? (double)(gs * rowfac) : 0.0);

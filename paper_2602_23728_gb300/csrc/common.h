@@ -61,6 +61,7 @@ struct phx_ctx {
     int opt_side_sms = -1;                        // SMs of the side stream (-1: default, 0: one stream)
     int opt_vel_fp32 = 0;                         // velocity products of phx_harmonic in FP32
     int opt_harm_tr = 1;                          // phx_harmonic solves one q of each {q, -q} pair
+    int opt_sc_mfree = 0;                         // phx_kappa_sc: 0 dense Gamma1 when it fits, 1 matrix-free, 2 dense
     unsigned long long opt_wait_ns = 2000000000ull;   // bound of every device barrier wait
     int opt_starve = 0;                           // test hook: tensor-core producers issue nothing
 };
@@ -232,6 +233,10 @@ struct G1Target {
     int64_t ld;                 // row stride (elements)
     const int32_t* tr_code;     // device, [nq]
     double scale;               // the linewidth prefactor pi hbar conv^3 / (8 N_q)
+    // matrix-free form (tensor-core paths): with lam set, mat is unused and the pass adds
+    // y[a][r] += sum_c Gamma1[r][c] lam[a][c] (planes [3][ld], FP64) for every row r it covers
+    const double* lam = nullptr;
+    double* y = nullptr;
 };
 
 // gamma path shared parameters

@@ -49,7 +49,8 @@ constexpr size_t kSmemLimit = 232448;          // 227 KB opt-in
 
 // EPI_GT: EPI_G for up to kMaxT temperatures; EPI_GS: EPI_G plus the off-diagonal scattering
 // rows of Eq. (gamma1)
-enum { EPI_M = 0, EPI_X = 1, EPI_G = 2, EPI_GT = 3, EPI_GS = 4 };
+// EPI_GL: EPI_GS's rows applied to mean free paths instead of stored (matrix-free iteration)
+enum { EPI_M = 0, EPI_X = 1, EPI_G = 2, EPI_GT = 3, EPI_GS = 4, EPI_GL = 5 };
 constexpr int kMaxT = 4;
 enum { P_BF16X3 = 0, P_TF32 = 1 };
 
@@ -99,6 +100,9 @@ struct TcArgs {
     int64_t g1_row0;            // row of (this q, band nu0)
     const int32_t* tr_code;
     double g1_scale;
+    // EPI_GL: y[a][r] += sum_c Gamma1[r][c] lam[a][c] (planes [3][g1_ld], FP64)
+    const double* lam;
+    double* ylam;
     unsigned long long wait_ns; // bound of every barrier wait
     int starve;                 // test hook: the producer issues nothing (waits then run out)
 };
@@ -164,6 +168,7 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
     __shared__ float s_f1[kMaxNp], s_n1[kMaxNp], s_if1[kMaxNp];
     __shared__ float s_n1t[EPI == EPI_GT ? kMaxT * kMaxNp : 1];
     __shared__ float s_rows[EPI == EPI_GS ? 2 : 1][4][32];   // EPI_GS: part-1 row sums per lane group
+    __shared__ float s_lam[EPI == EPI_GL ? 3 : 1][EPI == EPI_GL ? kMaxNp : 1];   // EPI_GL: signed f' lambda'
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int np = args.np, mg = args.mg, NA = 2 * mg, nk = args.nk, stages = args.stages;
@@ -355,7 +360,7 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                 atomicExch(args.status, (int)PHX_ERR_TIMEOUT);
             }
             if (epi_barrier_any(kEpiThreads, !ok || abort_flag != 0)) break;   // one decision for all
-            if ((EPI == EPI_G || EPI == EPI_GT || EPI == EPI_GS) && p != cur_p) {
+            if ((EPI == EPI_G || EPI == EPI_GT || EPI == EPI_GS || EPI == EPI_GL) && p != cur_p) {
                 // partner tables of this problem's q' (the previous tile is done: barrier above)
                 q1 = args.qp1[p];
                 q2 = phx_third_index(args.iq, q1, args.m1, args.m2, args.m3);
@@ -372,6 +377,14 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                         for (int t = 0; t < kMaxT; ++t)
                             s_n1t[t * kMaxNp + j] =
                                 (v && t < args.n_t) ? (float)args.nB[t * args.nb_stride + (int64_t)q1 * args.n + j] : 0.0f;
+                    if (EPI == EPI_GL) {
+                        // column (q', nu'): f' lambda signed by the time-reversal code of q'
+                        const int cq = args.tr_code[q1];
+                        const int64_t col = (int64_t)(abs(cq) - 1) * args.n + j;
+                        const bool use = v && cq != 0 && col < args.g1_ld;
+                        const double fs = cq > 0 ? (double)f1 : -(double)f1;
+                        for (int a = 0; a < 3; ++a) s_lam[a][j] = use ? (float)(fs * args.lam[a * args.g1_ld + col]) : 0.0f;
+                    }
                 }
                 epi_barrier(kEpiThreads);
                 cur_p = p;
@@ -565,6 +578,87 @@ __global__ void __launch_bounds__(kernel_threads<EPI>(), 1) tc_gemm_kernel(const
                     const int prev = __shfl_up_sync(0xffffffffu, key, 1);
                     if (valid && (lane == 0 || prev != key) && dg != 0.0)
                         atomicAdd(&args.gacc[t * args.t_stride + args.nu0 + nu], dg);
+                }
+            } else if (EPI == EPI_GL) {
+                // EPI_GS's element weight e, applied instead of stored: e adds to the linewidth of
+                // (q, nu) and (scale / f) e (f' lambda(q', nu') + f'' lambda(q'', nu'')), signed by
+                // the time-reversal codes, to y of row (q, nu); segmented sums over the rows of
+                // each band in the warp, the first lane of a segment adds them
+                const int nu = row / args.n, n2i = row % args.n;
+                float f0 = 0.f, f2 = 0.f, nn2 = 0.f;
+                double f0d = 1.0, f2d = 0.0;
+                if (valid) {
+                    f0d = args.freq[(int64_t)args.iq * args.n + args.nu0 + nu];
+                    f0 = (float)f0d;
+                    f2d = args.freq[(int64_t)q2 * args.n + n2i];
+                    f2 = (float)f2d;
+                    nn2 = (float)args.nB[(int64_t)q2 * args.n + n2i];
+                }
+                const bool live = valid && f0 >= args.f_min && f2 >= args.f_min;
+                const bool gauss = args.shape == PHX_GAUSS;
+                const float a = -1.f / (args.sigma * args.sigma), h2 = 0.25f * args.sigma * args.sigma;
+                const float norm = gauss ? 0.56418958354775628f / args.sigma : 0.5f * args.sigma / 3.14159265358979f;
+                const float rowfac = live ? norm / (1558.5454565440389f * f0 * f2) : 0.0f;
+                const float d02 = f0 - f2, s02 = f0 + f2, lim = args.window * args.sigma;
+                const float one_n2 = 1.f + nn2;
+                const int key = valid ? nu : -1 - lane;
+                float l2[3] = {0.f, 0.f, 0.f};
+                {
+                    const int cq = args.tr_code[q2];
+                    const int64_t col = (int64_t)(abs(cq) - 1) * args.n + n2i;
+                    if (live && cq != 0 && col < args.g1_ld) {
+                        const double fs = cq > 0 ? f2d : -f2d;
+                        for (int c = 0; c < 3; ++c) l2[c] = (float)(fs * args.lam[c * args.g1_ld + col]);
+                    }
+                }
+                unsigned seg = 0;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const int off = 1 << k;
+                    const int k2 = __shfl_down_sync(0xffffffffu, key, off);
+                    if (lane + off < 32 && k2 == key) seg |= 1u << k;
+                }
+                const int prev_key = __shfl_up_sync(0xffffffffu, key, 1);
+                const bool head = lane == 0 || prev_key != key;
+                float gs = 0.f, y0 = 0.f, y1 = 0.f, y2 = 0.f;
+                float vi[16];
+                for (int j0 = half * 16; j0 < mg; j0 += kStride) {
+                    tc::tmem_ld16(taddr + j0, v);
+                    tc::tmem_ld16(taddr + mg + j0, vi);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int j = m0 + j0 + i;
+                        const float f1 = s_f1[j], n1 = s_n1[j], if1 = s_if1[j];
+                        const float x = d02 - f1, y = d02 + f1, z = s02 - f1;
+                        const float gd = fabsf(x) < lim ? (gauss ? __expf(a * x * x) : __frcp_rn(x * x + h2)) : 0.f;
+                        const float ga = fabsf(y) < lim ? (gauss ? __expf(a * y * y) : __frcp_rn(y * y + h2)) : 0.f;
+                        const float gb = pk && fabsf(z) < lim ? (gauss ? __expf(a * z * z) : __frcp_rn(z * z + h2)) : 0.f;
+                        const float w = (cA * (one_n2 + n1) * gd + cB * (n1 - nn2) * (ga - gb)) * (if1 * rowfac);
+                        const float e = fmaf(v[i], v[i], vi[i] * vi[i]) * w;
+                        gs += e;
+                        y0 = fmaf(e, s_lam[0][j], y0);
+                        y1 = fmaf(e, s_lam[1][j], y1);
+                        y2 = fmaf(e, s_lam[2][j], y2);
+                    }
+                }
+                double dg = (double)gs;
+                double dy[3] = {(double)fmaf(gs, l2[0], y0), (double)fmaf(gs, l2[1], y1), (double)fmaf(gs, l2[2], y2)};
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const double og = __shfl_down_sync(0xffffffffu, dg, 1 << k);
+                    const double o0 = __shfl_down_sync(0xffffffffu, dy[0], 1 << k);
+                    const double o1 = __shfl_down_sync(0xffffffffu, dy[1], 1 << k);
+                    const double o2 = __shfl_down_sync(0xffffffffu, dy[2], 1 << k);
+                    if (seg & (1u << k)) { dg += og; dy[0] += o0; dy[1] += o1; dy[2] += o2; }
+                }
+                if (valid && head) {
+                    if (dg != 0.0) atomicAdd(&args.gacc[args.nu0 + nu], dg);
+                    const int64_t grow = args.g1_row0 + nu;
+                    if (grow < args.g1_rows) {
+                        const double rs = args.g1_scale / f0d;
+                        for (int c = 0; c < 3; ++c)
+                            if (dy[c] != 0.0) atomicAdd(&args.ylam[c * args.g1_ld + grow], rs * dy[c]);
+                    }
                 }
             } else if (EPI == EPI_GS) {
                 // EPI_G with the per-element weight e = |V|^2 x (decay + absorption weight) x the
@@ -1172,6 +1266,7 @@ template <int PREC>
 cudaError_t launch_chain_mode(ChainArgs& a, int mode, size_t smem, int ctas, cudaStream_t s) {
     if (mode == CHAIN_GT) return launch_chain<PREC, CHAIN_GT>(a, smem, ctas, s);
     if (mode == CHAIN_GS) return launch_chain<PREC, CHAIN_GS>(a, smem, ctas, s);
+    if (mode == CHAIN_GL) return launch_chain<PREC, CHAIN_GL>(a, smem, ctas, s);
     return launch_chain<PREC, CHAIN_G>(a, smem, ctas, s);
 }
 
@@ -1508,9 +1603,11 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
         if (g1) {
             aC.g1 = (float*)g1->mat; aC.g1_ld = g1->ld; aC.tr_code = g1->tr_code; aC.g1_scale = (float)g1->scale;
             aC.g1_rows = (int64_t)n_irr * n;
+            aC.lam = g1->lam; aC.ylam = g1->y;
         }
     }
-    const int chain_mode = n_t > 0 ? CHAIN_GT : (g1 ? CHAIN_GS : CHAIN_G);
+    const bool g1_apply = g1 && g1->lam;
+    const int chain_mode = n_t > 0 ? CHAIN_GT : (g1 ? (g1_apply ? CHAIN_GL : CHAIN_GS) : CHAIN_G);
     aD.np = qp_np; aD.mg = qp_np; aD.n_groups = 1; aD.nk = P.nk_d; aD.stages = P.st_d;
     aD.n_acc = (4 * qp_np <= 512) ? 2 : 1;
     aD.tmem_cols = tmem_cols_for(2 * qp_np, aD.n_acc);
@@ -1534,6 +1631,7 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
     if (g1) {
         aB.g1 = (float*)g1->mat; aB.g1_ld = g1->ld; aB.tr_code = g1->tr_code; aB.g1_scale = g1->scale;
         aB.g1_rows = (int64_t)n_irr * n;
+        aB.lam = g1->lam; aB.ylam = g1->y;
     }
 
     // With a side stream: the per-q lists, the fold and the Fourier GEMM run on s2 over `side`
@@ -1655,6 +1753,8 @@ phx_status tc_enqueue(phx_ctx* ctx, const TcPlan& P, const phx_fc3* f, const TcB
                 pp = phx_prof_begin(ctx, s);
                 if (n_t > 0)
                     PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_GT>(ctx, aB, P.stream_b, Qt, main_ctas, s)));
+                else if (g1_apply)
+                    PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_GL>(ctx, aB, P.stream_b, Qt, main_ctas, s)));
                 else if (g1)
                     PHX_CUDA_CHECK(ctx, (launch_gemm_any<PREC, EPI_GS>(ctx, aB, P.stream_b, Qt, main_ctas, s)));
                 else

@@ -611,40 +611,33 @@ __global__ void velocity_kernel(const double2* __restrict__ E, const double2* __
 // |x - nearest integer| below the tolerance of q-point identity (reduced coordinates)
 __device__ __forceinline__ bool near_integer(double x) { return fabs(x - rint(x)) < 1e-9; }
 
-// One thread per q_i: the first j (ascending, j < i) with q_j = q_i or q_j = -q_i mod G.  The
-// classes are unions of two G-translate sets, so the first index met is the class minimum and
-// every member finds the same one.  q_j tiles are staged in shared memory.
+// One warp per q_i: the first j (ascending, j < i) with q_j = q_i or q_j = -q_i mod G, found
+// 32 candidates at a time with a ballot.  The classes are unions of two G-translate sets, so
+// the first index met is the class minimum and every member finds the same one.
 __global__ void __launch_bounds__(256)
 tr_classes_kernel(const double* __restrict__ q_frac, int nq, int32_t* __restrict__ code, int32_t* __restrict__ skip) {
-    __shared__ double tq[3][256];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool act = i < nq;
-    const double a0 = act ? q_frac[3 * i] : 0.0, a1 = act ? q_frac[3 * i + 1] : 0.0,
-                 a2 = act ? q_frac[3 * i + 2] : 0.0;
+    const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= nq) return;                                   // whole warp
+    const double a0 = q_frac[3 * i], a1 = q_frac[3 * i + 1], a2 = q_frac[3 * i + 2];
     int rep = i, cj = 0;
-    bool done = !act;
-    const int j_end = min(nq, (blockIdx.x + 1) * blockDim.x);   // no j at or beyond the block's last i
-    for (int t0 = 0; t0 < j_end; t0 += 256) {
-        const int jl = t0 + threadIdx.x;
-        if (jl < nq)
-            for (int c = 0; c < 3; ++c) tq[c][threadIdx.x] = q_frac[3 * jl + c];
-        __syncthreads();
-        const int lim = min(256, j_end - t0);
-        for (int k = 0; k < lim && !done; ++k) {
-            const int j = t0 + k;
-            if (j >= i) { done = true; break; }
-            const double b0 = tq[0][k], b1 = tq[1][k], b2 = tq[2][k];
-            const bool same = near_integer(b0 - a0) && near_integer(b1 - a1) && near_integer(b2 - a2);
-            const bool neg = near_integer(b0 + a0) && near_integer(b1 + a1) && near_integer(b2 + a2);
-            if (same || neg) {
-                rep = j;
-                cj = same ? 0 : 1;
-                done = true;
-            }
+    for (int j0 = 0; j0 < i; j0 += 32) {
+        const int j = j0 + lane;
+        bool same = false, neg = false;
+        if (j < i) {
+            const double b0 = q_frac[3 * j], b1 = q_frac[3 * j + 1], b2 = q_frac[3 * j + 2];
+            same = near_integer(b0 - a0) && near_integer(b1 - a1) && near_integer(b2 - a2);
+            neg = near_integer(b0 + a0) && near_integer(b1 + a1) && near_integer(b2 + a2);
         }
-        if (__syncthreads_and(done)) break;
+        const unsigned m = __ballot_sync(0xffffffffu, same || neg);
+        if (m) {
+            const int k = __ffs(m) - 1;
+            rep = j0 + k;
+            cj = __shfl_sync(0xffffffffu, (same ? 0 : 1), k);
+            break;
+        }
     }
-    if (act) {
+    if (lane == 0) {
         code[i] = 2 * rep + cj;
         skip[i] = rep != i;
     }
@@ -678,7 +671,7 @@ tr_fill_kernel(const int32_t* __restrict__ code, int n, double* __restrict__ fre
 
 cudaError_t phx_launch_tr_classes(const double* q_frac, int nq, int32_t* code, int32_t* skip, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
-    tr_classes_kernel<<<(nq + 255) / 256, 256, 0, s>>>(q_frac, nq, code, skip);
+    tr_classes_kernel<<<(int)(((int64_t)nq * 32 + 255) / 256), 256, 0, s>>>(q_frac, nq, code, skip);
     return cudaGetLastError();
 }
 

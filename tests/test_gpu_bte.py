@@ -147,6 +147,38 @@ def test_tensor_core_within_bar(ctx, case, precision, bar, chain):
         assert ek < 1e-2
 
 
+@pytest.mark.parametrize("chain", [1, 2])
+def test_matrix_free_matches_dense(ctx, phx, case, chain):
+    """PHX_OPT_SC_MATRIX_FREE: Gamma1 applied to the mean free paths inside every iteration's
+    contraction pass instead of stored (chain 1: the chained kernel where it fits, 2: the two
+    GEMMs).  Gamma0, every kappa iterate and the mean free paths equal the dense form's to
+    FP32 accumulation order, and the iterates are within the kappa bar of the oracle.  The
+    FP64 path and the gamma1 output need the dense form."""
+    ctx.set_option("chain", chain)
+    try:
+        ctx.set_option("sc_matrix_free", 2)
+        d = _run(ctx, case, "bf16x3")
+        ctx.set_option("sc_matrix_free", 1)
+        assert ctx.get_option("sc_matrix_free") == 1
+        m = _run(ctx, case, "bf16x3")
+        with pytest.raises(phx.PhxError):
+            _run(ctx, case, "fp64")
+        with pytest.raises(phx.PhxError):
+            _run(ctx, case, "bf16x3", want_gamma1=True)
+    finally:
+        ctx.set_option("sc_matrix_free", 0)
+        ctx.set_option("chain", 0)
+    assert m["n_iter"] == d["n_iter"] == case["n_iter"]
+    e0 = float(np.abs(m["gamma0"] - d["gamma0"]).max() / d["gamma0"].max())
+    ek = _frob(m["kappa"], d["kappa"])
+    el = float(np.abs(m["mfp"] - d["mfp"]).max() / np.abs(d["mfp"]).max())
+    eo = _frob(m["kappa"], case["hist"])
+    print(f"{case['name']} chain {chain}: matrix-free vs dense Gamma0 {e0:.1e} kappa {ek:.1e} mfp {el:.1e}; "
+          f"vs oracle kappa {eo:.1e}")
+    assert e0 <= 1e-6 and ek <= 1e-6 and el <= 1e-5
+    assert eo < KAPPA_BAR
+
+
 def test_converged_iterate_solves_the_inverse_problem(ctx, case):
     r = _run(ctx, case, "fp64", max_iter=400, tol=1e-14)
     assert r["converged"] and r["n_iter"] < 400

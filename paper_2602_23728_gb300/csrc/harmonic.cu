@@ -360,20 +360,21 @@ hh_reduce_kernel(const double2* __restrict__ Dg, double2* __restrict__ Rg, doubl
 }
 
 __global__ void __launch_bounds__(kQlThreads)
-ql_back_kernel(const double2* __restrict__ Rg, const double* __restrict__ scratch, double* __restrict__ Zg, int n,
+ql_back_kernel(const double2* __restrict__ Rg, const double* __restrict__ scratch, int n,
                double* __restrict__ freq, double2* __restrict__ evec, int32_t* __restrict__ status,
                const int32_t* __restrict__ skip) {
     if (skip && skip[blockIdx.x]) return;
-    __shared__ double d[kHhqlMaxModes], e[kHhqlMaxModes], rc[kHhqlMaxModes], rs[kHhqlMaxModes];
+    extern __shared__ double Z[];                            // real n x n, column-major
+    __shared__ double d[kHhqlMaxModes], e[kHhqlMaxModes];
+    __shared__ double rcb[2][kHhqlMaxModes], rsb[2][kHhqlMaxModes];   // rotations of two rounds
     __shared__ double2 ph[kHhqlMaxModes];
     __shared__ int rank_of[kHhqlMaxModes];
-    __shared__ int sweep_lo, sweep_hi, sweep_fail;
+    __shared__ int sw_lo[2], sw_hi[2], sweep_fail;
     const int qi = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int64_t nn = (int64_t)n * n;
     const double2* R = Rg + (int64_t)qi * nn;
     const double* sc = scratch + (int64_t)qi * 4 * n;
-    double* Z = Zg + (int64_t)qi * nn * 2;                  // real n x n, column-major
     double2* Eo = evec + (int64_t)qi * nn;
     if (tid == 0) {
         double2 dl = make_double2(1.0, 0.0);
@@ -396,28 +397,34 @@ ql_back_kernel(const double2* __restrict__ Rg, const double* __restrict__ scratc
     // symmetric QR step with Wilkinson shift inside the symmetric QR algorithm): every round
     // zeroes the negligible off-diagonals, takes the lowest unreduced block [lo, hi], and chases
     // one bulge from its top to its bottom with Givens rotations Q_k on rows/columns (k, k+1),
-    // T <- Q_k T Q_k^T, Z <- Z Q_k^T.  Thread 0 updates (d, e) and records (c_k, s_k); every
-    // thread then applies the round's rotations to its rows of Z.
+    // T <- Q_k T Q_k^T, Z <- Z Q_k^T.  The rounds are pipelined: warp 0 finds and chases round
+    // r + 1 (it needs only d and e) while warps 1-3 apply the rotations of round r to the rows
+    // of Z, one row per thread, from a second buffer.
     const int max_rounds = kQlMaxIter * (n > 0 ? n : 1);
-    for (int round = 0;; ++round) {
-        if (tid == 0) {
-            int hi = -1, lo = 0;
-            for (int k = 0; k + 1 < n; ++k)
-                if (fabs(e[k]) <= 2.2204460492503131e-16 * (fabs(d[k]) + fabs(d[k + 1]))) e[k] = 0.0;
-            for (int k = n - 2; k >= 0; --k)
-                if (e[k] != 0.0) { hi = k + 1; break; }
-            if (hi > 0) {
-                lo = hi - 1;
-                while (lo > 0 && e[lo - 1] != 0.0) --lo;
-            }
-            if (hi < 0 || round >= max_rounds) {
-                sweep_lo = sweep_hi = 0;                     // done (or given up)
-                if (hi >= 0) sweep_fail = 1;
+    auto chase = [&](int b, int round) {
+        // deflation test of every off-diagonal, lanes in parallel
+        for (int k = lane; k + 1 < n; k += 32)
+            if (fabs(e[k]) <= 2.2204460492503131e-16 * (fabs(d[k]) + fabs(d[k + 1]))) e[k] = 0.0;
+        __syncwarp();
+        int hk = -1;                                         // the last nonzero off-diagonal
+        for (int k = lane; k + 1 < n; k += 32)
+            if (e[k] != 0.0) hk = k;
+        for (int o = 16; o > 0; o >>= 1) hk = max(hk, __shfl_xor_sync(0xffffffffu, hk, o));
+        const int hi = hk + 1;
+        int zk = -1;                                         // the last zero one below it
+        for (int k = lane; k < hi - 1; k += 32)
+            if (e[k] == 0.0) zk = k;
+        for (int o = 16; o > 0; o >>= 1) zk = max(zk, __shfl_xor_sync(0xffffffffu, zk, o));
+        const int lo = zk + 1;
+        if (lane == 0) {
+            if (hk < 0 || round >= max_rounds) {
+                sw_lo[b] = sw_hi[b] = 0;                     // done (or given up)
+                if (hk >= 0) sweep_fail = 1;
             } else {
                 // Wilkinson shift: the eigenvalue of the block's trailing 2x2 nearer d[hi]
-                const double dl = 0.5 * (d[hi - 1] - d[hi]), b = e[hi - 1];
-                const double den = dl + copysign(hypot(dl, b), dl);
-                const double mu = d[hi] - (den != 0.0 ? b * (b / den) : b);
+                const double dl = 0.5 * (d[hi - 1] - d[hi]), bq = e[hi - 1];
+                const double den = dl + copysign(hypot(dl, bq), dl);
+                const double mu = d[hi] - (den != 0.0 ? bq * (bq / den) : bq);
                 double x = d[lo] - mu, z = e[lo];
                 // d[k] and e[k] of the rotation in flight are carried in registers (each rotation
                 // rewrites them for the next), so the serial chain touches shared memory only
@@ -445,37 +452,37 @@ ql_back_kernel(const double2* __restrict__ Rg, const double* __restrict__ scratc
                         a = dk1;
                         bb = en * c;
                     }
-                    rc[k] = c;
-                    rs[k] = sn;
+                    rcb[b][k] = c;
+                    rsb[b][k] = sn;
                 }
-                sweep_lo = lo;
-                sweep_hi = hi;
+                sw_lo[b] = lo;
+                sw_hi[b] = hi;
             }
         }
-        __syncthreads();
-        const int lo = sweep_lo, hi = sweep_hi;
-        if (hi <= lo) break;
-        // Z <- Z Q_lo^T ... Q_{hi-1}^T on columns (k, k+1): column k is final after rotation k,
-        // column k+1 is carried to the next rotation in a register
-        // (the columns a block of 8 rotations reads are loaded together, so their latencies
-        // overlap instead of following each store)
-        for (int row = tid; row < n; row += nt) {
-            double carry = Z[(int64_t)lo * n + row];
-            for (int k0 = lo; k0 < hi; k0 += 8) {
-                const int kb = min(8, hi - k0);
-                double zc[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) zc[u] = u < kb ? Z[(int64_t)(k0 + u + 1) * n + row] : 0.0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (u >= kb) break;
-                    const int k = k0 + u;
-                    const double c = rc[k], sn = rs[k];
-                    Z[(int64_t)k * n + row] = c * carry + sn * zc[u];
-                    carry = c * zc[u] - sn * carry;
+        __syncwarp();
+    };
+    if (warp == 0) chase(0, 0);
+    __syncthreads();
+    for (int round = 0;; ++round) {
+        const int b = round & 1;
+        const int lo = sw_lo[b], hi = sw_hi[b];
+        if (hi <= lo) break;                                 // same decision in every thread
+        if (warp == 0) {
+            chase(b ^ 1, round + 1);
+        } else {
+            // Z <- Z Q_lo^T ... Q_{hi-1}^T on columns (k, k+1) of this thread's row: column k is
+            // final after rotation k, column k+1 is carried to the next rotation in a register
+            const int row = tid - 32;
+            if (row < n) {
+                double carry = Z[(int64_t)lo * n + row];
+                for (int k = lo; k < hi; ++k) {
+                    const double c = rcb[b][k], sn = rsb[b][k];
+                    const double z1 = Z[(int64_t)(k + 1) * n + row];
+                    Z[(int64_t)k * n + row] = c * carry + sn * z1;
+                    carry = c * z1 - sn * carry;
                 }
+                Z[(int64_t)hi * n + row] = carry;
             }
-            Z[(int64_t)hi * n + row] = carry;
         }
         __syncthreads();
     }
@@ -705,8 +712,12 @@ cudaError_t phx_launch_jacobi(double* A, double* V, int n, int nq, double* freq,
         cudaError_t e = cudaFuncSetAttribute(hh_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         hh_reduce_kernel<<<nq, 256, smem, s>>>((const double2*)A, (double2*)V, scratch, n, skip);
-        ql_back_kernel<<<nq, kQlThreads, 0, s>>>((const double2*)V, scratch, A, n, freq, (double2*)evec, status,
-                                                 skip);
+        // Z (real n x n) in shared memory
+        const size_t zbytes = (size_t)n * n * sizeof(double);
+        e = cudaFuncSetAttribute(ql_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zbytes);
+        if (e != cudaSuccess) return e;
+        ql_back_kernel<<<nq, kQlThreads, zbytes, s>>>((const double2*)V, scratch, n, freq, (double2*)evec, status,
+                                                      skip);
         return cudaGetLastError();
     }
     const size_t static_bytes = 8 * 1024;     // rotation tables etc. (upper bound)

@@ -84,3 +84,46 @@ def test_create_without_gpu_fails_loudly(phx):
         pytest.skip("a GPU is present")
     with pytest.raises(phx.PhxError):
         phx.Context(0)
+
+
+def _header_structs():
+    """Field lists (name, C type) of the typedef'd structs of the header, in order."""
+    text = ""
+    for name in os.listdir(os.path.join(ROOT, "include")):
+        if name.endswith(".h"):
+            text += open(os.path.join(ROOT, "include", name)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, tag in re.findall(r"typedef struct\s*\{(.*?)\}\s*(phx_[a-z0-9_]+)\s*;", text, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"(.*?)([A-Za-z_][A-Za-z0-9_]*)\s*(\[\s*(\d+)\s*\])?$", decl)
+            ctype = m.group(1).replace("const ", "").strip()
+            fields.append((m.group(2), ctype, int(m.group(4)) if m.group(4) else None))
+        out[tag] = fields
+    return out
+
+
+@pytest.mark.parametrize("tag,cls", [("phx_cell", "Cell"), ("phx_ifc2", "Ifc2"), ("phx_ifc3", "Ifc3"),
+                                     ("phx_broadening", "Broadening"), ("phx_job", "Job"), ("phx_tune", "Tune")])
+def test_ctypes_structs_mirror_the_header(phx, tag, cls):
+    """The binding's ctypes mirrors of the ABI structs have the header's fields, in order and
+    with matching C types (pointer, int32, int64, double, nested struct, fixed array)."""
+    import paper_2602_23728_gb300._lib as L
+    structs = _header_structs()
+    assert tag in structs
+    mirror = getattr(L, cls)._fields_
+    assert [f[0] for f in mirror] == [f[0] for f in structs[tag]]
+    scalar = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double}
+    for (name, ctype, count), (mname, mtype) in zip(structs[tag], mirror):
+        if ctype.endswith("*"):
+            assert mtype is ctypes.c_void_p, (tag, name)
+        elif count is not None:
+            assert mtype == scalar[ctype] * count, (tag, name)
+        elif ctype in scalar:
+            assert mtype is scalar[ctype], (tag, name)
+        else:                                           # nested struct by value
+            assert ctype.startswith("phx_") and mtype.__name__ == {"phx_broadening": "Broadening"}[ctype], (tag, name)

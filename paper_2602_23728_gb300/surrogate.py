@@ -146,10 +146,7 @@ def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh,
     # uncertain mode ranks in the top (100 - uncertainty_pct) % of the other q-points outside
     # the subgrid
     cand = np.array([k for k in range(len(irr)) if not train_mask0[k]], dtype=np.int64)
-    ood = cand[np.isinf(score[cand])]
-    rest = cand[~np.isinf(score[cand])]
-    n_fb = int(np.ceil((100.0 - uncertainty_pct) / 100.0 * len(cand)))
-    pick = rest[np.argsort(-score[rest], kind="stable")[:n_fb]] if n_fb > 0 else rest[:0]
+    ood, pick = fallback_rows(score, cand, uncertainty_pct)
     fb_q = sorted(int(irr[k]) for k in np.concatenate([ood, pick]))
     t0 = _timer(torch)
     if fb_q:
@@ -214,6 +211,20 @@ def run(ctx, phx, lattice, masses, ifc2_idx, ifc2_val, ifc3_idx, ifc3_val, mesh,
         out["triplets_exact"] = int((fr >= f_min).sum()) * nq * n * n
     model.close()
     return out
+
+
+def fallback_rows(score, cand, uncertainty_pct):
+    """Rows (irreducible q-points) sent back to the exact kernel among the candidates `cand`:
+    every one whose score is infinite (a mode outside the network's domain), and the
+    (100 - uncertainty_pct) % of all candidates with the largest finite scores (ensemble
+    spread; ties keep candidate order).  Returns (outside, by_spread)."""
+    cand = np.asarray(cand, dtype=np.int64)
+    score = np.asarray(score, dtype=np.float64)
+    ood = cand[np.isinf(score[cand])]
+    rest = cand[~np.isinf(score[cand])]
+    n_fb = int(np.ceil((100.0 - uncertainty_pct) / 100.0 * len(cand)))
+    pick = rest[np.argsort(-score[rest], kind="stable")[:n_fb]] if n_fb > 0 else rest[:0]
+    return ood, pick
 
 
 def _orbit_map(mesh, rotations, reps, phx):

@@ -99,3 +99,22 @@ def test_subgrid_points():
     for p in pts:
         i, j, k = p // (mesh[1] * mesh[2]), (p // mesh[2]) % mesh[1], p % mesh[2]
         assert i % 2 == 0 and j % 2 == 0 and k % 2 == 0
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the oracle on the host's cores, a bounded q' sample per
+    step) prints one JSON line with the metric, unit and direction of the GPU arm and its
+    cpu_baseline and e2e objects."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--ref-qp", "4"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "triplets/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 1 and d["dtype"] == "f64"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
